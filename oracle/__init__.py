@@ -1,0 +1,228 @@
+"""FP64 CPU oracle for the SCA+ADAM potential (arXiv 2311.04435, Eq. 1 and Eq. 2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  The product package never imports it, and it imports nothing from the
+product package except the seeded input generators (which hold none of the
+method's arithmetic).
+
+The arithmetic lives in ``sca_oracle.c`` (plain C, FP64, dense complex LU with
+partial pivoting, explicit inverse columns, a Jacobi eigenvalue route and
+explicit Adam); this file compiles it with gcc and exposes it through ctypes.
+Every function documents the passage of the paper it follows in the C source.
+
+Parity status: every function here is pinned by tests in
+``tests/test_oracle_pins.py`` (Fourier closed forms at phi = 0 and for a
+staggered field, the eigenvalue route, finite differences, the Hartree-Fock
+gap equation and the paper's printed critical ionic potentials).  The basin
+reached by Adam from a random start has no closed form: it is pinned only
+through the per-step quantities above ("parity unpinned" for the basin itself).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sca_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libsca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Params(ctypes.Structure):
+    """Mirror of the physical parameters: lattice L, Matsubara count, precision
+    tag (ignored by the oracle), ionic convention (0: -/+Delta as in Eq. 1,
+    1: -/+Delta/2), hopping t, interaction U, ionic Delta, temperature T, mu."""
+
+    _fields_ = [("L", ctypes.c_int32), ("n_omega", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("ionic", ctypes.c_int32), ("t", ctypes.c_double), ("U", ctypes.c_double),
+                ("delta", ctypes.c_double), ("T", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("grad_tol", ctypes.c_double),
+                ("max_steps", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile sca_oracle.c into _build/libsca_oracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            P = ctypes.POINTER(Params)
+            l.orc_hamiltonian.argtypes = [P, dp, dp, ctypes.c_int, dp]
+            l.orc_omega_grad.argtypes = [P, dp, dp, dp, dp, dp, dp]
+            l.orc_omega_grad.restype = ctypes.c_int
+            l.orc_omega_grad_eig.argtypes = [P, dp, dp, dp, dp, dp, dp]
+            l.orc_omega_grad_eig.restype = ctypes.c_int
+            l.orc_block.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+            l.orc_block.restype = ctypes.c_int
+            l.orc_blocks_sample.argtypes = [P, dp, dp, ctypes.c_int, ip, dp, dp]
+            l.orc_blocks_sample.restype = ctypes.c_int
+            l.orc_seed_phi.argtypes = [ctypes.c_uint64, ctypes.c_int, dp]
+            l.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            l.orc_splitmix64.restype = ctypes.c_uint64
+            l.orc_adam_run.argtypes = [P, dp, ctypes.POINTER(Adam), dp, dp, dp, ip, dp, dp]
+            l.orc_adam_run.restype = ctypes.c_int
+            l.orc_num_threads.restype = ctypes.c_int
+            l.orc_omega_n.argtypes = [P, ctypes.c_int]
+            l.orc_omega_n.restype = ctypes.c_double
+            _lib = l
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(L, n_omega, U, T, delta=0.0, t=1.0, mu=0.0, ionic=0, prec=0) -> Params:
+    return Params(int(L), int(n_omega), int(prec), int(ionic), float(t), float(U),
+                  float(delta), float(T), float(mu))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def hamiltonian(p: Params, phi, sigma: int, eps_extra=None) -> np.ndarray:
+    N = p.L * p.L
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    H = np.zeros((N, N))
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    lib().orc_hamiltonian(ctypes.byref(p), _dp(ee), _dp(phi), int(sigma), _dp(H))
+    return H
+
+
+def omega_grad(p: Params, phi, eps_extra=None, per_block: bool = False):
+    """Omega, dOmega/dphi by the LU route; with per_block, also ld[b] and
+    sigma*Re G_ii[b, i] for every block b = 2n + s."""
+    N, B = p.L * p.L, 2 * p.n_omega
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    om = np.zeros(1)
+    g = np.zeros(N)
+    ld = np.zeros(B) if per_block else None
+    gd = np.zeros((B, N)) if per_block else None
+    rc = lib().orc_omega_grad(ctypes.byref(p), _dp(ee), _dp(phi), _dp(om), _dp(g), _dp(ld), _dp(gd))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    if per_block:
+        return float(om[0]), g, ld, gd
+    return float(om[0]), g
+
+
+def omega_only(p: Params, phi, eps_extra=None) -> float:
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    om = np.zeros(1)
+    rc = lib().orc_omega_grad(ctypes.byref(p), _dp(ee), _dp(phi), _dp(om), None, None, None)
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    return float(om[0])
+
+
+def omega_grad_eig(p: Params, phi, eps_extra=None, per_block: bool = False):
+    """Same quantities through the Jacobi eigenvalue route."""
+    N, B = p.L * p.L, 2 * p.n_omega
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    om = np.zeros(1)
+    g = np.zeros(N)
+    ld = np.zeros(B)
+    gd = np.zeros((B, N))
+    lib().orc_omega_grad_eig(ctypes.byref(p), _dp(ee), _dp(phi), _dp(om), _dp(g), _dp(ld), _dp(gd))
+    if per_block:
+        return float(om[0]), g, ld, gd
+    return float(om[0]), g
+
+
+def block(p: Params, phi, n: int, sigma: int, eps_extra=None, full: bool = False):
+    """ln|det A_{n,sigma}|, G_ii (complex) and optionally the full inverse."""
+    N = p.L * p.L
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    ld = np.zeros(1)
+    dre, dim = np.zeros(N), np.zeros(N)
+    fb = np.zeros((N, N, 2)) if full else None
+    rc = lib().orc_block(ctypes.byref(p), _dp(ee), _dp(phi), int(n), int(sigma), _dp(ld),
+                         _dp(dre), _dp(dim), _dp(fb))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    G = None if fb is None else fb[..., 0] + 1j * fb[..., 1]
+    return float(ld[0]), dre + 1j * dim, G
+
+
+def blocks_sample(p: Params, phi, blocks, eps_extra=None):
+    """ld and sigma*Re G_ii for the listed blocks only (OpenMP over blocks)."""
+    N = p.L * p.L
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    bl = np.ascontiguousarray(blocks, dtype=np.int32)
+    ld = np.zeros(len(bl))
+    gd = np.zeros((len(bl), N))
+    rc = lib().orc_blocks_sample(ctypes.byref(p), _dp(ee), _dp(phi), len(bl),
+                                 bl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(ld), _dp(gd))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    return ld, gd
+
+
+def seed_phi(seed: int, N: int) -> np.ndarray:
+    out = np.zeros(N)
+    lib().orc_seed_phi(ctypes.c_uint64(seed), int(N), _dp(out))
+    return out
+
+
+def splitmix64(seed: int, k: int) -> int:
+    return int(lib().orc_splitmix64(ctypes.c_uint64(seed), ctypes.c_uint64(k)))
+
+
+def omega_n(p: Params, n: int) -> float:
+    return float(lib().orc_omega_n(ctypes.byref(p), int(n)))
+
+
+def adam_run(p: Params, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, grad_tol=0.0, max_steps=100,
+             seed=0, phi0=None, eps_extra=None, history: bool = False):
+    """Adam from phi0 (or the seeded start).  Returns (phi, steps, Omega, max|g|)
+    plus, with history, the per-step Omega and max|g| arrays."""
+    N = p.L * p.L
+    phi = seed_phi(seed, N) if phi0 is None else np.array(phi0, dtype=np.float64, copy=True)
+    a = Adam(lr, beta1, beta2, eps, grad_tol, int(max_steps), ctypes.c_uint64(seed).value)
+    oh = np.zeros(max(max_steps, 1)) if history else None
+    gh = np.zeros(max(max_steps, 1)) if history else None
+    steps = ctypes.c_int32(0)
+    om, gm = np.zeros(1), np.zeros(1)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    rc = lib().orc_adam_run(ctypes.byref(p), _dp(ee), ctypes.byref(a), _dp(phi), _dp(oh), _dp(gh),
+                            ctypes.byref(steps), _dp(om), _dp(gm))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    out = (phi, int(steps.value), float(om[0]), float(gm[0]))
+    if history:
+        return out + (oh[: steps.value + 1 if steps.value < max_steps else max_steps], gh[: steps.value + 1 if steps.value < max_steps else max_steps])
+    return out
