@@ -1,0 +1,262 @@
+/*
+ * sca.h -- C ABI of the GB300 (sm_103a) SCA+ADAM library.
+ *
+ * The library evaluates, differentiates and minimises the semiclassical (SCA)
+ * potential of the 2D ionic Hubbard model of Park & Lee, arXiv 2311.04435:
+ *
+ *   Omega(phi) = sum_i phi_i^2 / U  -  2T sum_{n=0}^{n_omega-1} sum_{sigma=+-1}
+ *                ln |det A_{n,sigma}(phi)|,
+ *   A_{n,sigma} = (i omega_n + mu) I - H_sigma(phi),  omega_n = (2n+1) pi T,
+ *   H_sigma(phi) = K + diag(eps_i - sigma phi_i),
+ *
+ * on an L x L periodic square lattice (site i = x*L + y, sublattice sign
+ * s_i = (-1)^(x+y), A <=> s = +1), K the nearest-neighbour hopping -t with
+ * bonds accumulated (L = 2 gives -2t), eps_i = -s_i Delta (Eq. 1: -Delta on A,
+ * +Delta on B) or -s_i Delta/2 with SCA_IONIC_HALF.  (Paper: Eq. 1 for the
+ * Hamiltonian, Sec. II HS line and Eq. 2 for the potential; the factor 2 and
+ * n >= 0 pair each omega_n with -omega_n, whose determinant is the complex
+ * conjugate; the -beta inside the determinant of Eq. 2 is a constant and is
+ * dropped; phi is normalised so that the stationary point is the Hartree-Fock
+ * gap phi_i = U m_i / 2.)
+ *
+ * Gradient: dOmega/dphi_i = 2 phi_i / U - 2T sum_{n,sigma} sigma Re G_{n sigma, ii},
+ * G = A^{-1}.  Minimisation: Adam (Sec. II: "ADAM optimizer based on the
+ * PyTorch library"; Kingma & Ba 2014) with bias correction and PyTorch's
+ * arithmetic order.
+ *
+ * Conventions for every call:
+ *  - Every function returns an sca_status; none aborts.  On failure,
+ *    sca_last_error() returns a message for the calling thread.
+ *  - The caller owns every pointer it passes; the library copies host arrays
+ *    in and out before returning.  The context owns all device workspace.
+ *  - "host" arrays are ordinary CPU memory; "_dev" arrays are device pointers
+ *    (cudaMalloc / torch CUDA tensors) on the context's device.
+ *  - Arrays of N = L*L sites are float64 in site order i = x*L + y.
+ *  - A context is not thread-safe; use one per thread.  A server is safe for
+ *    concurrent sca_submit / sca_poll from several threads.
+ *  - Blocks are numbered b = 2n + s with s = 0 for sigma = +1 (up) and s = 1
+ *    for sigma = -1 (down).
+ */
+#ifndef SCA_GB300_H
+#define SCA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sca_ctx sca_ctx;
+typedef struct sca_server sca_server;
+
+typedef enum {
+  SCA_OK = 0,
+  SCA_EINVAL = 1,      /* invalid argument (parameters, sizes, NULL pointers) */
+  SCA_ENOMEM = 2,      /* device or host allocation failed */
+  SCA_EBUDGET = 3,     /* request does not fit the server's HBM budget */
+  SCA_ECUDA = 4,       /* a CUDA runtime call failed (message has the CUDA error) */
+  SCA_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
+  SCA_EPENDING = 6,    /* request not finished yet (sca_poll) */
+  SCA_ENONFINITE = 7,  /* Omega or the gradient became NaN/Inf, or a block was singular */
+  SCA_ENOTFOUND = 8,   /* unknown request id */
+  SCA_ENOSTATE = 9     /* call order: e.g. sca_adam_step before sca_adam_init */
+} sca_status;
+
+/* Arithmetic of the dense contractions.  FP64: everything in float64.
+ * FP32: blocks stored as complex64, CUDA-core float32 contractions.
+ * 3XTF32: complex64 blocks, contractions on tcgen05 tensor cores in split
+ * TF32 (hi*hi + hi*lo + lo*hi) with float32 accumulation.
+ * For the three reduced-precision modes ln|u_kk| is accumulated in float64
+ * and every diagonal G_ii gets one float64 refinement step
+ * (G_ii <- 2 X_ii - (X A X^T)_ii with the sparse A). */
+typedef enum {
+  SCA_PREC_FP64 = 0,
+  SCA_PREC_FP32 = 1,
+  SCA_PREC_3XTF32 = 2,
+  SCA_PREC_BF16X3 = 3  /* reserved; sca_create returns SCA_EINVAL */
+} sca_prec;
+
+typedef enum {
+  SCA_IONIC_PAPER = 0, /* eps_i = -s_i * Delta (Eq. 1) */
+  SCA_IONIC_HALF = 1   /* eps_i = -s_i * Delta / 2 */
+} sca_ionic;
+
+/* Physical parameters.  L even, 2 <= L <= 64; 1 <= n_omega <= 16384; U > 0; T > 0;
+ * t, Delta, mu finite. */
+typedef struct {
+  int32_t L, n_omega, prec, ionic;
+  double t, U, delta, T, mu;
+} sca_params;
+
+/* Adam settings.  lr > 0, 0 <= beta1, beta2 < 1, eps > 0.  grad_tol and
+ * max_steps are used by sca_solve and the server (stop when max|g| < grad_tol
+ * or after max_steps updates).  seed selects the SplitMix64 start field
+ * phi0_i = top53(splitmix64(seed, i)) * 2^-53 - 1/2 when no phi0 is given. */
+typedef struct {
+  double lr, beta1, beta2, eps, grad_tol;
+  int32_t max_steps;
+  uint64_t seed;
+} sca_adam;
+
+/* ----------------------------------------------------------- contexts ---- */
+
+/* Creates a context for one parameter set on the current CUDA device and
+ * allocates its device workspace (all 2*n_omega blocks resident unless the
+ * environment variable SCA_MAX_BLOCKS_RESIDENT caps the chunk size).
+ * Errors: SCA_EINVAL (bad parameters, out != NULL required), SCA_ENOMEM,
+ * SCA_ECUDA. */
+sca_status sca_create(const sca_params* params, sca_ctx** out);
+
+/* Frees the context and its workspace.  NULL is ignored. */
+void sca_destroy(sca_ctx* ctx);
+
+/* Bytes of device memory a context with these parameters allocates. */
+sca_status sca_workspace_bytes(const sca_params* params, uint64_t* bytes);
+
+/* Adds a per-site energy eps_extra[i] (N host doubles) to H_sigma, e.g. the
+ * random on-site potential of the disordered model (Sec. IV).  NULL clears
+ * it.  Errors: SCA_EINVAL, SCA_ECUDA. */
+sca_status sca_set_site_energy(sca_ctx* ctx, const double* eps_extra_host);
+
+/* Omega(phi) for a host field phi (N doubles).  Runs the blocked pivoted LU
+ * of every block (Eq. 2; no inverse).  Errors: SCA_EINVAL, SCA_ENONFINITE,
+ * SCA_ECUDA. */
+sca_status sca_potential(sca_ctx* ctx, const double* phi_host, double* omega);
+
+/* Omega(phi) and its gradient (grad: N host doubles).  Runs the blocked
+ * Gauss-Jordan inversion of every block, whose pivots are those of the LU
+ * (same ln|det|) and whose result is G = A^{-1}.  Errors as sca_potential. */
+sca_status sca_grad(sca_ctx* ctx, const double* phi_host, double* omega, double* grad);
+
+/* Device-pointer variants.  d_phi: N doubles; d_omega: 1 double; d_grad: N
+ * doubles; stream: a cudaStream_t (NULL = legacy default stream).  They
+ * enqueue the work on `stream` and return without synchronising; Omega is
+ * written by a kernel.  A non-finite result is not reported here (check the
+ * outputs); launch errors return SCA_ECUDA. */
+sca_status sca_potential_dev(sca_ctx* ctx, const double* d_phi, double* d_omega, void* stream);
+sca_status sca_grad_dev(sca_ctx* ctx, const double* d_phi, double* d_omega, double* d_grad,
+                        void* stream);
+
+/* Autograd split (device pointers, asynchronous on `stream`).
+ * sca_forward_dev: Omega(phi) through the blocked Gauss-Jordan inversion of every block; the
+ * inverses stay resident in the context's workspace.
+ * sca_backward_dev: the adjoint stage from those resident inverses: the diagonal of
+ * G = A^{-1} (refined in float64 for the reduced precisions) reduced into
+ * d_grad = dOmega/dphi.  It must follow a sca_forward_dev with the same d_phi contents and no
+ * other call on the context in between; it returns SCA_ENOSTATE otherwise, or when the
+ * workspace is chunked (not every block resident). */
+sca_status sca_forward_dev(sca_ctx* ctx, const double* d_phi, double* d_omega, void* stream);
+sca_status sca_backward_dev(sca_ctx* ctx, const double* d_phi, double* d_grad, void* stream);
+
+/* Per-block diagnostics for testing each step of the path (host outputs):
+ * ld[b] = ln|det A_b| (2*n_omega doubles) and, if gdiag != NULL,
+ * gdiag[b*N + i] = sigma_b * Re G_{b,ii} (refined as for sca_grad). */
+sca_status sca_blocks(sca_ctx* ctx, const double* phi_host, double* ld, double* gdiag);
+
+/* Writes the assembled blocks A_b (before factorisation) for b in
+ * [b0, b0+count) as interleaved complex128, row-major N x N each, into host
+ * memory out (count*N*N*2 doubles).  For testing the assembly step. */
+sca_status sca_debug_assemble(sca_ctx* ctx, const double* phi_host, int32_t b0, int32_t count,
+                              double* out);
+
+/* -------------------------------------------------------------- Adam ---- */
+
+/* Starts an Adam run: phi <- phi0 (N host doubles) or the SplitMix64 field
+ * of adam->seed when phi0 == NULL; moments m = v = 0; step counter 0.  phi,
+ * m and v stay resident on the device.  Errors: SCA_EINVAL, SCA_ECUDA. */
+sca_status sca_adam_init(sca_ctx* ctx, const sca_adam* adam, const double* phi0_host);
+
+/* Applies nsteps >= 1 Adam updates.  Each update evaluates Omega and the
+ * gradient at the current phi, then moves phi.  *omega and *gmax (may be
+ * NULL) receive Omega and max|g| at the phi of the last update's gradient.
+ * Errors: SCA_ENOSTATE (no sca_adam_init), SCA_ENONFINITE, SCA_ECUDA. */
+sca_status sca_adam_step(sca_ctx* ctx, int32_t nsteps, double* omega, double* gmax);
+
+/* Copies the current phi (N doubles) to host memory. */
+sca_status sca_get_phi(sca_ctx* ctx, double* phi_out);
+
+/* Copies phi, m, v (N doubles each, any may be NULL) and the step count. */
+sca_status sca_get_state(sca_ctx* ctx, double* phi, double* m, double* v, int32_t* step);
+
+/* Restores phi, m, v and the step count (checkpoint resume).  The run then
+ * continues bit-identically to one that was never interrupted. */
+sca_status sca_set_state(sca_ctx* ctx, const sca_adam* adam, const double* phi, const double* m,
+                         const double* v, int32_t step);
+
+/* One-shot minimisation: creates a context, runs Adam from phi0 (NULL =
+ * seeded) until max|g| < adam->grad_tol or adam->max_steps updates, and
+ * returns the final phi (N doubles, may be NULL), Omega and max|g| at the
+ * final phi and the number of updates applied. */
+sca_status sca_solve(const sca_params* params, const sca_adam* adam, const double* phi0_host,
+                     double* phi_out, double* omega, int32_t* steps, double* gmax);
+
+/* ------------------------------------------------------------ serving ---- */
+
+/* Creates a serving loop on the current device with an HBM admission budget
+ * (bytes of workspace that admitted requests may hold at once) and at most
+ * max_slots requests in flight.  A host thread admits queued requests as
+ * slots and budget free up and advances all admitted requests together:
+ * each round runs one Adam update for every in-flight request (their blocks
+ * overlap on the device), so new requests join while others run
+ * (continuous batching).  Errors: SCA_EINVAL, SCA_ENOMEM, SCA_ECUDA. */
+sca_status sca_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, sca_server** out);
+
+/* Queues a solve request (parameters and Adam settings are copied; phi0 is
+ * the seeded field of adam->seed).  *req_id receives its id.  Errors:
+ * SCA_EINVAL, SCA_EBUDGET (the request alone exceeds the budget). */
+sca_status sca_submit(sca_server* srv, const sca_params* params, const sca_adam* adam,
+                      uint64_t* req_id);
+
+/* Result of a request: SCA_EPENDING while queued or running; SCA_OK with phi
+ * (N doubles, may be NULL), Omega, updates applied and max|g| once done; the
+ * request's own error status if it failed; SCA_ENOTFOUND for unknown ids.
+ * A finished request stays pollable until the server is destroyed. */
+sca_status sca_poll(sca_server* srv, uint64_t req_id, double* phi_out, double* omega,
+                    int32_t* steps, double* gmax);
+
+/* Per-request timing in seconds since server creation: arrival (submit),
+ * admission, first update, completion (negative while not reached). */
+sca_status sca_request_times(sca_server* srv, uint64_t req_id, double* submit_s, double* admit_s,
+                             double* start_s, double* finish_s);
+
+/* Stops the loop (in-flight requests are abandoned) and frees everything. */
+void sca_server_destroy(sca_server* srv);
+
+/* ------------------------------------------------------------ streams ---- */
+
+/* Makes every later call on this context enqueue on `stream` (a cudaStream_t; NULL
+ * restores the context's own stream).  The host-buffer calls still synchronise that
+ * stream before returning. */
+sca_status sca_set_stream(sca_ctx* ctx, void* stream);
+
+/* Per-kernel timing.  While enabled, every launch of the context is bracketed by CUDA
+ * events on the stream it is launched on, and the elapsed times are accumulated per kernel
+ * kind when the calling API function synchronises.  Kinds: 0 assemble, 1 panel, 2 swap,
+ * 3 trinv, 4 prep, 5 update (rank-nb contraction), 6 refine (adjoint diag(G)),
+ * 7 reduce (+Adam).  Enabling resets the counters.  Timing adds a small host overhead per
+ * launch; keep it off when measuring throughput. */
+sca_status sca_profile_enable(sca_ctx* ctx, int32_t enable);
+sca_status sca_profile_read(sca_ctx* ctx, int32_t kind, double* total_ms, uint64_t* launches);
+
+/* Algorithmic floating-point operations of one gradient evaluation (all blocks, real flops,
+ * complex multiply-add = 8): 8 N^3 per block for the Gauss-Jordan inversion. */
+double sca_flops_per_grad(const sca_params* params);
+
+/* ------------------------------------------------------------------ misc -- */
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* sca_last_error(void);
+
+/* Library version string. */
+const char* sca_version(void);
+
+/* Number of kernels this process has launched through the library (all
+ * contexts and servers).  For launch accounting. */
+uint64_t sca_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCA_GB300_H */

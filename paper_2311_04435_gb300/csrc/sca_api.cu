@@ -1,0 +1,638 @@
+// C ABI of the SCA+ADAM library: parameter validation, workspace planning, contexts, the
+// Adam driver and the one-shot solver.  All arithmetic runs in the kernels of sca_core.cu
+// and sca_tc.cu; this file only moves data and sequences launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sca_internal.h"
+
+namespace sca {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+thread_local std::string t_err;
+}
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+sca_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
+  return SCA_ECUDA;
+}
+
+static sca_status validate(const sca_params* p) {
+  if (!p) { set_error("params is NULL"); return SCA_EINVAL; }
+  if (p->L < 2 || p->L > 64 || (p->L & 1)) {
+    set_error("L must be even with 2 <= L <= 64");
+    return SCA_EINVAL;
+  }
+  if (p->n_omega < 1 || p->n_omega > 16384) { set_error("n_omega must be in [1, 16384]"); return SCA_EINVAL; }
+  if (!(p->U > 0) || !std::isfinite(p->U)) { set_error("U must be finite and > 0"); return SCA_EINVAL; }
+  if (!(p->T > 0) || !std::isfinite(p->T)) { set_error("T must be finite and > 0"); return SCA_EINVAL; }
+  if (!std::isfinite(p->t) || !std::isfinite(p->delta) || !std::isfinite(p->mu)) {
+    set_error("t, delta and mu must be finite");
+    return SCA_EINVAL;
+  }
+  if (p->prec < SCA_PREC_FP64 || p->prec > SCA_PREC_3XTF32) {
+    set_error("prec must be SCA_PREC_FP64, SCA_PREC_FP32 or SCA_PREC_3XTF32");
+    return SCA_EINVAL;
+  }
+  if (p->ionic != SCA_IONIC_PAPER && p->ionic != SCA_IONIC_HALF) {
+    set_error("ionic must be SCA_IONIC_PAPER or SCA_IONIC_HALF");
+    return SCA_EINVAL;
+  }
+  return SCA_OK;
+}
+
+static sca_status validate_adam(const sca_adam* a) {
+  if (!a) { set_error("adam is NULL"); return SCA_EINVAL; }
+  if (!(a->lr > 0) || !std::isfinite(a->lr) || !(a->beta1 >= 0 && a->beta1 < 1) ||
+      !(a->beta2 >= 0 && a->beta2 < 1) || !(a->eps > 0) || !(a->grad_tol >= 0) ||
+      a->max_steps < 0) {
+    set_error("invalid Adam settings (lr > 0, 0 <= beta < 1, eps > 0, grad_tol >= 0, max_steps >= 0)");
+    return SCA_EINVAL;
+  }
+  return SCA_OK;
+}
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+sca_status plan(const sca_params& p, Engine& e) {
+  e.p = p;
+  e.L = p.L;
+  e.N = p.L * p.L;
+  e.B = 2 * p.n_omega;
+  e.fp64 = (p.prec == SCA_PREC_FP64);
+  e.refine = !e.fp64;
+  e.delta_eff = (p.ionic == SCA_IONIC_HALF) ? 0.5 * p.delta : p.delta;
+  // tcgen05 path for blocks of at least 128 rows; smaller blocks use CUDA cores.
+  e.tc = (p.prec == SCA_PREC_3XTF32) && e.N >= 128 && tc_supported();
+  int nb = e.fp64 ? 32 : (e.tc ? 64 : 32);
+  if (const char* v = std::getenv("SCA_NB")) {
+    const int x = std::atoi(v);
+    if (x >= 8 && x <= 128 && (x % 8) == 0) nb = x;
+  }
+  if (e.tc) nb = std::max(32, nb / 32 * 32);
+  e.nb = std::min(nb, e.tc ? nb : e.N);
+  e.ldm = (int)round_up((size_t)e.N, 32);
+  e.chunk = e.B;
+  if (const char* v = std::getenv("SCA_MAX_BLOCKS_RESIDENT")) {
+    const int x = std::atoi(v);
+    if (x >= 1) e.chunk = std::min(e.B, x);
+  }
+  const size_t S = e.fp64 ? 8 : 4;
+  e.plane_stride = (size_t)e.N * e.ldm;
+  e.mat_stride = 2 * e.plane_stride;
+  e.fw_plane = (size_t)e.N * e.nb;
+  e.fw_mat = (e.tc ? 4 : 2) * e.fw_plane;
+  const size_t C = S;  // compute type of the small kernels = storage type
+  size_t bytes = 0;
+  bytes += (size_t)e.chunk * e.mat_stride * S;           // blocks
+  bytes += 2 * (size_t)e.chunk * e.fw_mat * S;            // F, W
+  bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
+  bytes += 2 * (size_t)e.chunk * e.N * sizeof(int);       // piv, perm
+  bytes += (size_t)e.B * sizeof(double) * (1 + e.N);      // ld, gd
+  bytes += (size_t)e.N * sizeof(double) * 7 + 256;        // eps, phi, m, v, g, in, misc
+  e.bytes = bytes;
+  return SCA_OK;
+}
+
+template <typename T>
+static sca_status dev_alloc(T** p, size_t bytes, Engine& e, const char* what) {
+  cudaError_t err = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    release(e);
+    set_error(std::string("cudaMalloc failed for ") + what + " (" + std::to_string(bytes) +
+              " bytes): " + cudaGetErrorString(err));
+    return SCA_ENOMEM;
+  }
+  return SCA_OK;
+}
+
+sca_status allocate(Engine& e) {
+  const size_t S = e.fp64 ? 8 : 4;
+  sca_status st;
+#define SCA_ALLOC(ptr, bytes, what) \
+  if ((st = dev_alloc(&(ptr), (bytes), e, what)) != SCA_OK) return st;
+  SCA_ALLOC(e.M, (size_t)e.chunk * e.mat_stride * S, "blocks");
+  SCA_ALLOC(e.F, (size_t)e.chunk * e.fw_mat * S, "F");
+  SCA_ALLOC(e.W, (size_t)e.chunk * e.fw_mat * S, "W");
+  SCA_ALLOC(e.Tinv, (size_t)e.chunk * 2 * e.nb * e.nb * 2 * S, "Tinv");
+  SCA_ALLOC(e.piv, (size_t)e.chunk * e.N * sizeof(int), "piv");
+  SCA_ALLOC(e.perm, (size_t)e.chunk * e.N * sizeof(int), "perm");
+  SCA_ALLOC(e.flags, 16, "flags");
+  SCA_ALLOC(e.ld, (size_t)e.B * sizeof(double), "ld");
+  SCA_ALLOC(e.gd, (size_t)e.B * e.N * sizeof(double), "gd");
+  SCA_ALLOC(e.d_phi, (size_t)e.N * sizeof(double), "phi");
+  SCA_ALLOC(e.d_m, (size_t)e.N * sizeof(double), "m");
+  SCA_ALLOC(e.d_v, (size_t)e.N * sizeof(double), "v");
+  SCA_ALLOC(e.d_g, (size_t)e.N * sizeof(double), "g");
+  SCA_ALLOC(e.d_status, 8 * sizeof(double), "status");
+  SCA_ALLOC(e.d_omega, 8 * sizeof(double), "omega");
+#undef SCA_ALLOC
+  cudaError_t err = cudaMallocHost((void**)&e.h_status, 8 * sizeof(double));
+  if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMallocHost"); }
+  err = cudaMemset(e.flags, 0, 16);
+  if (err == cudaSuccess) err = cudaMemset(e.d_status, 0, 8 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemset(e.d_m, 0, (size_t)e.N * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemset(e.d_v, 0, (size_t)e.N * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemset(e.F, 0, (size_t)e.chunk * e.fw_mat * S);
+  if (err == cudaSuccess) err = cudaMemset(e.W, 0, (size_t)e.chunk * e.fw_mat * S);
+  if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
+  if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
+  return SCA_OK;
+}
+
+void prof_begin(Engine& e, int kind, cudaStream_t s) {
+  Profiler* p = e.prof;
+  if (!p || !p->on) return;
+  if (p->used + 2 > p->npool) {  // grow the event pool
+    const int n = std::max(64, 2 * p->npool);
+    cudaEvent_t* np = (cudaEvent_t*)std::realloc(p->pool, sizeof(cudaEvent_t) * n);
+    if (!np) return;
+    p->pool = np;
+    for (int k = p->npool; k < n; ++k) cudaEventCreate(&p->pool[k]);
+    p->npool = n;
+  }
+  if (p->nrec + 1 > p->cap) {
+    const int n = std::max(32, 2 * p->cap);
+    Profiler::Rec* nr = (Profiler::Rec*)std::realloc(p->recs, sizeof(Profiler::Rec) * n);
+    if (!nr) return;
+    p->recs = nr;
+    p->cap = n;
+  }
+  Profiler::Rec& r = p->recs[p->nrec++];
+  r.kind = kind;
+  r.a = p->pool[p->used++];
+  r.b = p->pool[p->used++];
+  cudaEventRecord(r.a, s);
+}
+
+void prof_end(Engine& e, int kind, cudaStream_t s) {
+  Profiler* p = e.prof;
+  if (!p || !p->on || p->nrec == 0) return;
+  Profiler::Rec& r = p->recs[p->nrec - 1];
+  if (r.kind == kind) cudaEventRecord(r.b, s);
+}
+
+void prof_collect(Engine& e) {
+  Profiler* p = e.prof;
+  if (!p) return;
+  for (int k = 0; k < p->nrec; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->recs[k].a, p->recs[k].b) == cudaSuccess) {
+      p->ms[p->recs[k].kind] += ms;
+      p->n[p->recs[k].kind] += 1;
+    }
+  }
+  (void)cudaGetLastError();
+  p->nrec = 0;
+  p->used = 0;
+}
+
+void prof_free(Engine& e) {
+  Profiler* p = e.prof;
+  if (!p) return;
+  for (int k = 0; k < p->npool; ++k) cudaEventDestroy(p->pool[k]);
+  std::free(p->pool);
+  std::free(p->recs);
+  delete p;
+  e.prof = nullptr;
+}
+
+void release(Engine& e) {
+  prof_free(e);
+  tc_release(e);
+  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.piv, e.perm, e.flags, e.ld, e.gd, e.eps_extra,
+                  e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (e.h_status) cudaFreeHost(e.h_status);
+  e.M = e.F = e.W = e.Tinv = nullptr;
+  e.piv = e.perm = e.flags = nullptr;
+  e.ld = e.gd = e.eps_extra = e.d_phi = e.d_m = e.d_v = e.d_g = e.d_status = e.d_omega = nullptr;
+  e.h_status = nullptr;
+}
+
+}  // namespace sca
+
+using namespace sca;
+
+struct sca_ctx {
+  Engine e;
+  cudaStream_t own = nullptr;     // the context's stream
+  cudaStream_t stream = nullptr;  // stream in use (own or the caller's, sca_set_stream)
+  double* d_in = nullptr;  // N doubles: host-supplied phi
+  sca_adam adam{};
+  bool adam_ready = false;
+  int32_t step = 0;
+  bool kept = false;  // inverses of every block resident from sca_forward_dev
+};
+
+namespace {
+
+sca_status sync_status(sca_ctx* c, cudaStream_t s) {
+  cudaError_t err = cudaMemcpyAsync(c->e.h_status, c->e.d_status, 8 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_fail(err, "status read-back");
+  prof_collect(c->e);
+  return SCA_OK;
+}
+
+sca_status check_finite(sca_ctx* c) {
+  if (c->e.h_status[4] != 0.0) {
+    set_error("non-finite Omega or gradient, or a singular block");
+    return SCA_ENONFINITE;
+  }
+  return SCA_OK;
+}
+
+sca_status upload_phi(sca_ctx* c, const double* phi_host) {
+  if (!phi_host) { set_error("phi is NULL"); return SCA_EINVAL; }
+  cudaError_t err = cudaMemcpyAsync(c->d_in, phi_host, sizeof(double) * c->e.N,
+                                    cudaMemcpyHostToDevice, c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "phi upload");
+  return SCA_OK;
+}
+
+AdamStep adam_step_args(const sca_adam& a, int32_t step) {
+  AdamStep as;
+  const double bc1 = 1.0 - std::pow(a.beta1, (double)step);
+  const double bc2 = 1.0 - std::pow(a.beta2, (double)step);
+  as.lr_over_bc1 = a.lr / bc1;
+  as.sqrt_bc2 = std::sqrt(bc2);
+  as.beta1 = a.beta1;
+  as.beta2 = a.beta2;
+  as.eps = a.eps;
+  as.grad_tol = a.grad_tol;
+  return as;
+}
+
+}  // namespace
+
+extern "C" {
+
+sca_status sca_workspace_bytes(const sca_params* params, uint64_t* bytes) {
+  sca_status st = validate(params);
+  if (st != SCA_OK) return st;
+  if (!bytes) { set_error("bytes is NULL"); return SCA_EINVAL; }
+  Engine e;
+  plan(*params, e);
+  *bytes = e.bytes;
+  return SCA_OK;
+}
+
+sca_status sca_create(const sca_params* params, sca_ctx** out) {
+  sca_status st = validate(params);
+  if (st != SCA_OK) return st;
+  if (!out) { set_error("out is NULL"); return SCA_EINVAL; }
+  *out = nullptr;
+  sca_ctx* c = new (std::nothrow) sca_ctx();
+  if (!c) { set_error("host allocation failed"); return SCA_ENOMEM; }
+  plan(*params, c->e);
+  if ((st = allocate(c->e)) != SCA_OK) { delete c; return st; }
+  cudaError_t err = cudaMalloc((void**)&c->d_in, sizeof(double) * c->e.N);
+  if (err != cudaSuccess) { release(c->e); delete c; return cuda_fail(err, "cudaMalloc phi"); }
+  err = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+  c->stream = c->own;
+  if (err != cudaSuccess) {
+    cudaFree(c->d_in);
+    release(c->e);
+    delete c;
+    return cuda_fail(err, "cudaStreamCreate");
+  }
+  *out = c;
+  return SCA_OK;
+}
+
+void sca_destroy(sca_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own) cudaStreamDestroy(c->own);
+  if (c->d_in) cudaFree(c->d_in);
+  release(c->e);
+  delete c;
+}
+
+sca_status sca_set_site_energy(sca_ctx* c, const double* eps_extra_host) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  if (!eps_extra_host) {
+    if (c->e.eps_extra) { cudaStreamSynchronize(c->stream); cudaFree(c->e.eps_extra); }
+    c->e.eps_extra = nullptr;
+    return SCA_OK;
+  }
+  cudaError_t err = cudaSuccess;
+  if (!c->e.eps_extra) err = cudaMalloc((void**)&c->e.eps_extra, sizeof(double) * c->e.N);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(c->e.eps_extra, eps_extra_host, sizeof(double) * c->e.N, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return cuda_fail(err, "site energy upload");
+  return SCA_OK;
+}
+
+sca_status sca_forward_dev(sca_ctx* c, const double* d_phi, double* d_omega, void* stream) {
+  if (!c || !d_phi || !d_omega) { set_error("NULL argument"); return SCA_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->kept = false;
+  sca_status st = run_blocks(c->e, d_phi, true, s, /*refine_stage=*/false);
+  if (st != SCA_OK) return st;
+  if ((st = run_reduce(c->e, d_phi, d_omega, nullptr, nullptr, s)) != SCA_OK) return st;
+  c->kept = (c->e.chunk == c->e.B);
+  return SCA_OK;
+}
+
+sca_status sca_backward_dev(sca_ctx* c, const double* d_phi, double* d_grad, void* stream) {
+  if (!c || !d_phi || !d_grad) { set_error("NULL argument"); return SCA_EINVAL; }
+  if (!c->kept) {
+    set_error("sca_backward_dev needs the resident inverses of a preceding sca_forward_dev");
+    return SCA_ENOSTATE;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->kept = false;
+  sca_status st = run_refine_resident(c->e, d_phi, s);
+  if (st != SCA_OK) return st;
+  return run_reduce(c->e, d_phi, c->e.d_omega, d_grad, nullptr, s);
+}
+
+sca_status sca_potential_dev(sca_ctx* c, const double* d_phi, double* d_omega, void* stream) {
+  if (!c || !d_phi || !d_omega) { set_error("NULL argument"); return SCA_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->kept = false;
+  sca_status st = run_blocks(c->e, d_phi, false, s);
+  if (st != SCA_OK) return st;
+  return run_reduce(c->e, d_phi, d_omega, nullptr, nullptr, s);
+}
+
+sca_status sca_grad_dev(sca_ctx* c, const double* d_phi, double* d_omega, double* d_grad,
+                        void* stream) {
+  if (!c || !d_phi || !d_omega || !d_grad) { set_error("NULL argument"); return SCA_EINVAL; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->kept = false;
+  sca_status st = run_blocks(c->e, d_phi, true, s);
+  if (st != SCA_OK) return st;
+  return run_reduce(c->e, d_phi, d_omega, d_grad, nullptr, s);
+}
+
+sca_status sca_potential(sca_ctx* c, const double* phi_host, double* omega) {
+  if (!c || !omega) { set_error("NULL argument"); return SCA_EINVAL; }
+  sca_status st = upload_phi(c, phi_host);
+  if (st != SCA_OK) return st;
+  if ((st = sca_potential_dev(c, c->d_in, c->e.d_omega, c->stream)) != SCA_OK) return st;
+  if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+  *omega = c->e.h_status[0];
+  return check_finite(c);
+}
+
+sca_status sca_grad(sca_ctx* c, const double* phi_host, double* omega, double* grad) {
+  if (!c || !omega || !grad) { set_error("NULL argument"); return SCA_EINVAL; }
+  sca_status st = upload_phi(c, phi_host);
+  if (st != SCA_OK) return st;
+  if ((st = sca_grad_dev(c, c->d_in, c->e.d_omega, c->e.d_g, c->stream)) != SCA_OK) return st;
+  cudaError_t err = cudaMemcpyAsync(grad, c->e.d_g, sizeof(double) * c->e.N,
+                                    cudaMemcpyDeviceToHost, c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "grad read-back");
+  if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+  *omega = c->e.h_status[0];
+  return check_finite(c);
+}
+
+sca_status sca_blocks(sca_ctx* c, const double* phi_host, double* ld, double* gdiag) {
+  if (!c || !ld) { set_error("NULL argument"); return SCA_EINVAL; }
+  sca_status st = upload_phi(c, phi_host);
+  if (st != SCA_OK) return st;
+  const bool g = gdiag != nullptr;
+  c->kept = false;
+  if ((st = run_blocks(c->e, c->d_in, g, c->stream)) != SCA_OK) return st;
+  if ((st = run_reduce(c->e, c->d_in, c->e.d_omega, g ? c->e.d_g : nullptr, nullptr,
+                       c->stream)) != SCA_OK)
+    return st;
+  cudaError_t err = cudaMemcpyAsync(ld, c->e.ld, sizeof(double) * c->e.B, cudaMemcpyDeviceToHost,
+                                    c->stream);
+  if (err == cudaSuccess && g)
+    err = cudaMemcpyAsync(gdiag, c->e.gd, sizeof(double) * c->e.B * c->e.N,
+                          cudaMemcpyDeviceToHost, c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "block read-back");
+  if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+  return check_finite(c);
+}
+
+sca_status sca_debug_assemble(sca_ctx* c, const double* phi_host, int32_t b0, int32_t count,
+                              double* out) {
+  if (!c || !out) { set_error("NULL argument"); return SCA_EINVAL; }
+  if (b0 < 0 || count < 1 || b0 + count > c->e.B || count > c->e.chunk) {
+    set_error("block range out of bounds");
+    return SCA_EINVAL;
+  }
+  sca_status st = upload_phi(c, phi_host);
+  if (st != SCA_OK) return st;
+  c->kept = false;
+  if ((st = run_assemble_only(c->e, c->d_in, b0, count, c->stream)) != SCA_OK) return st;
+  const int N = c->e.N;
+  const size_t S = c->e.fp64 ? 8 : 4;
+  const size_t bytes = (size_t)count * c->e.mat_stride * S;
+  char* h = (char*)std::malloc(bytes);
+  if (!h) { set_error("host allocation failed"); return SCA_ENOMEM; }
+  cudaError_t err = cudaMemcpyAsync(h, c->e.M, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) { std::free(h); return cuda_fail(err, "assemble read-back"); }
+  for (int m = 0; m < count; ++m)
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        const size_t o = (size_t)m * c->e.mat_stride + (size_t)i * c->e.ldm + j;
+        const size_t q = o + c->e.plane_stride;
+        double vr, vi;
+        if (c->e.fp64) { vr = ((double*)h)[o]; vi = ((double*)h)[q]; }
+        else { vr = ((float*)h)[o]; vi = ((float*)h)[q]; }
+        out[2 * (((size_t)m * N + i) * N + j)] = vr;
+        out[2 * (((size_t)m * N + i) * N + j) + 1] = vi;
+      }
+  std::free(h);
+  return SCA_OK;
+}
+
+sca_status sca_adam_init(sca_ctx* c, const sca_adam* adam, const double* phi0_host) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  sca_status st = validate_adam(adam);
+  if (st != SCA_OK) return st;
+  cudaError_t err;
+  if (phi0_host) {
+    err = cudaMemcpyAsync(c->e.d_phi, phi0_host, sizeof(double) * c->e.N, cudaMemcpyHostToDevice,
+                          c->stream);
+    if (err != cudaSuccess) return cuda_fail(err, "phi0 upload");
+  } else if ((st = run_seed_phi(c->e.d_phi, c->e.N, adam->seed, c->stream)) != SCA_OK) {
+    return st;
+  }
+  err = cudaMemsetAsync(c->e.d_m, 0, sizeof(double) * c->e.N, c->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->e.d_v, 0, sizeof(double) * c->e.N, c->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->e.d_status, 0, 8 * sizeof(double), c->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->e.flags, 0, 16, c->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "adam init");
+  c->adam = *adam;
+  c->adam_ready = true;
+  c->step = 0;
+  return SCA_OK;
+}
+
+// Enqueues `n` Adam iterations (gradient + gated update) without synchronising.
+static sca_status enqueue_adam(sca_ctx* c, int32_t n) {
+  c->kept = false;
+  for (int32_t k = 0; k < n; ++k) {
+    const AdamStep as = adam_step_args(c->adam, c->step + 1);
+    sca_status st = run_blocks(c->e, c->e.d_phi, true, c->stream);
+    if (st != SCA_OK) return st;
+    if ((st = run_reduce(c->e, c->e.d_phi, c->e.d_omega, nullptr, &as, c->stream)) != SCA_OK)
+      return st;
+    c->step += 1;
+  }
+  return SCA_OK;
+}
+
+sca_status sca_adam_step(sca_ctx* c, int32_t nsteps, double* omega, double* gmax) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  if (!c->adam_ready) { set_error("sca_adam_init has not been called"); return SCA_ENOSTATE; }
+  if (nsteps < 1) { set_error("nsteps must be >= 1"); return SCA_EINVAL; }
+  // Plain Adam: no convergence gate for explicit steps.
+  const double tol = c->adam.grad_tol;
+  c->adam.grad_tol = 0.0;
+  sca_status st = enqueue_adam(c, nsteps);
+  c->adam.grad_tol = tol;
+  if (st != SCA_OK) return st;
+  if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+  if (omega) *omega = c->e.h_status[0];
+  if (gmax) *gmax = c->e.h_status[1];
+  return check_finite(c);
+}
+
+sca_status sca_get_phi(sca_ctx* c, double* phi_out) {
+  if (!c || !phi_out) { set_error("NULL argument"); return SCA_EINVAL; }
+  cudaError_t err = cudaMemcpyAsync(phi_out, c->e.d_phi, sizeof(double) * c->e.N,
+                                    cudaMemcpyDeviceToHost, c->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "phi read-back");
+  return SCA_OK;
+}
+
+sca_status sca_get_state(sca_ctx* c, double* phi, double* m, double* v, int32_t* step) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  const size_t nb = sizeof(double) * c->e.N;
+  cudaError_t err = cudaSuccess;
+  if (phi) err = cudaMemcpyAsync(phi, c->e.d_phi, nb, cudaMemcpyDeviceToHost, c->stream);
+  if (err == cudaSuccess && m) err = cudaMemcpyAsync(m, c->e.d_m, nb, cudaMemcpyDeviceToHost, c->stream);
+  if (err == cudaSuccess && v) err = cudaMemcpyAsync(v, c->e.d_v, nb, cudaMemcpyDeviceToHost, c->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "state read-back");
+  if (step) *step = c->step;
+  return SCA_OK;
+}
+
+sca_status sca_set_state(sca_ctx* c, const sca_adam* adam, const double* phi, const double* m,
+                         const double* v, int32_t step) {
+  if (!c || !phi || !m || !v) { set_error("NULL argument"); return SCA_EINVAL; }
+  sca_status st = validate_adam(adam);
+  if (st != SCA_OK) return st;
+  if (step < 0) { set_error("step must be >= 0"); return SCA_EINVAL; }
+  const size_t nb = sizeof(double) * c->e.N;
+  cudaError_t err = cudaMemcpyAsync(c->e.d_phi, phi, nb, cudaMemcpyHostToDevice, c->stream);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->e.d_m, m, nb, cudaMemcpyHostToDevice, c->stream);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(c->e.d_v, v, nb, cudaMemcpyHostToDevice, c->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->e.d_status, 0, 8 * sizeof(double), c->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "state upload");
+  c->adam = *adam;
+  c->adam_ready = true;
+  c->step = step;
+  return SCA_OK;
+}
+
+sca_status sca_solve(const sca_params* params, const sca_adam* adam, const double* phi0_host,
+                     double* phi_out, double* omega, int32_t* steps, double* gmax) {
+  sca_status st = validate_adam(adam);
+  if (st != SCA_OK) return st;
+  sca_ctx* c = nullptr;
+  if ((st = sca_create(params, &c)) != SCA_OK) return st;
+  if ((st = sca_adam_init(c, adam, phi0_host)) != SCA_OK) { sca_destroy(c); return st; }
+  // The device gates each update on max|g| >= grad_tol and counts the updates it applied
+  // (status[5]); once converged phi no longer moves, so batches may overshoot safely.
+  const int32_t batch = 16;
+  int32_t launched = 0;
+  bool converged = false;
+  while (launched < adam->max_steps && !converged) {
+    const int32_t n = std::min(batch, adam->max_steps - launched);
+    if ((st = enqueue_adam(c, n)) != SCA_OK) { sca_destroy(c); return st; }
+    launched += n;
+    if ((st = sync_status(c, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
+    if ((st = check_finite(c)) != SCA_OK) { sca_destroy(c); return st; }
+    converged = c->e.h_status[5] < (double)launched;
+  }
+  // Omega and max|g| at the final phi.
+  if (!converged) {
+    if ((st = run_blocks(c->e, c->e.d_phi, true, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
+    if ((st = run_reduce(c->e, c->e.d_phi, c->e.d_omega, c->e.d_g, nullptr, c->stream)) != SCA_OK) {
+      sca_destroy(c);
+      return st;
+    }
+    if ((st = sync_status(c, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
+    if ((st = check_finite(c)) != SCA_OK) { sca_destroy(c); return st; }
+  }
+  if (omega) *omega = c->e.h_status[0];
+  if (gmax) *gmax = c->e.h_status[1];
+  if (steps) *steps = (int32_t)c->e.h_status[5];
+  if (phi_out) st = sca_get_phi(c, phi_out);
+  sca_destroy(c);
+  return st;
+}
+
+sca_status sca_set_stream(sca_ctx* c, void* stream) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  cudaError_t err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "stream switch");
+  c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own;
+  return SCA_OK;
+}
+
+sca_status sca_profile_enable(sca_ctx* c, int32_t enable) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  if (!c->e.prof) {
+    c->e.prof = new (std::nothrow) Profiler();
+    if (!c->e.prof) { set_error("host allocation failed"); return SCA_ENOMEM; }
+  }
+  cudaStreamSynchronize(c->stream);
+  prof_collect(c->e);
+  c->e.prof->on = enable != 0;
+  for (int k = 0; k < kKinds; ++k) { c->e.prof->ms[k] = 0.0; c->e.prof->n[k] = 0; }
+  return SCA_OK;
+}
+
+sca_status sca_profile_read(sca_ctx* c, int32_t kind, double* total_ms, uint64_t* launches) {
+  if (!c || kind < 0 || kind >= kKinds) { set_error("bad context or kernel kind"); return SCA_EINVAL; }
+  cudaError_t err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "profile read");
+  prof_collect(c->e);
+  if (total_ms) *total_ms = c->e.prof ? c->e.prof->ms[kind] : 0.0;
+  if (launches) *launches = c->e.prof ? c->e.prof->n[kind] : 0;
+  return SCA_OK;
+}
+
+double sca_flops_per_grad(const sca_params* p) {
+  if (!p) return 0.0;
+  const double N = (double)p->L * p->L;
+  return 8.0 * N * N * N * 2.0 * p->n_omega;
+}
+
+const char* sca_last_error(void) { return t_err.c_str(); }
+
+const char* sca_version(void) { return "sca-gb300 0.1 (sm_103a)"; }
+
+uint64_t sca_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

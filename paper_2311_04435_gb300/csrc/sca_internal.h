@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include "../../include/sca.h"
+
+namespace sca {
+
+// Counts every kernel launched through the library (sca_kernel_launches()).
+extern std::atomic<uint64_t> g_launches;
+
+// Thread-local error message plumbing.
+void set_error(const std::string& msg);
+sca_status cuda_fail(cudaError_t e, const char* where);
+
+// Device buffers and sizes of one parameter set.  Blocks are stored planar:
+// for block m of a chunk, the real plane is M + m*mat_stride and the
+// imaginary plane follows at + plane_stride; rows have `ldm` elements.
+struct Engine {
+  sca_params p{};
+  int L = 0, N = 0, B = 0;
+  int nb = 0;            // Gauss-Jordan / LU block width
+  int ldm = 0;           // row stride of a block plane (elements)
+  int chunk = 0;         // blocks resident at once
+  bool fp64 = false;     // storage and arithmetic of the blocks
+  bool refine = false;   // FP64 refinement of diag(G)
+  bool tc = false;       // tcgen05 3xTF32 rank-nb update
+  double delta_eff = 0;  // Delta or Delta/2 (ionic convention)
+  size_t plane_stride = 0, mat_stride = 0;  // elements
+  size_t fw_plane = 0, fw_mat = 0;          // F / W panel strides (elements)
+
+  void* M = nullptr;        // chunk blocks
+  void* F = nullptr;        // chunk x 2 planes x N x nb (x2 hi/lo for tc)
+  void* W = nullptr;        // same, W^T
+  void* Tinv = nullptr;     // chunk x 2 x nb x nb complex (compute type)
+  int* piv = nullptr;       // chunk x N
+  int* perm = nullptr;      // chunk x N
+  int* flags = nullptr;     // 1 int: nonfinite / singular
+  double* ld = nullptr;     // B
+  double* gd = nullptr;     // B x N
+  double* eps_extra = nullptr;  // N or null
+  double* d_phi = nullptr;  // N (Adam state)
+  double* d_m = nullptr;
+  double* d_v = nullptr;
+  double* d_g = nullptr;
+  double* d_status = nullptr;   // 8 doubles
+  double* d_omega = nullptr;    // 1 double scratch
+  double* h_status = nullptr;   // pinned 8 doubles
+  void* tmap = nullptr;         // host-side tensor-map storage (tc path)
+  size_t bytes = 0;
+  struct Profiler* prof = nullptr;  // per-kernel event timing (sca_profile_enable)
+};
+
+// Kernel kinds for per-launch timing.
+enum KernelKind { kAssemble = 0, kPanel, kSwap, kTrinv, kPrep, kUpdate, kRefine, kReduce, kKinds };
+
+// Event bracketing of launches while profiling is on (no-ops otherwise).
+struct Profiler {
+  bool on = false;
+  double ms[kKinds] = {};
+  uint64_t n[kKinds] = {};
+  struct Rec { int kind; cudaEvent_t a, b; };
+  Rec* recs = nullptr;
+  int nrec = 0, cap = 0;
+  cudaEvent_t* pool = nullptr;
+  int npool = 0, used = 0;
+};
+void prof_begin(Engine& e, int kind, cudaStream_t s);
+void prof_end(Engine& e, int kind, cudaStream_t s);
+void prof_collect(Engine& e);  // after a synchronisation: accumulate elapsed times
+void prof_free(Engine& e);
+
+// Workspace layout / sizing (no allocation).
+sca_status plan(const sca_params& p, Engine& e);
+sca_status allocate(Engine& e);
+void release(Engine& e);
+
+// Enqueue: evaluate every block for field d_phi; on return (asynchronous),
+// e.ld[b] holds ln|det A_b| and, if want_grad, e.gd[b*N+i] holds
+// sigma_b Re G_{b,ii}.
+sca_status run_blocks(Engine& e, const double* d_phi, bool want_grad, cudaStream_t s,
+                      bool refine_stage = true);
+
+// Gradient stage alone, from the inverses left resident by run_blocks(..., want_grad=true,
+// refine_stage=false) (requires every block resident: chunk == B).
+sca_status run_refine_resident(Engine& e, const double* d_phi, cudaStream_t s);
+
+// Enqueue the reduction of ld / gd into Omega (d_omega) and the gradient
+// (d_grad, may be null).  With adam != null also the Adam update of e.d_phi
+// (step index `step` >= 1).  Writes status[0..7].
+struct AdamStep {
+  double lr_over_bc1, sqrt_bc2, beta1, beta2, eps, grad_tol;
+};
+sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d_grad,
+                      const AdamStep* adam, cudaStream_t s);
+
+// Assembled blocks (for sca_debug_assemble).
+sca_status run_assemble_only(Engine& e, const double* d_phi, int b0, int count, cudaStream_t s);
+
+// Seeded start field on the device.
+sca_status run_seed_phi(double* d_phi, int N, uint64_t seed, cudaStream_t s);
+
+// tcgen05 3xTF32 rank-nb update (sca_tc.cu).
+bool tc_supported();
+sca_status tc_prepare(Engine& e);
+void tc_release(Engine& e);
+sca_status tc_update(Engine& e, int cnt, int k0, int kb, int r0, int c0, bool gj, cudaStream_t s);
+
+}  // namespace sca

@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, step by step.
+
+Tolerances: float64 path <= 1e-10 relative in Omega and the gradient; reduced precisions
+(complex64 blocks, float64 log-det accumulation and float64 refinement of diag(G))
+<= 1e-5 relative in Omega; the refined gradient is checked at 1e-7 of max(1, |g|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_04435_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "fp32", "3xtf32"]
+
+
+def oparams(p: api.Params):
+    return oracle.make_params(p.L, p.n_omega, U=p.U, T=p.T, delta=p.delta, t=p.t, mu=p.mu,
+                              ionic=0 if p.ionic == "paper" else 1)
+
+
+def tol(prec):
+    return dict(om=1e-10, ld=1e-10, g=1e-10) if prec == "fp64" else dict(om=1e-5, ld=2e-6, g=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", [2, 4, 6])
+def test_assemble_matches_oracle(prec, L):
+    p = api.Params(L, 3, U=5.0, T=0.07, delta=0.4, mu=0.2, prec=prec, ionic="half")
+    phi = inputs.random_phi(L, p.N, 1.3)
+    with api.Context(p) as c:
+        A = c.assemble(phi, 0, 2 * p.n_omega)
+    op = oparams(p)
+    for b in range(2 * p.n_omega):
+        n, sg = b // 2, (1 if b % 2 == 0 else -1)
+        H = oracle.hamiltonian(op, phi, sg)
+        ref = (p.mu + 1j * oracle.omega_n(op, n)) * np.eye(p.N) - H
+        if prec == "fp64":
+            assert np.array_equal(A[b], ref)
+        else:
+            assert np.allclose(A[b], ref.astype(np.complex64), rtol=0, atol=0)
+
+
+# sizes spanning several panels and a ragged tail (nb = 32 on CUDA cores, 64 on tensor cores)
+CASES = [
+    (2, 5, 0.0, 0.0),      # accumulated bonds, single tiny panel
+    (4, 16, 0.0, 0.0),     # 16x16 blocks
+    (6, 7, 0.7, 0.1),      # 36: ragged single panel
+    (10, 5, 0.5, 0.0),     # 100: 3 full panels + ragged 4
+    (12, 4, 1.0, -0.2),    # 144: 4.5 panels
+    (14, 3, 0.5, 0.0),     # 196
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L,nw,delta,mu", CASES)
+def test_blocks_logdet_and_diag_match_oracle(prec, L, nw, delta, mu):
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=delta, mu=mu, prec=prec)
+    phi = inputs.random_phi(100 + L, p.N, 1.0)
+    with api.Context(p) as c:
+        ld, gd = c.blocks(phi, grad=True)
+        om_lu = c.potential(phi)
+        om, g = c.grad(phi)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+    scale = max(1.0, np.abs(o_gd).max())
+    assert np.max(np.abs(gd - o_gd)) <= t["g"] * scale
+    assert om == pytest.approx(o_om, rel=t["om"])
+    assert om_lu == pytest.approx(o_om, rel=t["om"])
+    assert np.max(np.abs(g - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_larger_block_20x20_matches_oracle(prec):
+    p = api.Params(20, 2, U=6.0, T=0.1, delta=0.5, prec=prec)
+    phi = inputs.seed_phi(0, p.N)
+    with api.Context(p) as c:
+        ld, gd = c.blocks(phi, grad=True)
+    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, list(range(4)))
+    t = tol(prec)
+    assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_disorder_site_energy_and_half_convention(prec):
+    p = api.Params(6, 6, U=3.0, T=0.2, delta=0.9, prec=prec, ionic="half")
+    phi = inputs.random_phi(7, p.N)
+    ee = inputs.random_phi(8, p.N, 0.5)
+    with api.Context(p) as c:
+        c.set_site_energy(ee)
+        om, g = c.grad(phi)
+    o_om, o_g = oracle.omega_grad(oparams(p), phi, eps_extra=ee)
+    t = tol(prec)
+    assert om == pytest.approx(o_om, rel=t["om"])
+    assert np.max(np.abs(g - o_g)) <= 10 * t["g"] * max(1.0, np.abs(o_g).max())
+
+
+def test_seeded_start_field_is_bit_exact():
+    p = api.Params(8, 1, U=4.0, T=0.1)
+    with api.Context(p) as c:
+        for seed in (0, 1, 2**40 + 3):
+            c.adam_init(api.AdamConfig(seed=seed))
+            assert np.array_equal(c.phi(), inputs.seed_phi(seed, p.N))
+
+
+def test_adam_trajectory_4x4_matches_oracle():
+    """4x4 Hubbard, U=6, T=0.1, 64 frequencies, seed 0, lr=0.01: 300 Adam steps."""
+    p = api.Params(4, 64, U=6.0, T=0.1)
+    steps = 300
+    ad = api.AdamConfig(lr=0.01, max_steps=steps, seed=0)
+    phi_o, k, om_o, gm_o, oh, gh = oracle.adam_run(oparams(p), lr=0.01, max_steps=steps, seed=0,
+                                                   history=True)
+    with api.Context(p) as c:
+        c.adam_init(ad)
+        om1, gm1 = c.adam_step(1)
+        assert om1 == pytest.approx(oh[0], rel=1e-12)
+        assert gm1 == pytest.approx(gh[0], rel=1e-10)
+        om, gm = c.adam_step(steps - 1)
+        phi = c.phi()
+    assert om == pytest.approx(oh[steps - 1], rel=1e-10)
+    assert np.max(np.abs(phi - phi_o)) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_semantics_match_oracle(prec):
+    p = api.Params(4, 16, U=6.0, T=0.1, prec=prec)
+    ad = api.AdamConfig(lr=0.02, grad_tol=1e-4, max_steps=700, seed=3)
+    r = api.solve(p, ad)
+    phi_o, k, om_o, gm_o = oracle.adam_run(oparams(p), lr=0.02, grad_tol=1e-4, max_steps=700, seed=3)
+    if prec == "fp64":
+        assert r.steps == k
+        assert np.max(np.abs(r.phi - phi_o)) < 1e-9
+        assert r.omega == pytest.approx(om_o, rel=1e-10)
+    else:
+        assert abs(r.steps - k) <= 2
+        assert np.max(np.abs(r.phi - phi_o)) < 1e-5
+        assert r.omega == pytest.approx(om_o, rel=1e-5)
+    assert r.gmax < 1e-4 or r.steps == 700
+
+
+def test_checkpoint_resume_is_bit_identical():
+    p = api.Params(4, 8, U=4.0, T=0.2, delta=0.3)
+    ad = api.AdamConfig(lr=0.01, seed=5)
+    with api.Context(p) as a:
+        a.adam_init(ad)
+        a.adam_step(40)
+        phi_ref = a.phi()
+    with api.Context(p) as b:
+        b.adam_init(ad)
+        b.adam_step(15)
+        st = b.get_state()
+    with api.Context(p) as c:
+        c.set_state(ad, st)
+        c.adam_step(25)
+        assert np.array_equal(c.phi(), phi_ref)
+
+
+def test_nonfinite_phi_reported():
+    p = api.Params(4, 4, U=4.0, T=0.1)
+    phi = np.zeros(p.N)
+    phi[3] = np.nan
+    with api.Context(p) as c:
+        with pytest.raises(Exception, match="SCA_ENONFINITE"):
+            c.grad(phi)
+        # the context stays usable
+        om, g = c.grad(np.zeros(p.N))
+        assert np.isfinite(om)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autograd_function_matches_oracle_and_fd(prec):
+    torch = pytest.importorskip("torch")
+    p = api.Params(4, 8, U=4.0, T=0.1, delta=0.5, prec=prec)
+    phi0 = inputs.random_phi(21, p.N)
+    with api.Context(p) as c:
+        x = torch.tensor(phi0, dtype=torch.float64, device="cuda", requires_grad=True)
+        om = api.sca_potential(x, c)
+        om.backward()
+        g = x.grad.cpu().numpy()
+        o_om, o_g = oracle.omega_grad(oparams(p), phi0)
+        t = tol(prec)
+        assert float(om) == pytest.approx(o_om, rel=t["om"])
+        assert np.max(np.abs(g - o_g)) <= 10 * t["g"] * max(1.0, np.abs(o_g).max())
+        if prec == "fp64":
+            xx = torch.tensor(phi0[:], dtype=torch.float64, device="cuda", requires_grad=True)
+            assert torch.autograd.gradcheck(lambda v: api.sca_potential(v, c), (xx,), eps=1e-6,
+                                            atol=1e-6, rtol=1e-5)
+
+
+def test_forward_backward_entry_points():
+    torch = pytest.importorskip("torch")
+    p = api.Params(6, 5, U=4.0, T=0.15, delta=0.2, prec="fp32")
+    phi0 = inputs.random_phi(5, p.N)
+    with api.Context(p) as c:
+        x = torch.tensor(phi0, dtype=torch.float64, device="cuda")
+        om = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(x)
+        c.forward_dev(x, om)
+        c.backward_dev(x, g)
+        torch.cuda.synchronize()
+        om2, g2 = c.grad(phi0)
+        assert float(om) == pytest.approx(om2, rel=1e-12)
+        assert np.allclose(g.cpu().numpy(), g2, rtol=1e-12, atol=1e-14)
+        with pytest.raises(Exception, match="SCA_ENOSTATE"):
+            c.backward_dev(x, g)
