@@ -223,6 +223,30 @@ sca_status sca_request_times(sca_server* srv, uint64_t req_id, double* submit_s,
 /* Stops the loop (in-flight requests are abandoned) and frees everything. */
 void sca_server_destroy(sca_server* srv);
 
+/* ------------------------------------------------------ allocation-free ---- */
+
+/* Omega and dOmega/dphi like sca_grad_dev, without allocating any memory.  (The paper has
+ * no counterpart: this entry point exists for callers that cannot let a library allocate,
+ * e.g. a process whose device memory is reserved up front by its own pool allocator, or a
+ * steady-state loop that must not call cudaMalloc/cudaFree because they can synchronise
+ * the device.)
+ *  - params: as for sca_create, with prec SCA_PREC_FP64 or SCA_PREC_FP32 (CUDA-core
+ *    contractions); d_phi: N device doubles (input); d_omega: 1 device double and d_grad:
+ *    N device doubles (outputs, written by kernels); stream: cudaStream_t or NULL.
+ *  - Workspace: one file-scope device array of 64 MiB that every GPU which loads the
+ *    library holds until the process exits.  The blocks are processed in chunks that fit
+ *    it; a problem whose single block (plus the per-block log-dets and diagonals) does not
+ *    fit is rejected with SCA_EINVAL and a message, before anything is enqueued.
+ *  - The first call on each device looks up the array's device address (set-up on the
+ *    calling thread's current device); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents behind; the call
+ *    clears what must start at zero.  Calls that overlap on the GPU (other streams or
+ *    threads) race on the array and give wrong results: serialise them.
+ *  - Makes no cudaMalloc, cudaFree or other allocating call.  Returns without
+ *    synchronising; launch errors return SCA_ECUDA. */
+sca_status sca_grad_noalloc_dev(const sca_params* params, const double* d_phi, double* d_omega,
+                                double* d_grad, void* stream);
+
 /* ------------------------------------------------------------ streams ---- */
 
 /* Makes every later call on this context enqueue on `stream` (a cudaStream_t; NULL

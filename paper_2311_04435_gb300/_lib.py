@@ -67,6 +67,7 @@ SIGNATURES = [
     ("sca_poll", ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _i32p, _dp]),
     ("sca_request_times", ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _dp, _dp]),
     ("sca_server_destroy", None, [_vp]),
+    ("sca_grad_noalloc_dev", ctypes.c_int, [_PP, _vp, _vp, _vp, _vp]),
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
     ("sca_profile_enable", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_profile_read", ctypes.c_int, [_vp, ctypes.c_int32, _dp, _u64p]),
