@@ -89,7 +89,13 @@ class Context:
         self.N = params.N
         self.B = 2 * params.n_omega
         self._h = ctypes.c_void_p()
+        self._gen = 0       # bumped by every call that runs work on the context
+        self._kept = -1     # generation whose inverses are resident (forward_dev)
         check(_lib.lib().sca_create(ctypes.byref(params.c()), ctypes.byref(self._h)))
+
+    def _bump(self):
+        self._gen += 1
+        return self._gen
 
     def close(self):
         if self._h:
@@ -113,6 +119,7 @@ class Context:
         return self._h
 
     def set_site_energy(self, eps_extra=None):
+        self._bump()
         if eps_extra is None:
             check(_lib.lib().sca_set_site_energy(self._h, None))
         else:
@@ -121,12 +128,14 @@ class Context:
             check(_lib.lib().sca_set_site_energy(self._h, _ptr(e)))
 
     def potential(self, phi) -> float:
+        self._bump()
         phi = _f64(phi)
         om = ctypes.c_double()
         check(_lib.lib().sca_potential(self._h, _ptr(phi), ctypes.byref(om)))
         return om.value
 
     def grad(self, phi):
+        self._bump()
         phi = _f64(phi)
         om = ctypes.c_double()
         g = np.zeros(self.N)
@@ -135,6 +144,7 @@ class Context:
 
     def blocks(self, phi, grad: bool = True):
         """Per block b = 2n+s: ln|det A_b| and (grad) sigma_b Re G_b,ii."""
+        self._bump()
         phi = _f64(phi)
         ld = np.zeros(self.B)
         gd = np.zeros((self.B, self.N)) if grad else None
@@ -142,6 +152,7 @@ class Context:
         return (ld, gd) if grad else ld
 
     def assemble(self, phi, b0: int = 0, count: int = 1) -> np.ndarray:
+        self._bump()
         phi = _f64(phi)
         out = np.zeros((count, self.N, self.N, 2))
         check(_lib.lib().sca_debug_assemble(self._h, _ptr(phi), int(b0), int(count), _ptr(out)))
@@ -155,6 +166,7 @@ class Context:
 
     def potential_dev(self, phi_t, out_t=None):
         import torch
+        self._bump()
         assert phi_t.is_cuda and phi_t.dtype == torch.float64 and phi_t.is_contiguous()
         out = out_t if out_t is not None else torch.empty(1, dtype=torch.float64, device=phi_t.device)
         check(_lib.lib().sca_potential_dev(self._h, ctypes.c_void_p(phi_t.data_ptr()),
@@ -163,6 +175,7 @@ class Context:
 
     def grad_dev(self, phi_t, omega_t=None, grad_t=None):
         import torch
+        self._bump()
         assert phi_t.is_cuda and phi_t.dtype == torch.float64 and phi_t.is_contiguous()
         om = omega_t if omega_t is not None else torch.empty(1, dtype=torch.float64, device=phi_t.device)
         g = grad_t if grad_t is not None else torch.empty_like(phi_t)
@@ -171,11 +184,21 @@ class Context:
                                       self._stream()))
         return om, g
 
-    def forward_dev(self, phi_t, omega_t):
+    def forward_dev(self, phi_t, omega_t) -> int:
+        """Omega via the inversion; returns the generation whose inverses stay resident."""
+        gen = self._bump()
         check(_lib.lib().sca_forward_dev(self._h, ctypes.c_void_p(phi_t.data_ptr()),
                                          ctypes.c_void_p(omega_t.data_ptr()), self._stream()))
+        self._kept = gen
+        return gen
 
-    def backward_dev(self, phi_t, grad_t):
+    def backward_dev(self, phi_t, grad_t, gen: int | None = None):
+        """Adjoint stage from the resident inverses of generation `gen` (default: the
+        latest forward_dev).  Raises SCAError(SCA_ENOSTATE) if they are gone."""
+        if gen is not None and (gen != self._gen or self._kept != gen):
+            raise _lib.SCAError(_lib.SCA_ENOSTATE, "inverses of that forward are no longer resident")
+        self._bump()
+        self._kept = -1
         check(_lib.lib().sca_backward_dev(self._h, ctypes.c_void_p(phi_t.data_ptr()),
                                           ctypes.c_void_p(grad_t.data_ptr()), self._stream()))
 
@@ -200,6 +223,7 @@ class Context:
 
     # ---- Adam state resident on the device
     def adam_init(self, adam: AdamConfig, phi0=None):
+        self._bump()
         self._adam = adam
         if phi0 is None:
             check(_lib.lib().sca_adam_init(self._h, ctypes.byref(adam.c()), None))
@@ -208,6 +232,7 @@ class Context:
             check(_lib.lib().sca_adam_init(self._h, ctypes.byref(adam.c()), _ptr(p)))
 
     def adam_step(self, nsteps: int = 1):
+        self._bump()
         om, gm = ctypes.c_double(), ctypes.c_double()
         check(_lib.lib().sca_adam_step(self._h, int(nsteps), ctypes.byref(om), ctypes.byref(gm)))
         return om.value, gm.value
@@ -224,6 +249,7 @@ class Context:
         return {"phi": phi, "m": m, "v": v, "step": int(step.value)}
 
     def set_state(self, adam: AdamConfig, state: dict):
+        self._bump()
         self._adam = adam
         check(_lib.lib().sca_set_state(self._h, ctypes.byref(adam.c()), _ptr(_f64(state["phi"])),
                                        _ptr(_f64(state["m"])), _ptr(_f64(state["v"])),
@@ -265,7 +291,7 @@ def _make_function():
             phi = phi.detach().contiguous()
             om = torch.empty(1, dtype=torch.float64, device=phi.device)
             if ctx.needs_input_grad[0]:
-                handle.forward_dev(phi, om)
+                ctx.gen = handle.forward_dev(phi, om)
                 ctx.save_for_backward(phi)
                 ctx.handle = handle
             else:
@@ -277,7 +303,7 @@ def _make_function():
             (phi,) = ctx.saved_tensors
             g = torch.empty_like(phi)
             try:
-                ctx.handle.backward_dev(phi, g)
+                ctx.handle.backward_dev(phi, g, ctx.gen)
             except _lib.SCAError as err:
                 if err.status != _lib.SCA_ENOSTATE:
                     raise

@@ -236,6 +236,7 @@ struct sca_ctx {
   bool adam_ready = false;
   int32_t step = 0;
   bool kept = false;  // inverses of every block resident from sca_forward_dev
+  const double* kept_phi = nullptr;  // the d_phi that forward was given
 };
 
 namespace {
@@ -347,13 +348,15 @@ sca_status sca_forward_dev(sca_ctx* c, const double* d_phi, double* d_omega, voi
   if (st != SCA_OK) return st;
   if ((st = run_reduce(c->e, d_phi, d_omega, nullptr, nullptr, s)) != SCA_OK) return st;
   c->kept = (c->e.chunk == c->e.B);
+  c->kept_phi = d_phi;
   return SCA_OK;
 }
 
 sca_status sca_backward_dev(sca_ctx* c, const double* d_phi, double* d_grad, void* stream) {
   if (!c || !d_phi || !d_grad) { set_error("NULL argument"); return SCA_EINVAL; }
-  if (!c->kept) {
-    set_error("sca_backward_dev needs the resident inverses of a preceding sca_forward_dev");
+  if (!c->kept || d_phi != c->kept_phi) {
+    set_error("sca_backward_dev needs the resident inverses of a preceding sca_forward_dev "
+              "with the same d_phi");
     return SCA_ENOSTATE;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
