@@ -92,7 +92,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.plane_stride = (size_t)e.N * e.ldm;
   e.mat_stride = 2 * e.plane_stride;
   e.fw_plane = (size_t)e.N * e.nb;
-  e.fw_mat = (e.tc ? 4 : 2) * e.fw_plane;
+  e.fw_mat = (e.tc ? 6 : 2) * e.fw_plane;
   const size_t C = S;  // compute type of the small kernels = storage type
   size_t bytes = 0;
   bytes += (size_t)e.chunk * e.mat_stride * S;           // blocks
@@ -251,6 +251,10 @@ sca_status sync_status(sca_ctx* c, cudaStream_t s) {
 }
 
 sca_status check_finite(sca_ctx* c) {
+  if (((int)c->e.h_status[6]) & 2) {
+    set_error("a bounded device-side wait in the tensor-core update ran out");
+    return SCA_ETIMEOUT;
+  }
   if (c->e.h_status[4] != 0.0) {
     set_error("non-finite Omega or gradient, or a singular block");
     return SCA_ENONFINITE;

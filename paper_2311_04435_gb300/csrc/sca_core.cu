@@ -273,9 +273,10 @@ __global__ void k_trinv(const S* M, int ldm, size_t mat_stride, size_t plane_str
 // Then M' = mask(M) - F W (mask zeroes row block K and column block K for Gauss-Jordan).
 // With `split`, planes are {re_hi, im_hi, re_lo, im_lo}: hi = value with the low 13
 // mantissa bits cleared (exact TF32), lo = value - hi.
+// W additionally carries -im (hi, lo) in planes 4 and 5 for the tensor-core complex product.
 template <typename S>
 __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, double vre, double vim,
-                                         bool split) {
+                                         bool split, bool neg) {
   if (!split) {
     base[off] = (S)vre;
     base[plane + off] = (S)vim;
@@ -288,6 +289,10 @@ __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, doub
     b[plane + off] = hi;
     b[2 * plane + off] = fr - hr;
     b[3 * plane + off] = fi - hi;
+    if (neg) {
+      b[4 * plane + off] = -hi;
+      b[5 * plane + off] = -(fi - hi);
+    }
   }
 }
 
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
       }
     }
-    store_fw(out, fw_plane, obase + c, vre, vim, split != 0);
+    store_fw(out, fw_plane, obase + c, vre, vim, split != 0, which == 1);
   }
 }
 
@@ -558,6 +563,7 @@ __global__ void __launch_bounds__(RT)
     status[3] = s_ab[0] / N;
     status[4] = nonfinite ? 1.0 : 0.0;
     if (update) status[5] += 1.0;
+    status[6] = flags ? (double)*flags : 0.0;
   }
 }
 

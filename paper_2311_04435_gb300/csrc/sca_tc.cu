@@ -1,14 +1,481 @@
-// tcgen05 (5th-generation tensor core) 3xTF32 rank-nb update for sm_103a.
+// tcgen05 (5th-generation tensor core) rank-nb update of the Gauss-Jordan / LU sweep on
+// sm_103a, in split TF32 ("3xTF32") with float32 accumulation:
+//
+//   M[i, j] <- mask(i, j) M[i, j] - sum_c F[i, c] W[j, c]          (complex, planar)
+//
+// Complex product as one real MMA of width 256: for a 128-row tile of F and a 128-column
+// tile of W, the 128 x 256 real tile [C_re | C_im] is
+//   F_re [W_re | W_im] + F_im [-W_im | W_re],
+// so the B operand of the first product is the 256-row stack (W_re; W_im) and that of the
+// second (-W_im; W_re).  Shared memory holds (-W_im, W_re, W_im) contiguously, and both stacks
+// are windows of it.  Each real product is split as hi*hi + hi*lo + lo*hi with hi = the value
+// truncated to TF32 and lo = value - hi (written by the prep kernel), i.e. 6 MMAs of
+// M=128, N=256, K=8 per K step.
+//
+// Kernel structure (persistent, one CTA per SM, 192 threads):
+//   warp 0  : TMA producer (cp.async.bulk.tensor, 2-stage shared-memory ring, K = 16 per stage)
+//   warp 1  : TMEM allocator and MMA issuer (tcgen05.mma, one elected thread)
+//   warps 2-5: epilogue (tcgen05.ld of the accumulator, read-modify-write of M in HBM)
+// Accumulators are double buffered in TMEM (2 x 256 columns) so the epilogue of one tile
+// overlaps the MMAs of the next.  Every mbarrier wait is bounded; on time-out the kernel
+// records an error, stops issuing work, waits (bounded) for its own copies, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+
 #include "sca_internal.h"
 
 namespace sca {
+namespace {
 
-bool tc_supported() { return false; }
-sca_status tc_prepare(Engine&) { return SCA_OK; }
-void tc_release(Engine&) {}
-sca_status tc_update(Engine&, int, int, int, int, int, bool, cudaStream_t) {
-  set_error("tcgen05 update not available");
-  return SCA_EINVAL;
+constexpr int kBM = 128;           // F rows per tile
+constexpr int kBNc = 128;          // complex W columns per tile (real MMA N = 256)
+constexpr int kKS = 16;            // K per pipeline stage (SWIZZLE_64B rows of 64 bytes)
+constexpr int kStages = 2;
+constexpr int kTileBytes = kBM * kKS * 4;             // one 128 x 16 float plane: 8 KB
+constexpr int kStageBytes = 10 * kTileBytes;          // 4 F planes + 6 W planes: 80 KB
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;                   // 2 accumulators x 256 columns
+constexpr long long kWaitCycles = 4000000000ll;       // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and raises the CTA's abort flag) if the phase does not
+// complete within kWaitCycles, or if another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05), K-major operand with 64-byte swizzle:
+// rows of 64 bytes, 8-row core groups 512 bytes apart (stride byte offset), leading byte
+// offset unused for swizzled K-major layouts, descriptor version 1, layout code 4 (64B).
+__device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
+  d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, D = f32, A = B = tf32, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+struct TcArgs {
+  float* M;
+  int N, ldm;
+  long long mat_stride, plane_stride;  // floats
+  int nb;                              // K extent (multiple of 16)
+  int r0, c0;                          // first updated row / column
+  int k0, kb, gj;                      // masked block K (Gauss-Jordan)
+  int tiles_m, tiles_n, tiles;         // per block, and total
+  int fplanes, wplanes;                // planes per block in the F / W tensor maps
+  int* err;                            // device error word (bit 1: wait time-out)
+};
+
+// Shared-memory stage layout (each slot one 128 x 16 float plane, 8 KB, 1024-aligned):
+//   0 F_re_hi  1 F_im_hi  2 F_re_lo  3 F_im_lo
+//   4 -W_im_hi 5 W_re_hi  6 W_im_hi  7 -W_im_lo 8 W_re_lo 9 W_im_lo
+// Global planes: F {0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo};
+//                W {0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo, 4 -im_hi, 5 -im_lo}.
+__constant__ int kFPlaneOfSlot[4] = {0, 1, 2, 3};
+__constant__ int kWPlaneOfSlot[6] = {4, 0, 1, 5, 2, 3};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_update_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmW,
+                TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* full = bars;                 // [kStages]
+  uint64_t* empty = bars + kStages;      // [kStages]
+  uint64_t* tfull = bars + 2 * kStages;  // [2]
+  uint64_t* tempty = tfull + 2;          // [2]
+  uint64_t* mdone = tempty + 2;          // [1] all MMAs of this CTA completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int ksteps = a.nb / kKS;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int last_parity[kStages];
+      for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
+      for (int t = blockIdx.x; t < a.tiles && !*abort_flag; t += gridDim.x) {
+        const int mat = t / (a.tiles_m * a.tiles_n);
+        const int rem = t - mat * a.tiles_m * a.tiles_n;
+        const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+        const int frow = a.r0 + tm * kBM, wrow = a.c0 + tn * kBNc;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
+          mbar_expect_tx(&full[stage], kStageBytes);
+          unsigned char* st = smem + stage * kStageBytes;
+          for (int s = 0; s < 4; ++s)
+            tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKS, frow,
+                        mat * a.fplanes + kFPlaneOfSlot[s]);
+          for (int s = 0; s < 6; ++s)
+            tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKS, wrow,
+                        mat * a.wplanes + kWPlaneOfSlot[s]);
+          last_parity[stage] = (int)phase;
+          if (++stage == kStages) { stage = 0; phase ^= 1; }
+        }
+      }
+      // Drain: every copy issued must have landed before the CTA leaves (bounded wait; after
+      // a normal run these phases have long completed and the waits return at once).
+      volatile int drain_abort = 0;
+      for (int s = 0; s < kStages; ++s)
+        if (last_parity[s] >= 0) (void)mbar_wait(&full[s], (uint32_t)last_parity[s], &drain_abort);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int iter = 0;
+      for (int t = blockIdx.x; t < a.tiles && !*abort_flag; t += gridDim.x, ++iter) {
+        const int buf = iter & 1;
+        const uint32_t use = (uint32_t)(iter >> 1);  // times this buffer was used before
+        if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256);
+        bool ok = true;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + stage * kStageBytes);
+#pragma unroll
+          for (int k8 = 0; k8 < 2; ++k8) {
+            const uint32_t off = (uint32_t)(k8 * 32);
+            const uint64_t fr_hi = sdesc_k64(st + 0 * kTileBytes + off);
+            const uint64_t fi_hi = sdesc_k64(st + 1 * kTileBytes + off);
+            const uint64_t fr_lo = sdesc_k64(st + 2 * kTileBytes + off);
+            const uint64_t fi_lo = sdesc_k64(st + 3 * kTileBytes + off);
+            const uint64_t b2_hi = sdesc_k64(st + 4 * kTileBytes + off);  // (-W_im; W_re)
+            const uint64_t b1_hi = sdesc_k64(st + 5 * kTileBytes + off);  // (W_re; W_im)
+            const uint64_t b2_lo = sdesc_k64(st + 7 * kTileBytes + off);
+            const uint64_t b1_lo = sdesc_k64(st + 8 * kTileBytes + off);
+            const uint32_t acc0 = (ks > 0 || k8 > 0) ? 1u : 0u;
+            mma_tf32(d_tmem, fr_hi, b1_hi, acc0);
+            mma_tf32(d_tmem, fr_hi, b1_lo, 1u);
+            mma_tf32(d_tmem, fr_lo, b1_hi, 1u);
+            mma_tf32(d_tmem, fi_hi, b2_hi, 1u);
+            mma_tf32(d_tmem, fi_hi, b2_lo, 1u);
+            mma_tf32(d_tmem, fi_lo, b2_hi, 1u);
+          }
+          mma_commit(&empty[stage]);  // frees the stage once these MMAs have read it
+          if (++stage == kStages) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+      }
+      // All MMAs issued by this thread complete before TMEM is released.
+      mma_commit(mdone);
+      volatile int drain_abort = 0;
+      (void)mbar_wait(mdone, 0, &drain_abort);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..5)
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int row_in_tile = q * 32 + lane;
+    int iter = 0;
+    for (int t = blockIdx.x; t < a.tiles; t += gridDim.x, ++iter) {
+      const int buf = iter & 1;
+      const uint32_t use = (uint32_t)(iter >> 1);
+      if (!mbar_wait(&tfull[buf], use & 1, abort_flag)) break;
+      tc_fence_after();
+      const int mat = t / (a.tiles_m * a.tiles_n);
+      const int rem = t - mat * a.tiles_m * a.tiles_n;
+      const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+      const int i = a.r0 + tm * kBM + row_in_tile;
+      const int j0 = a.c0 + tn * kBNc;
+      float* re = a.M + (long long)mat * a.mat_stride;
+      float* im = re + a.plane_stride;
+      const bool row_ok = i < a.N;
+      const bool rowk = a.gj && i >= a.k0 && i < a.k0 + a.kb;
+      const uint32_t tbase = tmem_base + (uint32_t)(buf * 256) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int cc = 0; cc < kBNc; cc += 32) {
+        uint32_t cr[32], ci[32];
+        tmem_ld32(tbase + (uint32_t)cc, cr);
+        tmem_ld32(tbase + (uint32_t)(kBNc + cc), ci);
+        tmem_ld_wait();
+        if (row_ok) {
+          const long long o = (long long)i * a.ldm + j0 + cc;
+          const bool colk = a.gj && (j0 + cc < a.k0 + a.kb) && (j0 + cc + 32 > a.k0);
+          if (!rowk && !colk && j0 + cc + 32 <= a.N) {
+            float4* pr = reinterpret_cast<float4*>(re + o);
+            float4* pi = reinterpret_cast<float4*>(im + o);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              float4 vr = pr[e], vi = pi[e];
+              vr.x -= __uint_as_float(cr[4 * e + 0]); vr.y -= __uint_as_float(cr[4 * e + 1]);
+              vr.z -= __uint_as_float(cr[4 * e + 2]); vr.w -= __uint_as_float(cr[4 * e + 3]);
+              vi.x -= __uint_as_float(ci[4 * e + 0]); vi.y -= __uint_as_float(ci[4 * e + 1]);
+              vi.z -= __uint_as_float(ci[4 * e + 2]); vi.w -= __uint_as_float(ci[4 * e + 3]);
+              pr[e] = vr;
+              pi[e] = vi;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const int j = j0 + cc + e;
+              if (j < a.N) {
+                const bool keep = !(rowk || (a.gj && j >= a.k0 && j < a.k0 + a.kb));
+                const float mr = keep ? re[o + e] : 0.f, mi = keep ? im[o + e] : 0.f;
+                re[o + e] = mr - __uint_as_float(cr[e]);
+                im[o + e] = mi - __uint_as_float(ci[e]);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(a.err, 2);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+struct TcMaps {
+  CUtensorMap F, W;
+  int sms = 0;
+};
+
+// 3-D map over [blocks*planes][N rows][nb] floats, box 16 x 128 x 1, 64-byte swizzle.
+bool make_map(CUtensorMap* m, void* base, int nb, int N, long long zdim) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)nb, (cuuint64_t)N, (cuuint64_t)zdim};
+  cuuint64_t strides[2] = {(cuuint64_t)nb * 4, (cuuint64_t)N * nb * 4};
+  cuuint32_t box[3] = {(cuuint32_t)kKS, (cuuint32_t)kBM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_supported() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+sca_status tc_prepare(Engine& e) {
+  if (e.nb % kKS != 0) {
+    set_error("tcgen05 update needs nb to be a multiple of 16");
+    return SCA_EINVAL;
+  }
+  TcMaps* t = new TcMaps();
+  std::memset(&t->F, 0, sizeof(t->F));
+  std::memset(&t->W, 0, sizeof(t->W));
+  const long long zf = (long long)e.chunk * (long long)(e.fw_mat / e.fw_plane);
+  if (!make_map(&t->F, e.F, e.nb, e.N, zf) || !make_map(&t->W, e.W, e.nb, e.N, zf)) {
+    delete t;
+    set_error("cuTensorMapEncodeTiled failed for the rank-nb factors");
+    return SCA_ECUDA;
+  }
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (err != cudaSuccess) {
+    delete t;
+    return cuda_fail(err, "tcgen05 update set-up");
+  }
+  e.tmap = t;
+  return SCA_OK;
+}
+
+void tc_release(Engine& e) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t) return;
+  delete t;
+  e.tmap = nullptr;
+}
+
+sca_status tc_update(Engine& e, int cnt, int k0, int kb, int r0, int c0, bool gj, cudaStream_t s) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t) {
+    set_error("tcgen05 update used before tc_prepare");
+    return SCA_ENOSTATE;
+  }
+  TcArgs a;
+  a.M = static_cast<float*>(e.M);
+  a.N = e.N;
+  a.ldm = e.ldm;
+  a.mat_stride = (long long)e.mat_stride;
+  a.plane_stride = (long long)e.plane_stride;
+  a.nb = e.nb;
+  a.r0 = r0;
+  a.c0 = c0;
+  a.k0 = k0;
+  a.kb = kb;
+  a.gj = gj ? 1 : 0;
+  a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
+  a.tiles_n = (e.N - c0 + kBNc - 1) / kBNc;
+  a.tiles = a.tiles_m * a.tiles_n * cnt;
+  a.fplanes = a.wplanes = (int)(e.fw_mat / e.fw_plane);
+  a.err = e.flags;
+  if (a.tiles <= 0) return SCA_OK;
+  const int grid = std::min(a.tiles, t->sms);
+  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "tcgen05 update launch");
+  return SCA_OK;
+}
+
 
 }  // namespace sca
