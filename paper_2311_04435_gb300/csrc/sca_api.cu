@@ -75,13 +75,26 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.delta_eff = (p.ionic == SCA_IONIC_HALF) ? 0.5 * p.delta : p.delta;
   // tcgen05 path for blocks of at least 128 rows; smaller blocks use CUDA cores.
   e.tc = (p.prec == SCA_PREC_3XTF32) && e.N >= 128 && tc_supported();
-  int nb = e.fp64 ? 32 : (e.tc ? 64 : 32);
+  int nb = e.fp64 ? 32 : (e.tc ? 128 : 64);
   if (const char* v = std::getenv("SCA_NB")) {
     const int x = std::atoi(v);
-    if (x >= 8 && x <= 128 && (x % 8) == 0) nb = x;
+    if (x >= 16 && x <= (e.fp64 ? 64 : 128) && (x % 16) == 0) nb = x;
   }
-  if (e.tc) nb = std::max(32, nb / 32 * 32);
   e.nb = std::min(nb, e.tc ? nb : e.N);
+  // Blocks with omega_n > 4|t| are strictly diagonally dominant by columns (|a_jj| >= omega_n,
+  // off-diagonal column sum 4|t|); dominance survives elimination, so partial pivoting keeps
+  // the diagonal and those blocks skip the pivot search.  They are b >= piv_blocks.
+  int n_piv = 0;
+  const double thr = 4.0 * std::fabs(p.t) * (1.0 + 1e-3);
+  while (n_piv < p.n_omega && (2.0 * n_piv + 1.0) * M_PI * p.T <= thr) ++n_piv;
+  e.piv_blocks = 2 * n_piv;
+  if (const char* v = std::getenv("SCA_PIVOT_ALL"))
+    if (std::atoi(v) != 0) e.piv_blocks = e.B;
+  // Width of the pivoted group's shared-memory panel: N x nb_piv complex values <= 200 KB.
+  const size_t cbytes = e.fp64 ? 16 : 8;
+  int nbp = 1;
+  while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2) * cbytes <= 200 * 1024) nbp *= 2;
+  e.nb_piv = nbp;
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;
   if (const char* v = std::getenv("SCA_MAX_BLOCKS_RESIDENT")) {
@@ -149,6 +162,10 @@ sca_status allocate(Engine& e) {
   if (err == cudaSuccess) err = cudaMemset(e.W, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
+  err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming);
+  if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }
   return SCA_OK;
 }
 
@@ -212,6 +229,11 @@ void prof_free(Engine& e) {
 void release(Engine& e) {
   prof_free(e);
   tc_release(e);
+  if (e.side) { cudaStreamSynchronize(e.side); cudaStreamDestroy(e.side); }
+  if (e.ev_fork) cudaEventDestroy(e.ev_fork);
+  if (e.ev_join) cudaEventDestroy(e.ev_join);
+  e.side = nullptr;
+  e.ev_fork = e.ev_join = nullptr;
   void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.piv, e.perm, e.flags, e.ld, e.gd, e.eps_extra,
                   e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
   for (void* q : ptrs)

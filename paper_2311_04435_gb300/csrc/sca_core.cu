@@ -86,100 +86,6 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
   }
 }
 
-// --------------------------------------------------------------------- panel
-// Pivoted LU of the column panel rows [k0, N) x cols [k0, k0+kb) of each block, in place.
-// One CTA per block.  Pivot: row of largest |z|^2 (first index on ties), found with warp
-// shuffles then across warps.  ld[b] += sum ln|u_kk| in float64.
-template <typename S, typename C, int NT>
-__global__ void __launch_bounds__(NT) k_panel(S* M, int N, int ldm, size_t mat_stride,
-                                              size_t plane_stride, int k0, int kb, int b0,
-                                              double* ld, int* piv, int* perm, int* flags) {
-  const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  S* re = M + mat * mat_stride;
-  S* im = re + plane_stride;
-  __shared__ C prow_re[256], prow_im[256];
-  __shared__ double red_v[NT / 32];
-  __shared__ int red_i[NT / 32];
-  __shared__ int s_p;
-  double ldacc = 0.0;
-  for (int c = 0; c < kb; ++c) {
-    const int col = k0 + c;
-    double best = -1.0;
-    int bi = N;
-    for (int r = col + tid; r < N; r += NT) {
-      const double a = (double)re[(size_t)r * ldm + col], q = (double)im[(size_t)r * ldm + col];
-      const double v = a * a + q * q;
-      if (v > best) { best = v; bi = r; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      best = (lane < NT / 32) ? red_v[lane] : -1.0;
-      bi = (lane < NT / 32) ? red_i[lane] : N;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) s_p = (bi < N) ? bi : col;
-    }
-    __syncthreads();
-    const int p = s_p;
-    if (p != col)
-      for (int j = tid; j < kb; j += NT) {
-        const size_t a = (size_t)col * ldm + k0 + j, q = (size_t)p * ldm + k0 + j;
-        const S tr = re[a], ti = im[a];
-        re[a] = re[q]; im[a] = im[q];
-        re[q] = tr; im[q] = ti;
-      }
-    if (tid == 0) {
-      piv[(size_t)mat * N + col] = p;
-      if (p != col) {
-        int* pm = perm + (size_t)mat * N;
-        const int tmp = pm[col];
-        pm[col] = pm[p];
-        pm[p] = tmp;
-      }
-    }
-    __syncthreads();
-    for (int j = c + tid; j < kb; j += NT) {
-      prow_re[j] = (C)re[(size_t)col * ldm + k0 + j];
-      prow_im[j] = (C)im[(size_t)col * ldm + k0 + j];
-    }
-    __syncthreads();
-    const double dre = (double)prow_re[c], dim = (double)prow_im[c];
-    const double mag2 = dre * dre + dim * dim;
-    const bool ok = (mag2 > 0.0) && isfinite(mag2);
-    if (tid == 0) {
-      if (!ok) atomicOr(flags, 1);
-      ldacc += 0.5 * log(ok ? mag2 : 1.0);
-    }
-    const C ire = ok ? (C)(dre / mag2) : (C)0, iim = ok ? (C)(-dim / mag2) : (C)0;
-    for (int r = col + 1 + tid; r < N; r += NT) {
-      S* rr = re + (size_t)r * ldm + k0;
-      S* ri = im + (size_t)r * ldm + k0;
-      const C are = (C)rr[c], aim = (C)ri[c];
-      const C lre = are * ire - aim * iim, lim = are * iim + aim * ire;
-      rr[c] = (S)lre;
-      ri[c] = (S)lim;
-      for (int j = c + 1; j < kb; ++j) {
-        const C ur = prow_re[j], ui = prow_im[j];
-        rr[j] = (S)((C)rr[j] - (lre * ur - lim * ui));
-        ri[j] = (S)((C)ri[j] - (lre * ui + lim * ur));
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) ld[b0 + mat] += ldacc;
-}
-
 // ---------------------------------------------------------------------- swap
 // Applies the panel's interchanges, in order, to the columns outside the panel
 // (columns >= jstart only).
@@ -205,75 +111,217 @@ __global__ void k_swap(S* M, int N, int ldm, size_t mat_stride, size_t plane_str
   }
 }
 
-// --------------------------------------------------------------------- trinv
-// inv(L11) (unit lower) and inv(U11) (upper) of the kb x kb pivot block, zero padded to
-// nb x nb.  Tinv layout per block: [0] = inv(L11), [1] = inv(U11), row-major nb x nb cpx<C>.
-template <typename S, typename C>
-__global__ void k_trinv(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0,
-                        int kb, int nb, cpx<C>* Tinv) {
+// ------------------------------------------------------------ panel (SMEM)
+// Pivoted LU of the column panel rows [k0, N) x cols [k0, k0+kb) of each block, one CTA per
+// block, the m x kb panel (m = N - k0) held in shared memory for the whole column loop.
+// Pivot: row of largest |z|^2 (first index on ties), found with warp shuffles then across
+// warps.  ld[b] += sum ln|u_kk| in float64; piv / perm record the interchanges.
+template <typename S, typename C, int NT>
+__global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t mat_stride,
+                                                   size_t plane_stride, int k0, int kb, int b0,
+                                                   double* ld, int* piv, int* perm, int* flags) {
   extern __shared__ unsigned char smem_raw[];
-  cpx<C>* blk = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
-  cpx<C>* Y = blk + kb * kb;                           // nb x nb
+  cpx<C>* P = reinterpret_cast<cpx<C>*>(smem_raw);  // m x kb, row-major
+  __shared__ double red_v[NT / 32];
+  __shared__ int red_i[NT / 32];
+  __shared__ int s_p;
+  const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = N - k0;
+  S* re = M + mat * mat_stride;
+  S* im = re + plane_stride;
+  for (int e = tid; e < m * kb; e += NT) {
+    const int r = e / kb, c = e - r * kb;
+    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+    P[e] = {(C)re[o], (C)im[o]};
+  }
+  __syncthreads();
+  double ldacc = 0.0;
+  for (int c = 0; c < kb; ++c) {
+    double best = -1.0;
+    int bi = m;
+    for (int r = c + tid; r < m; r += NT) {
+      const cpx<C> z = P[r * kb + c];
+      const double v = (double)z.re * z.re + (double)z.im * z.im;
+      if (v > best) { best = v; bi = r; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = (lane < NT / 32) ? red_v[lane] : -1.0;
+      bi = (lane < NT / 32) ? red_i[lane] : m;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) s_p = (bi < m) ? bi : c;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != c)
+      for (int j = tid; j < kb; j += NT) {
+        const cpx<C> t = P[c * kb + j];
+        P[c * kb + j] = P[p * kb + j];
+        P[p * kb + j] = t;
+      }
+    if (tid == 0) {
+      piv[(size_t)mat * N + k0 + c] = k0 + p;
+      if (p != c) {
+        int* pm = perm + (size_t)mat * N;
+        const int tmp = pm[k0 + c];
+        pm[k0 + c] = pm[k0 + p];
+        pm[k0 + p] = tmp;
+      }
+    }
+    __syncthreads();
+    const cpx<C> d = P[c * kb + c];
+    const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
+    const bool ok = (mag2 > 0.0) && isfinite(mag2);
+    if (tid == 0) {
+      if (!ok) atomicOr(flags, 1);
+      ldacc += 0.5 * log(ok ? mag2 : 1.0);
+    }
+    const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+    for (int r = c + 1 + tid; r < m; r += NT) {
+      const cpx<C> l = cmul(P[r * kb + c], inv);
+      P[r * kb + c] = l;
+      for (int j = c + 1; j < kb; ++j) {
+        const cpx<C> u = P[c * kb + j];
+        P[r * kb + j].re -= l.re * u.re - l.im * u.im;
+        P[r * kb + j].im -= l.re * u.im + l.im * u.re;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * kb; e += NT) {
+    const int r = e / kb, c = e - r * kb;
+    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+    re[o] = (S)P[e].re;
+    im[o] = (S)P[e].im;
+  }
+  if (tid == 0) ld[b0 + mat] += ldacc;
+}
+
+// ---------------------------------------------------------------- diag block
+// The kb x kb pivot block M[K, K] in shared memory.  factor = 1: the block is strictly
+// diagonally dominant by columns (i w_n dominates the hopping), so partial pivoting would
+// keep the diagonal at every step: LU without interchanges, ln|u_kk| into ld[b].  factor = 0:
+// the block already holds L11\U11 from the pivoted panel.  Then, in place, inv(U11) and
+// inv(L11) (column-oriented triangular inversion), and out to Tinv:
+//   slot 0: T = inv(M_KK) = inv(U11) inv(L11)      slot 1: inv(L11)      (nb x nb, padded)
+template <typename S, typename C, int NT>
+__global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat_stride,
+                                                 size_t plane_stride, int k0, int kb, int nb,
+                                                 int b0, double* ld, cpx<C>* Tinv, int factor,
+                                                 int* flags) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
+  cpx<C>* x = A + kb * kb;                           // kb scratch column
   const int mat = blockIdx.x, tid = threadIdx.x;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
+  for (int e = tid; e < kb * kb; e += NT) {
     const int r = e / kb, c = e - r * kb;
-    blk[e] = {(C)re[(size_t)(k0 + r) * ldm + k0 + c], (C)im[(size_t)(k0 + r) * ldm + k0 + c]};
+    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+    A[e] = {(C)re[o], (C)im[o]};
   }
-  for (int e = tid; e < nb * nb; e += blockDim.x) Y[e] = {(C)0, (C)0};
   __syncthreads();
-  cpx<C>* TL = Tinv + (size_t)mat * 2 * nb * nb;
-  cpx<C>* TU = TL + nb * nb;
-  const int j = tid;
-  if (j < kb) {  // column j of inv(L11): forward substitution with unit diagonal
-    Y[j * nb + j] = {(C)1, (C)0};
-    for (int r = j + 1; r < kb; ++r) {
+  if (factor) {
+    double ldacc = 0.0;
+    for (int c = 0; c < kb; ++c) {
+      const cpx<C> d = A[c * kb + c];
+      const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
+      const bool ok = (mag2 > 0.0) && isfinite(mag2);
+      if (tid == 0) {
+        if (!ok) atomicOr(flags, 1);
+        ldacc += 0.5 * log(ok ? mag2 : 1.0);
+      }
+      const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+      for (int r = c + 1 + tid; r < kb; r += NT) A[r * kb + c] = cmul(A[r * kb + c], inv);
+      __syncthreads();
+      const int w = kb - c - 1;
+      for (int e = tid; e < w * w; e += NT) {
+        const int r = c + 1 + e / w, j = c + 1 + e % w;
+        const cpx<C> l = A[r * kb + c], u = A[c * kb + j];
+        A[r * kb + j].re -= l.re * u.re - l.im * u.im;
+        A[r * kb + j].im -= l.re * u.im + l.im * u.re;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) ld[b0 + mat] += ldacc;
+  }
+  // inv(U11) in place: column j gets inv(U[0:j,0:j]) * U[0:j, j] * (-1/u_jj).
+  for (int j = 0; j < kb; ++j) {
+    for (int i = tid; i < j; i += NT) x[i] = A[i * kb + j];
+    __syncthreads();
+    const cpx<C> d = A[j * kb + j];
+    const C m2 = d.re * d.re + d.im * d.im;
+    const cpx<C> dinv = {d.re / m2, -d.im / m2};
+    for (int i = tid; i < j; i += NT) {
       cpx<C> s = {(C)0, (C)0};
-      for (int c = j; c < r; ++c) {
-        const cpx<C> t = cmul(blk[r * kb + c], Y[c * nb + j]);
+      for (int k = i; k < j; ++k) {
+        const cpx<C> t = cmul(A[i * kb + k], x[k]);
         s.re += t.re; s.im += t.im;
       }
-      Y[r * nb + j] = {-s.re, -s.im};
+      const cpx<C> q = cmul(s, dinv);
+      A[i * kb + j] = {-q.re, -q.im};
     }
+    __syncthreads();
+    if (tid == 0) A[j * kb + j] = dinv;
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += blockDim.x) TL[e] = Y[e];
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += blockDim.x) Y[e] = {(C)0, (C)0};
-  __syncthreads();
-  if (j < kb) {  // column j of inv(U11): back substitution
-    {
-      const cpx<C> d = blk[j * kb + j];
-      const C m2 = d.re * d.re + d.im * d.im;
-      Y[j * nb + j] = {d.re / m2, -d.im / m2};
-    }
-    for (int r = j - 1; r >= 0; --r) {
-      cpx<C> s = {(C)0, (C)0};
-      for (int c = r + 1; c <= j; ++c) {
-        const cpx<C> t = cmul(blk[r * kb + c], Y[c * nb + j]);
+  // inv(L11) (unit lower) in place: column j gets -inv(L[j+1:, j+1:]) * L[j+1:, j].
+  for (int j = kb - 2; j >= 0; --j) {
+    for (int i = j + 1 + tid; i < kb; i += NT) x[i] = A[i * kb + j];
+    __syncthreads();
+    for (int i = j + 1 + tid; i < kb; i += NT) {
+      cpx<C> s = x[i];
+      for (int k = j + 1; k < i; ++k) {
+        const cpx<C> t = cmul(A[i * kb + k], x[k]);
         s.re += t.re; s.im += t.im;
       }
-      const cpx<C> d = blk[r * kb + r];
-      const C m2 = d.re * d.re + d.im * d.im;
-      const cpx<C> id = {d.re / m2, -d.im / m2};
-      const cpx<C> q = cmul(s, id);
-      Y[r * nb + j] = {-q.re, -q.im};
+      A[i * kb + j] = {-s.re, -s.im};
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += blockDim.x) TU[e] = Y[e];
+  // T = inv(U11) inv(L11): T_ij = sum_{k >= max(i,j)} Uinv_ik Linv_kj, Linv_jj = 1.
+  cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
+  cpx<C>* Li = T + (size_t)nb * nb;
+  for (int e = tid; e < nb * nb; e += NT) {
+    const int i = e / nb, j = e - i * nb;
+    cpx<C> t = {(C)0, (C)0}, l = {(C)0, (C)0};
+    if (i < kb && j < kb) {
+      if (i <= j) t = A[i * kb + j];  // k = j term (unit diagonal of Linv)
+      for (int k = (i > j + 1 ? i : j + 1); k < kb; ++k) {
+        const cpx<C> p = cmul(A[i * kb + k], A[k * kb + j]);
+        t.re += p.re; t.im += p.im;
+      }
+      if (i > j) l = A[i * kb + j];
+      else if (i == j) l = {(C)1, (C)0};
+    }
+    T[e] = t;
+    Li[e] = l;
+  }
 }
 
 // ---------------------------------------------------------------------- prep
 // Rank-nb factors of one elimination step, written K-contiguous (N x nb, planar):
-//   Gauss-Jordan: F = [ M[i<k0, K] inv(U11) ; -inv(U11) ; M[i>=k0+kb, K] (= L21) ],
-//                 W^T[j] = (inv(L11) M[K, j])^T for j outside K, inv(L11)[:, j-k0] for j in K;
-//   LU:           F = L21 rows only, W^T[j] for j >= k0+kb only.
-// Then M' = mask(M) - F W (mask zeroes row block K and column block K for Gauss-Jordan).
-// With `split`, planes are {re_hi, im_hi, re_lo, im_lo}: hi = value with the low 13
-// mantissa bits cleared (exact TF32), lo = value - hi.
-// W additionally carries -im (hi, lo) in planes 4 and 5 for the tensor-core complex product.
+//   F[i]   = M[i, K] T              (rows outside K; T = inv(M_KK))
+//   F[i]   = M[i, K] inv(L11)       (rows below K after the pivoted panel: M[i, K] = L21)
+//   F[i]   = -T[i - k0]             (rows in K, Gauss-Jordan)
+//   W^T[j] = M[K, j]                (columns outside K)
+//   W^T[j] = e_{j - k0}             (columns in K, Gauss-Jordan)
+// so that M' = mask(M) - F W is one Gauss-Jordan sweep over K (mask zeroes row and column
+// block K) or, restricted to rows and columns past K, the LU Schur complement.
+// With `split`, planes are {re_hi, im_hi, re_lo, im_lo} (hi = value with the low 13 mantissa
+// bits cleared, exact in TF32; lo = value - hi) and W adds {-im_hi, -im_lo}.
 template <typename S>
 __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, double vre, double vim,
                                          bool split, bool neg) {
@@ -296,70 +344,132 @@ __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, doub
   }
 }
 
-template <typename S, typename C, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-    k_prep(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
-           int nb, const cpx<C>* Tinv, S* F, S* W, size_t fw_plane, size_t fw_mat, int gj,
-           int split) {
-  extern __shared__ unsigned char smem_raw[];
-  cpx<C>* T = reinterpret_cast<cpx<C>*>(smem_raw);  // nb x nb
-  const int mat = blockIdx.y, which = blockIdx.z;   // 0: F rows, 1: W rows
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// F: 64 rows x nb columns per CTA, 256 threads, 4 x (nb/16) complex outputs per thread.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256)
+    k_prep_f(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+             int nb, const cpx<C>* Tinv, S* F, size_t fw_plane, size_t fw_mat, int r_begin, int gj,
+             int pivoted, int split) {
+  constexpr int BR = 64;
+  constexpr int KC = sizeof(C) == 8 ? 8 : 16;
+  constexpr int NBMAX = sizeof(C) == 8 ? 64 : 128;
+  constexpr int MAXC = NBMAX / 16;
+  __shared__ C As[2][KC][BR + 1];
+  __shared__ cpx<C> Xs[2][KC][NBMAX];  // [0]: T chunk, [1]: inv(L11) chunk
+  const int mat = blockIdx.y;
+  const int i0 = r_begin + blockIdx.x * BR;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  const cpx<C>* TL = Tinv + (size_t)mat * 2 * nb * nb;
-  const cpx<C>* TU = TL + nb * nb;
-  // F uses inv(U11) as stored ([c'][c]); W uses inv(L11) transposed ([c'][c] = invL[c][c']).
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    if (which == 0) {
-      T[e] = TU[e];
-    } else {
-      const int cp = e / nb, c = e - cp * nb;
-      T[e] = TL[c * nb + cp];
-    }
-  }
-  __syncthreads();
-  S* out = (which == 0 ? F : W) + (size_t)mat * fw_mat;
-  const int row = blockIdx.x * WARPS + warp;
-  if (row >= N) return;
+  const cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
+  const cpx<C>* Li = T + (size_t)nb * nb;
   const int kend = k0 + kb;
-  const size_t obase = (size_t)row * nb;
-  if (!gj && row < kend) return;  // LU: only trailing rows / columns are used
-  for (int c = lane; c < nb; c += 32) {
-    double vre = 0.0, vim = 0.0;
-    if (c < kb) {
-      if (which == 0) {
-        if (row < k0) {
-          cpx<C> s = {(C)0, (C)0};
-          for (int cp = 0; cp < kb; ++cp) {
-            const cpx<C> x = {(C)re[(size_t)row * ldm + k0 + cp], (C)im[(size_t)row * ldm + k0 + cp]};
-            const cpx<C> t = cmul(x, T[cp * nb + c]);
-            s.re += t.re; s.im += t.im;
+  const int ncg = (nb + 15) / 16;  // column groups per thread
+  C ar[4][MAXC], ai[4][MAXC];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) { ar[a][q] = 0; ai[a][q] = 0; }
+  bool useL[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) useL[a] = pivoted && (i0 + ty + 16 * a) >= kend;
+  for (int kc = 0; kc < kb; kc += KC) {
+    for (int e = threadIdx.x; e < BR * KC; e += 256) {
+      const int r = e / KC, k = e - r * KC;
+      const int gi = i0 + r;
+      const bool in = gi < N && (kc + k) < kb;
+      As[0][k][r] = in ? (C)re[(size_t)gi * ldm + k0 + kc + k] : (C)0;
+      As[1][k][r] = in ? (C)im[(size_t)gi * ldm + k0 + kc + k] : (C)0;
+    }
+    for (int e = threadIdx.x; e < KC * nb; e += 256) {
+      const int k = e / nb, c = e - k * nb;
+      const bool in = (kc + k) < kb;
+      Xs[0][k][c] = in ? T[(size_t)(kc + k) * nb + c] : cpx<C>{(C)0, (C)0};
+      Xs[1][k][c] = (in && pivoted) ? Li[(size_t)(kc + k) * nb + c] : cpx<C>{(C)0, (C)0};
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KC; ++k) {
+      C fr[4], fi[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { fr[a] = As[0][k][ty + 16 * a]; fi[a] = As[1][k][ty + 16 * a]; }
+#pragma unroll
+      for (int q = 0; q < MAXC; ++q) {
+        if (q < ncg) {
+          const cpx<C> xt = Xs[0][k][tx + 16 * q];
+          const cpx<C> xl = Xs[1][k][tx + 16 * q];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const cpx<C> xv = useL[a] ? xl : xt;
+            ar[a][q] = fma(fr[a], xv.re, ar[a][q]);
+            ar[a][q] = fma(-fi[a], xv.im, ar[a][q]);
+            ai[a][q] = fma(fr[a], xv.im, ai[a][q]);
+            ai[a][q] = fma(fi[a], xv.re, ai[a][q]);
           }
-          vre = (double)s.re; vim = (double)s.im;
-        } else if (row < kend) {
-          const cpx<C> t = T[(row - k0) * nb + c];
-          vre = -(double)t.re; vim = -(double)t.im;
-        } else {
-          vre = (double)re[(size_t)row * ldm + k0 + c];
-          vim = (double)im[(size_t)row * ldm + k0 + c];
-        }
-      } else {
-        if (row >= k0 && row < kend) {
-          const cpx<C> t = T[(row - k0) * nb + c];  // invL[c][row-k0]
-          vre = (double)t.re; vim = (double)t.im;
-        } else {
-          cpx<C> s = {(C)0, (C)0};
-          for (int cp = 0; cp < kb; ++cp) {
-            const cpx<C> x = {(C)re[(size_t)(k0 + cp) * ldm + row], (C)im[(size_t)(k0 + cp) * ldm + row]};
-            const cpx<C> t = cmul(T[cp * nb + c], x);
-            s.re += t.re; s.im += t.im;
-          }
-          vre = (double)s.re; vim = (double)s.im;
         }
       }
     }
-    store_fw(out, fw_plane, obase + c, vre, vim, split != 0, which == 1);
+    __syncthreads();
+  }
+  S* out = F + (size_t)mat * fw_mat;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= N) continue;
+    const bool ink = gj && i >= k0 && i < kend;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+      if (q >= ncg) continue;
+      const int c = tx + 16 * q;
+      if (c >= nb) continue;
+      double vr, vi;
+      if (c >= kb) {
+        vr = 0.0; vi = 0.0;
+      } else if (ink) {
+        const cpx<C> t = T[(size_t)(i - k0) * nb + c];
+        vr = -(double)t.re; vi = -(double)t.im;
+      } else {
+        vr = (double)ar[a][q]; vi = (double)ai[a][q];
+      }
+      store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split != 0, false);
+    }
+  }
+}
+
+// W^T: 64 columns j x nb per CTA, transposed through shared memory.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_prep_w(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+             int nb, S* W, size_t fw_plane, size_t fw_mat, int c_begin, int gj, int split) {
+  extern __shared__ unsigned char smem_raw[];
+  S* tr = reinterpret_cast<S*>(smem_raw);  // [nb][65]
+  S* ti = tr + (size_t)nb * 65;
+  const int mat = blockIdx.y;
+  const int j0 = c_begin + blockIdx.x * 64;
+  const S* re = M + mat * mat_stride;
+  const S* im = re + plane_stride;
+  for (int e = threadIdx.x; e < nb * 64; e += 256) {
+    const int c = e >> 6, jj = e & 63;
+    const int j = j0 + jj;
+    const bool in = c < kb && j < N;
+    tr[c * 65 + jj] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
+    ti[c * 65 + jj] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+  }
+  __syncthreads();
+  S* out = W + (size_t)mat * fw_mat;
+  for (int e = threadIdx.x; e < nb * 64; e += 256) {
+    const int jj = e / nb, c = e - jj * nb;
+    const int j = j0 + jj;
+    if (j >= N) continue;
+    double vr, vi;
+    if (gj && j >= k0 && j < k0 + kb) {
+      vr = (c == j - k0) ? 1.0 : 0.0;
+      vi = 0.0;
+    } else {
+      vr = (double)tr[c * 65 + jj];
+      vi = (double)ti[c * 65 + jj];
+    }
+    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split != 0, true);
   }
 }
 
@@ -435,11 +545,13 @@ __global__ void __launch_bounds__(256)
 }
 
 // -------------------------------------------------------------------- refine
-// Per block and row i: x = row i of X = A^{-1} (X[i, perm[r]] = R[i, r]), then
-//   G_ii = 2 x_i - sum_j x_j (A x)_j   (refine; (A x)_j from the 5-point stencil in float64)
+// Adjoint diag(G).  Per block and row i: x = row i of X = A^{-1} (X[i, perm[r]] = R[i, r]),
+//   G_ii = 2 x_i - sum_j x_j (A x)_j   (refine: (A x)_j from the 5-point stencil in float64)
 //   G_ii = x_i                          (no refinement)
-// and gd[b*N + i] = sigma_b Re G_ii.  Refinement: one warp per row, the row scattered into
-// natural order in shared memory.  Without refinement: one thread per row reads R[i, pinv[i]].
+// and gd[b*N + i] = sigma_b Re G_ii.  With refinement: one warp per row, the row scattered
+// into natural order in shared memory, lanes walking the lattice column y, the stencil
+// diagonal a_jj = mu - h_j + i w_n cached per CTA.  Without: one thread per row reads
+// R[i, pinv[i]].
 template <typename S>
 __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
                          Lattice la, const int* perm, double* gd, int refine) {
@@ -457,27 +569,36 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
       gd[(size_t)b * N + i] = sg * (double)re[(size_t)i * ldm + sperm[i]];
     return;
   }
-  cpx<S>* rows = reinterpret_cast<cpx<S>*>(smem_raw + ((N * sizeof(int) + 15) / 16) * 16);
+  const size_t perm_bytes = ((N * sizeof(int) + 15) / 16) * 16;
+  double* diag = reinterpret_cast<double*>(smem_raw + perm_bytes);  // N: Re a_jj
+  cpx<S>* rows = reinterpret_cast<cpx<S>*>(smem_raw + perm_bytes + (size_t)N * sizeof(double));
   cpx<S>* x = rows + (size_t)warp * N;
-  for (int r = threadIdx.x; r < N; r += blockDim.x) sperm[r] = perm[(size_t)mat * N + r];
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    sperm[r] = perm[(size_t)mat * N + r];
+    diag[r] = la.mu - site_energy(la, r, sg);
+  }
   __syncthreads();
-  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const double w = (2.0 * n + 1.0) * kPi * la.T, t = la.t;
   for (int i = blockIdx.x * nwarps + warp; i < N; i += gridDim.x * nwarps) {
     for (int r = lane; r < N; r += 32)
       x[sperm[r]] = {re[(size_t)i * ldm + r], im[(size_t)i * ldm + r]};
     __syncwarp();
     double ar = 0.0, ai = 0.0;
-    for (int j = lane; j < N; j += 32) {
-      const int xx = j / L, yy = j - xx * L;
-      const int jxp = ((xx + 1) % L) * L + yy, jxm = ((xx + L - 1) % L) * L + yy;
-      const int jyp = xx * L + (yy + 1) % L, jym = xx * L + (yy + L - 1) % L;
-      const double dr = la.mu - site_energy(la, j, sg), di = w;  // A_jj
-      const double xjr = (double)x[j].re, xji = (double)x[j].im;
-      double yr = dr * xjr - di * xji, yi = dr * xji + di * xjr;  // (A x)_j
-      yr += la.t * ((double)x[jxp].re + (double)x[jxm].re + (double)x[jyp].re + (double)x[jym].re);
-      yi += la.t * ((double)x[jxp].im + (double)x[jxm].im + (double)x[jyp].im + (double)x[jym].im);
-      ar += xjr * yr - xji * yi;
-      ai += xjr * yi + xji * yr;
+    for (int y = lane; y < L; y += 32) {
+      const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+      for (int xx = 0; xx < L; ++xx) {
+        const int xp = (xx + 1 == L) ? 0 : xx + 1, xm = (xx == 0) ? L - 1 : xx - 1;
+        const int j = xx * L + y;
+        const cpx<S> vj = x[j], v1 = x[xp * L + y], v2 = x[xm * L + y];
+        const cpx<S> v3 = x[xx * L + yp], v4 = x[xx * L + ym];
+        const double dr = diag[j];
+        const double xjr = (double)vj.re, xji = (double)vj.im;
+        double yr = dr * xjr - w * xji, yi = dr * xji + w * xjr;  // a_jj x_j
+        yr += t * ((double)v1.re + (double)v2.re + (double)v3.re + (double)v4.re);
+        yi += t * ((double)v1.im + (double)v2.im + (double)v3.im + (double)v4.im);
+        ar += xjr * yr - xji * yi;
+        ai += xjr * yi + xji * yr;
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -598,10 +719,11 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int cnt, cudaStre
   const size_t perm_bytes = ((N * sizeof(int) + 15) / 16) * 16;
   prof_begin(e, kRefine, s);
   if (e.refine) {
+    const size_t fixed = perm_bytes + (size_t)N * sizeof(double);
     const size_t row_bytes = (size_t)N * sizeof(cpx<S>);
-    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (kRefineSmem - perm_bytes) / row_bytes));
-    const int gx = std::max(1, std::min((N + warps - 1) / warps, 64));
-    k_refine<S><<<dim3(gx, cnt), warps * 32, perm_bytes + warps * row_bytes, s>>>(
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (kRefineSmem - fixed) / row_bytes));
+    const int gx = std::max(1, std::min((N + warps - 1) / warps, 32));
+    k_refine<S><<<dim3(gx, cnt), warps * 32, fixed + warps * row_bytes, s>>>(
         M, e.ldm, e.mat_stride, e.plane_stride, b0, la, e.perm, e.gd, 1);
   } else {
     const int gx = std::max(1, std::min((N + 255) / 256, 16));
@@ -613,15 +735,83 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int cnt, cudaStre
   return SCA_OK;
 }
 
+// One group of blocks (workspace slots m0 .. m0+cnt-1, global indices b0 ..) through all
+// elimination steps.  pivoted: partial pivoting with the shared-memory panel of width nb;
+// otherwise the blocks are diagonally dominant and only the pivot block is factorised.
+template <typename S, typename C>
+sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, bool tcg,
+                     bool want_grad, cudaStream_t s) {
+  const int N = e.N;
+  S* M = static_cast<S*>(e.M) + (size_t)m0 * e.mat_stride;
+  S* F = static_cast<S*>(e.F) + (size_t)m0 * e.fw_mat;
+  S* W = static_cast<S*>(e.W) + (size_t)m0 * e.fw_mat;
+  cpx<C>* Tinv = static_cast<cpx<C>*>(e.Tinv) + (size_t)m0 * 2 * e.nb * e.nb;
+  int* piv = e.piv + (size_t)m0 * N;
+  int* perm = e.perm + (size_t)m0 * N;
+  const size_t fw_plane = (size_t)N * nb;
+  const int split = tcg ? 1 : 0;
+  for (int k0 = 0; k0 < N; k0 += nb) {
+    const int kb = std::min(nb, N - k0);
+    const int kend = k0 + kb;
+    if (pivoted) {
+      const size_t sm = sizeof(cpx<C>) * (size_t)(N - k0) * kb;
+      prof_begin(e, kPanel, s);
+      k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
+                                                    k0, kb, b0, e.ld, piv, perm, e.flags);
+      prof_end(e, kPanel, s);
+      SCA_LAUNCH_CHECK("panel");
+      if (!want_grad && kend == N) break;
+      const int jstart = want_grad ? 0 : kend;
+      const int ncols = N - jstart;
+      prof_begin(e, kSwap, s);
+      k_swap<S><<<dim3((ncols + 255) / 256, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
+                                                                 e.plane_stride, k0, kb, jstart, piv);
+      prof_end(e, kSwap, s);
+      SCA_LAUNCH_CHECK("swap");
+    }
+    {
+      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * kb + kb);
+      prof_begin(e, pivoted ? kTrinv : kPanel, s);
+      k_diag_inv<S, C, 512><<<cnt, 512, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
+                                                  nb, b0, e.ld, Tinv, pivoted ? 0 : 1, e.flags);
+      prof_end(e, pivoted ? kTrinv : kPanel, s);
+      SCA_LAUNCH_CHECK("diag");
+    }
+    if (!want_grad && kend == N) break;  // LU: nothing trails the last pivot block
+    const int r0 = want_grad ? 0 : kend, c0 = want_grad ? 0 : kend;
+    {
+      prof_begin(e, kPrep, s);
+      k_prep_f<S, C><<<dim3((N - r0 + 63) / 64, cnt), 256, 0, s>>>(
+          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, fw_plane, e.fw_mat, r0,
+          want_grad ? 1 : 0, pivoted ? 1 : 0, split);
+      const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
+      k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
+          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
+          want_grad ? 1 : 0, split);
+      prof_end(e, kPrep, s);
+      SCA_LAUNCH_CHECK("prep");
+    }
+    prof_begin(e, kUpdate, s);
+    if (tcg) {
+      sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s);
+      if (st != SCA_OK) return st;
+    } else {
+      dim3 grid((N - c0 + 63) / 64, (N - r0 + 63) / 64, cnt);
+      k_update_simt<S><<<grid, 256, 0, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, F, W, nb,
+                                            fw_plane, e.fw_mat, r0, c0, k0, kb, want_grad ? 1 : 0);
+      SCA_LAUNCH_CHECK("update");
+    }
+    prof_end(e, kUpdate, s);
+  }
+  return SCA_OK;
+}
+
 template <typename S, typename C>
 sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool refine_stage,
                         cudaStream_t s) {
   const Lattice la = make_lattice(e, d_phi);
-  const int N = e.N, nb = e.nb;
+  const int N = e.N;
   S* M = static_cast<S*>(e.M);
-  S* F = static_cast<S*>(e.F);
-  S* W = static_cast<S*>(e.W);
-  cpx<C>* Tinv = static_cast<cpx<C>*>(e.Tinv);
   cudaError_t err = cudaMemsetAsync(e.flags, 0, sizeof(int), s);
   if (err != cudaSuccess) return cuda_fail(err, "flags reset");
   for (int b0 = 0; b0 < e.B; b0 += e.chunk) {
@@ -631,60 +821,28 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
                                                e.ld, e.perm);
     prof_end(e, kAssemble, s);
     SCA_LAUNCH_CHECK("assemble");
-    for (int k0 = 0; k0 < N; k0 += nb) {
-      const int kb = std::min(nb, N - k0);
-      const int kend = k0 + kb;
-      prof_begin(e, kPanel, s);
-      k_panel<S, C, 256><<<cnt, 256, 0, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
-                                             b0, e.ld, e.piv, e.perm, e.flags);
-      prof_end(e, kPanel, s);
-      SCA_LAUNCH_CHECK("panel");
-      if (!want_grad && kend == N) break;  // LU: nothing trails the last panel
-      const int jstart = want_grad ? 0 : kend;
-      {
-        const int ncols = N - jstart;
-        prof_begin(e, kSwap, s);
-        k_swap<S><<<dim3((ncols + 255) / 256, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
-                                                                   e.plane_stride, k0, kb,
-                                                                   jstart, e.piv);
-        prof_end(e, kSwap, s);
-        SCA_LAUNCH_CHECK("swap");
-      }
-      {
-        const size_t sm = sizeof(cpx<C>) * ((size_t)kb * kb + (size_t)nb * nb);
-        prof_begin(e, kTrinv, s);
-        k_trinv<S, C><<<cnt, nb, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb,
-                                          Tinv);
-        prof_end(e, kTrinv, s);
-        SCA_LAUNCH_CHECK("trinv");
-      }
-      {
-        constexpr int WARPS = 8;
-        const size_t sm = sizeof(cpx<C>) * (size_t)nb * nb;
-        prof_begin(e, kPrep, s);
-        k_prep<S, C, WARPS><<<dim3((N + WARPS - 1) / WARPS, cnt, 2), WARPS * 32, sm, s>>>(
-            M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, W, e.fw_plane,
-            e.fw_mat, want_grad ? 1 : 0, e.tc ? 1 : 0);
-        prof_end(e, kPrep, s);
-        SCA_LAUNCH_CHECK("prep");
-      }
-      const int r0 = want_grad ? 0 : kend, c0 = want_grad ? 0 : kend;
-      prof_begin(e, kUpdate, s);
-      if (e.tc) {
-        sca_status st = tc_update(e, cnt, k0, kb, r0, c0, want_grad, s);
-        if (st != SCA_OK) return st;
-      } else {
-        dim3 grid((N - c0 + 63) / 64, (N - r0 + 63) / 64, cnt);
-        k_update_simt<S><<<grid, 256, 0, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, F, W, nb,
-                                              e.fw_plane, e.fw_mat, r0, c0, k0, kb,
-                                              want_grad ? 1 : 0);
-        SCA_LAUNCH_CHECK("update");
-      }
-      prof_end(e, kUpdate, s);
+    // blocks [0, piv_blocks) need pivoting (lowest frequencies), the rest are dominant
+    const int np = std::max(0, std::min(cnt, e.piv_blocks - b0));
+    const int nd = cnt - np;
+    const bool fork = np > 0 && nd > 0 && e.side != nullptr;
+    cudaStream_t sp = s;
+    if (fork) {
+      if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess) return cuda_fail(err, "fork");
+      if ((err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "fork");
+      sp = e.side;
+    }
+    sca_status st;
+    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb_piv, false, want_grad, sp)) != SCA_OK)
+      return st;
+    if (nd > 0 && (st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s)) != SCA_OK)
+      return st;
+    if (fork) {
+      if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "join");
+      if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "join");
     }
     if (want_grad && refine_stage) {
-      sca_status st = launch_refine<S>(e, la, b0, cnt, s);
-      if (st != SCA_OK) return st;
+      sca_status st2 = launch_refine<S>(e, la, b0, cnt, s);
+      if (st2 != SCA_OK) return st2;
     }
   }
   return SCA_OK;
@@ -695,9 +853,12 @@ sca_status set_smem_limits() {
   static bool done = false;
   if (done) return SCA_OK;
   cudaError_t err;
-  err = cudaFuncSetAttribute(k_trinv<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (err != cudaSuccess) return cuda_fail(err, "smem trinv");
-  err = cudaFuncSetAttribute(k_prep<S, C, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const int lim = 200 * 1024 + 1024;
+  err = cudaFuncSetAttribute(k_panel_smem<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (err != cudaSuccess) return cuda_fail(err, "smem panel");
+  err = cudaFuncSetAttribute(k_diag_inv<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (err != cudaSuccess) return cuda_fail(err, "smem diag");
+  err = cudaFuncSetAttribute(k_prep_w<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (err != cudaSuccess) return cuda_fail(err, "smem prep");
   err = cudaFuncSetAttribute(k_refine<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRefineSmem);
   if (err != cudaSuccess) return cuda_fail(err, "smem refine");

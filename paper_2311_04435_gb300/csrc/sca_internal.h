@@ -24,7 +24,9 @@ sca_status cuda_fail(cudaError_t e, const char* where);
 struct Engine {
   sca_params p{};
   int L = 0, N = 0, B = 0;
-  int nb = 0;            // Gauss-Jordan / LU block width
+  int nb = 0;            // Gauss-Jordan / LU block width (diagonally dominant blocks)
+  int nb_piv = 0;        // block width of the pivoted group (shared-memory panel)
+  int piv_blocks = 0;    // blocks b < piv_blocks need partial pivoting (omega_n <= 4|t|)
   int ldm = 0;           // row stride of a block plane (elements)
   int chunk = 0;         // blocks resident at once
   bool fp64 = false;     // storage and arithmetic of the blocks
@@ -54,6 +56,8 @@ struct Engine {
   void* tmap = nullptr;         // host-side tensor-map storage (tc path)
   size_t bytes = 0;
   struct Profiler* prof = nullptr;  // per-kernel event timing (sca_profile_enable)
+  cudaStream_t side = nullptr;      // stream of the pivoted group (runs beside the rest)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Kernel kinds for per-launch timing.
@@ -109,6 +113,7 @@ sca_status run_seed_phi(double* d_phi, int N, uint64_t seed, cudaStream_t s);
 bool tc_supported();
 sca_status tc_prepare(Engine& e);
 void tc_release(Engine& e);
-sca_status tc_update(Engine& e, int cnt, int k0, int kb, int r0, int c0, bool gj, cudaStream_t s);
+sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
+                     cudaStream_t s);
 
 }  // namespace sca

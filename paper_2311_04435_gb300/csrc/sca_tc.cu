@@ -161,6 +161,7 @@ struct TcArgs {
   int k0, kb, gj;                      // masked block K (Gauss-Jordan)
   int tiles_m, tiles_n, tiles;         // per block, and total
   int fplanes, wplanes;                // planes per block in the F / W tensor maps
+  int mat0;                            // workspace slot of the first block
   int* err;                            // device error word (bit 1: wait time-out)
 };
 
@@ -226,10 +227,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* st = smem + stage * kStageBytes;
           for (int s = 0; s < 4; ++s)
             tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKS, frow,
-                        mat * a.fplanes + kFPlaneOfSlot[s]);
+                        (a.mat0 + mat) * a.fplanes + kFPlaneOfSlot[s]);
           for (int s = 0; s < 6; ++s)
             tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKS, wrow,
-                        mat * a.wplanes + kWPlaneOfSlot[s]);
+                        (a.mat0 + mat) * a.wplanes + kWPlaneOfSlot[s]);
           last_parity[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1; }
         }
@@ -445,14 +446,16 @@ void tc_release(Engine& e) {
   e.tmap = nullptr;
 }
 
-sca_status tc_update(Engine& e, int cnt, int k0, int kb, int r0, int c0, bool gj, cudaStream_t s) {
+sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
+                     cudaStream_t s) {
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
   if (!t) {
     set_error("tcgen05 update used before tc_prepare");
     return SCA_ENOSTATE;
   }
   TcArgs a;
-  a.M = static_cast<float*>(e.M);
+  a.M = static_cast<float*>(e.M) + (size_t)m0 * e.mat_stride;
+  a.mat0 = m0;
   a.N = e.N;
   a.ldm = e.ldm;
   a.mat_stride = (long long)e.mat_stride;

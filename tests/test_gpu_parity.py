@@ -208,3 +208,22 @@ def test_forward_backward_entry_points():
         assert np.allclose(g.cpu().numpy(), g2, rtol=1e-12, atol=1e-14)
         with pytest.raises(Exception, match="SCA_ENOSTATE"):
             c.backward_dev(x, g)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pivot_free_blocks_match_forced_pivoting(prec, monkeypatch):
+    """Blocks with omega_n > 4|t| skip the pivot search (column diagonal dominance makes
+    partial pivoting keep the diagonal); forcing the pivoted panel on every block must give
+    the same results within rounding."""
+    p = api.Params(12, 10, U=4.0, T=0.1, delta=0.6, prec=prec)  # 6 pivoted + 14 dominant blocks
+    phi = inputs.random_phi(33, p.N)
+    with api.Context(p) as c:
+        ld_a, gd_a = c.blocks(phi)
+    monkeypatch.setenv("SCA_PIVOT_ALL", "1")
+    with api.Context(p) as c:
+        ld_b, gd_b = c.blocks(phi)
+    t = tol(prec)
+    assert np.allclose(ld_a, ld_b, rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(gd_a - gd_b)) <= t["g"] * max(1.0, np.abs(gd_b).max())
+    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, list(range(2 * p.n_omega)))
+    assert np.allclose(ld_a, o_ld, rtol=t["ld"], atol=t["ld"])
