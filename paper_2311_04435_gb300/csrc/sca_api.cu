@@ -90,10 +90,11 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.piv_blocks = 2 * n_piv;
   if (const char* v = std::getenv("SCA_PIVOT_ALL"))
     if (std::atoi(v) != 0) e.piv_blocks = e.B;
-  // Width of the pivoted group's shared-memory panel: N x nb_piv complex values <= 200 KB.
+  // Width of the pivoted group's shared-memory panel: N x (nb_piv + 1) complex values
+  // (rows padded by one) within 224 KB.
   const size_t cbytes = e.fp64 ? 16 : 8;
   int nbp = 1;
-  while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2) * cbytes <= 200 * 1024) nbp *= 2;
+  while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2 + 1) * cbytes <= 224 * 1024) nbp *= 2;
   e.nb_piv = nbp;
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;

@@ -54,8 +54,10 @@ __device__ __forceinline__ double site_energy(const Lattice& la, int i, int sg) 
 }
 
 // ------------------------------------------------------------------ assemble
-// A_b = (i w_n + mu) I - H_sigma(phi), b = 2n + s (Eq. 1 hopping +t off-diagonal per bond,
-// accumulated; diagonal mu - h_i + i w_n with h_i = eps_i - sigma phi_i).
+// A_b = (i w_n + mu) I - H_sigma(phi), b = 2n + s (Eq. 1 hopping: +t off-diagonal per bond,
+// accumulated; diagonal mu - h_i + i w_n with h_i = eps_i - sigma phi_i).  The blocks are
+// zero-filled with cudaMemsetAsync first; this kernel writes the stencil entries of each
+// row, one thread per row.
 template <typename S>
 __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
                            Lattice la, double* ld, int* perm) {
@@ -64,26 +66,22 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
   const double w = (2.0 * n + 1.0) * kPi * la.T;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
-  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
     const int x = i / L, y = i - x * L;
     const int jxp = ((x + 1) % L) * L + y, jxm = ((x + L - 1) % L) * L + y;
     const int jyp = x * L + (y + 1) % L, jym = x * L + (y + L - 1) % L;
-    const double h = site_energy(la, i, sg);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      double v = 0.0, q = 0.0;
-      if (j == jxp) v += la.t;
-      if (j == jxm) v += la.t;
-      if (j == jyp) v += la.t;
-      if (j == jym) v += la.t;
-      if (j == i) { v = la.mu - h; q = w; }
-      re[(size_t)i * ldm + j] = (S)v;
-      im[(size_t)i * ldm + j] = (S)q;
-    }
+    const size_t row = (size_t)i * ldm;
+    // bonds accumulate: for L = 2 the +x and -x neighbours are the same site
+    re[row + jxp] += (S)la.t;
+    re[row + jxm] += (S)la.t;
+    re[row + jyp] += (S)la.t;
+    re[row + jym] += (S)la.t;
+    re[row + i] = (S)(la.mu - site_energy(la, i, sg));
+    im[row + i] = (S)w;
+    perm[(size_t)mat * N + i] = i;
   }
-  if (blockIdx.x == 0) {
-    for (int r = threadIdx.x; r < N; r += blockDim.x) perm[(size_t)mat * N + r] = r;
-    if (threadIdx.x == 0) ld[b] = 0.0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
 }
 
 // ---------------------------------------------------------------------- swap
@@ -121,7 +119,8 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
                                                    size_t plane_stride, int k0, int kb, int b0,
                                                    double* ld, int* piv, int* perm, int* flags) {
   extern __shared__ unsigned char smem_raw[];
-  cpx<C>* P = reinterpret_cast<cpx<C>*>(smem_raw);  // m x kb, row-major
+  cpx<C>* P = reinterpret_cast<cpx<C>*>(smem_raw);  // m x (kb+1), row-major, padded
+  const int ps = kb + 1;  // odd row stride: conflict-free column access
   __shared__ double red_v[NT / 32];
   __shared__ int red_i[NT / 32];
   __shared__ int s_p;
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   for (int e = tid; e < m * kb; e += NT) {
     const int r = e / kb, c = e - r * kb;
     const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    P[e] = {(C)re[o], (C)im[o]};
+    P[r * ps + c] = {(C)re[o], (C)im[o]};
   }
   __syncthreads();
   double ldacc = 0.0;
@@ -140,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     double best = -1.0;
     int bi = m;
     for (int r = c + tid; r < m; r += NT) {
-      const cpx<C> z = P[r * kb + c];
+      const cpx<C> z = P[r * ps + c];
       const double v = (double)z.re * z.re + (double)z.im * z.im;
       if (v > best) { best = v; bi = r; }
     }
@@ -167,9 +166,9 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     const int p = s_p;
     if (p != c)
       for (int j = tid; j < kb; j += NT) {
-        const cpx<C> t = P[c * kb + j];
-        P[c * kb + j] = P[p * kb + j];
-        P[p * kb + j] = t;
+        const cpx<C> t = P[c * ps + j];
+        P[c * ps + j] = P[p * ps + j];
+        P[p * ps + j] = t;
       }
     if (tid == 0) {
       piv[(size_t)mat * N + k0 + c] = k0 + p;
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
       }
     }
     __syncthreads();
-    const cpx<C> d = P[c * kb + c];
+    const cpx<C> d = P[c * ps + c];
     const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
     const bool ok = (mag2 > 0.0) && isfinite(mag2);
     if (tid == 0) {
@@ -190,12 +189,12 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     }
     const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
     for (int r = c + 1 + tid; r < m; r += NT) {
-      const cpx<C> l = cmul(P[r * kb + c], inv);
-      P[r * kb + c] = l;
+      const cpx<C> l = cmul(P[r * ps + c], inv);
+      P[r * ps + c] = l;
       for (int j = c + 1; j < kb; ++j) {
-        const cpx<C> u = P[c * kb + j];
-        P[r * kb + j].re -= l.re * u.re - l.im * u.im;
-        P[r * kb + j].im -= l.re * u.im + l.im * u.re;
+        const cpx<C> u = P[c * ps + j];
+        P[r * ps + j].re -= l.re * u.re - l.im * u.im;
+        P[r * ps + j].im -= l.re * u.im + l.im * u.re;
       }
     }
     __syncthreads();
@@ -203,8 +202,8 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   for (int e = tid; e < m * kb; e += NT) {
     const int r = e / kb, c = e - r * kb;
     const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    re[o] = (S)P[e].re;
-    im[o] = (S)P[e].im;
+    re[o] = (S)P[r * ps + c].re;
+    im[o] = (S)P[r * ps + c].im;
   }
   if (tid == 0) ld[b0 + mat] += ldacc;
 }
@@ -222,21 +221,22 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
                                                  int b0, double* ld, cpx<C>* Tinv, int factor,
                                                  int* flags) {
   extern __shared__ unsigned char smem_raw[];
-  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
-  cpx<C>* x = A + kb * kb;                           // kb scratch column
+  const int as = kb + 1;                            // odd row stride (bank-conflict free)
+  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x (kb+1)
+  cpx<C>* x = A + kb * as;                           // kb scratch column
   const int mat = blockIdx.x, tid = threadIdx.x;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
   for (int e = tid; e < kb * kb; e += NT) {
     const int r = e / kb, c = e - r * kb;
     const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    A[e] = {(C)re[o], (C)im[o]};
+    A[r * as + c] = {(C)re[o], (C)im[o]};
   }
   __syncthreads();
   if (factor) {
     double ldacc = 0.0;
     for (int c = 0; c < kb; ++c) {
-      const cpx<C> d = A[c * kb + c];
+      const cpx<C> d = A[c * as + c];
       const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
       const bool ok = (mag2 > 0.0) && isfinite(mag2);
       if (tid == 0) {
@@ -244,14 +244,14 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
         ldacc += 0.5 * log(ok ? mag2 : 1.0);
       }
       const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
-      for (int r = c + 1 + tid; r < kb; r += NT) A[r * kb + c] = cmul(A[r * kb + c], inv);
+      for (int r = c + 1 + tid; r < kb; r += NT) A[r * as + c] = cmul(A[r * as + c], inv);
       __syncthreads();
       const int w = kb - c - 1;
       for (int e = tid; e < w * w; e += NT) {
         const int r = c + 1 + e / w, j = c + 1 + e % w;
-        const cpx<C> l = A[r * kb + c], u = A[c * kb + j];
-        A[r * kb + j].re -= l.re * u.re - l.im * u.im;
-        A[r * kb + j].im -= l.re * u.im + l.im * u.re;
+        const cpx<C> l = A[r * as + c], u = A[c * as + j];
+        A[r * as + j].re -= l.re * u.re - l.im * u.im;
+        A[r * as + j].im -= l.re * u.im + l.im * u.re;
       }
       __syncthreads();
     }
@@ -259,35 +259,35 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
   }
   // inv(U11) in place: column j gets inv(U[0:j,0:j]) * U[0:j, j] * (-1/u_jj).
   for (int j = 0; j < kb; ++j) {
-    for (int i = tid; i < j; i += NT) x[i] = A[i * kb + j];
+    for (int i = tid; i < j; i += NT) x[i] = A[i * as + j];
     __syncthreads();
-    const cpx<C> d = A[j * kb + j];
+    const cpx<C> d = A[j * as + j];
     const C m2 = d.re * d.re + d.im * d.im;
     const cpx<C> dinv = {d.re / m2, -d.im / m2};
     for (int i = tid; i < j; i += NT) {
       cpx<C> s = {(C)0, (C)0};
       for (int k = i; k < j; ++k) {
-        const cpx<C> t = cmul(A[i * kb + k], x[k]);
+        const cpx<C> t = cmul(A[i * as + k], x[k]);
         s.re += t.re; s.im += t.im;
       }
       const cpx<C> q = cmul(s, dinv);
-      A[i * kb + j] = {-q.re, -q.im};
+      A[i * as + j] = {-q.re, -q.im};
     }
     __syncthreads();
-    if (tid == 0) A[j * kb + j] = dinv;
+    if (tid == 0) A[j * as + j] = dinv;
     __syncthreads();
   }
   // inv(L11) (unit lower) in place: column j gets -inv(L[j+1:, j+1:]) * L[j+1:, j].
   for (int j = kb - 2; j >= 0; --j) {
-    for (int i = j + 1 + tid; i < kb; i += NT) x[i] = A[i * kb + j];
+    for (int i = j + 1 + tid; i < kb; i += NT) x[i] = A[i * as + j];
     __syncthreads();
     for (int i = j + 1 + tid; i < kb; i += NT) {
       cpx<C> s = x[i];
       for (int k = j + 1; k < i; ++k) {
-        const cpx<C> t = cmul(A[i * kb + k], x[k]);
+        const cpx<C> t = cmul(A[i * as + k], x[k]);
         s.re += t.re; s.im += t.im;
       }
-      A[i * kb + j] = {-s.re, -s.im};
+      A[i * as + j] = {-s.re, -s.im};
     }
     __syncthreads();
   }
@@ -298,16 +298,79 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
     const int i = e / nb, j = e - i * nb;
     cpx<C> t = {(C)0, (C)0}, l = {(C)0, (C)0};
     if (i < kb && j < kb) {
-      if (i <= j) t = A[i * kb + j];  // k = j term (unit diagonal of Linv)
+      if (i <= j) t = A[i * as + j];  // k = j term (unit diagonal of Linv)
       for (int k = (i > j + 1 ? i : j + 1); k < kb; ++k) {
-        const cpx<C> p = cmul(A[i * kb + k], A[k * kb + j]);
+        const cpx<C> p = cmul(A[i * as + k], A[k * as + j]);
         t.re += p.re; t.im += p.im;
       }
-      if (i > j) l = A[i * kb + j];
+      if (i > j) l = A[i * as + j];
       else if (i == j) l = {(C)1, (C)0};
     }
     T[e] = t;
     Li[e] = l;
+  }
+}
+
+// ------------------------------------------------------- dominant pivot block
+// T = inv(M_KK) for a strictly diagonally dominant pivot block (no interchanges needed, see
+// k_diag_inv) by in-place Gauss-Jordan in shared memory: kb sweeps, each updating the whole
+// kb x kb block in parallel.  ld[b] += sum ln|pivot| (the pivots of the LU).  Writes T to
+// Tinv slot 0 (nb x nb, zero padded).
+template <typename S, typename C, int NT>
+__global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_stride,
+                                                size_t plane_stride, int k0, int kb, int nb,
+                                                int b0, double* ld, cpx<C>* Tinv, int* flags) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
+  cpx<C>* prow = A + kb * kb;                        // scaled pivot row
+  cpx<C>* pcol = prow + kb;                          // pivot column
+  __shared__ cpx<C> s_dinv;
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const S* re = M + mat * mat_stride;
+  const S* im = re + plane_stride;
+  for (int e = tid; e < kb * kb; e += NT) {
+    const int r = e / kb, c = e - r * kb;
+    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+    A[e] = {(C)re[o], (C)im[o]};
+  }
+  __syncthreads();
+  double ldacc = 0.0;
+  for (int c = 0; c < kb; ++c) {
+    if (tid == 0) {
+      const cpx<C> d = A[c * kb + c];
+      const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
+      const bool ok = (mag2 > 0.0) && isfinite(mag2);
+      if (!ok) atomicOr(flags, 1);
+      ldacc += 0.5 * log(ok ? mag2 : 1.0);
+      s_dinv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+    }
+    __syncthreads();
+    const cpx<C> dinv = s_dinv;
+    for (int j = tid; j < kb; j += NT) {
+      prow[j] = cmul(A[c * kb + j], dinv);
+      pcol[j] = A[j * kb + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * kb; e += NT) {
+      const int r = e / kb, j = e - r * kb;
+      if (r == c) {
+        A[e] = (j == c) ? dinv : prow[j];
+      } else if (j == c) {
+        const cpx<C> q = cmul(pcol[r], dinv);
+        A[e] = {-q.re, -q.im};
+      } else {
+        const cpx<C> l = pcol[r], u = prow[j];
+        A[e].re -= l.re * u.re - l.im * u.im;
+        A[e].im -= l.re * u.im + l.im * u.re;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) ld[b0 + mat] += ldacc;
+  cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
+  for (int e = tid; e < nb * nb; e += NT) {
+    const int i = e / nb, j = e - i * nb;
+    T[e] = (i < kb && j < kb) ? A[i * kb + j] : cpx<C>{(C)0, (C)0};
   }
 }
 
@@ -546,12 +609,46 @@ __global__ void __launch_bounds__(256)
 
 // -------------------------------------------------------------------- refine
 // Adjoint diag(G).  Per block and row i: x = row i of X = A^{-1} (X[i, perm[r]] = R[i, r]),
-//   G_ii = 2 x_i - sum_j x_j (A x)_j   (refine: (A x)_j from the 5-point stencil in float64)
-//   G_ii = x_i                          (no refinement)
-// and gd[b*N + i] = sigma_b Re G_ii.  With refinement: one warp per row, the row scattered
-// into natural order in shared memory, lanes walking the lattice column y, the stencil
-// diagonal a_jj = mu - h_j + i w_n cached per CTA.  Without: one thread per row reads
-// R[i, pinv[i]].
+//   G_ii = 2 x_i - (x^T A x)    (refine: one Newton step on the inverse, diagonal only)
+//   G_ii = x_i                  (no refinement)
+// and gd[b*N + i] = sigma_b Re G_ii.  With A the 5-point stencil (A_jj = a_j + i w_n,
+// A_jk = t per bond) the quadratic form is a sum over sites and bonds:
+//   Re(x^T A x) = sum_j [a_j (Re x_j^2) - w_n Im x_j^2 + 2t Re(x_j (x_{j+x} + x_{j+y}))].
+// The residual it cancels against is ~1e-6 of its size, so it is evaluated to about 2^-44
+// relative: products of the stored float32 values are split exactly with FMA (TwoProduct)
+// and summed in double-float (TwoSum) arithmetic on the FP32 pipes; the float64 result is
+// formed once per row.  One warp per row, the row scattered into natural order in shared
+// memory, a_j cached per CTA as a double-float pair.
+struct dsf {
+  float h, l;
+};
+__device__ __forceinline__ dsf two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ dsf two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dsf fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dsf ds_add(dsf x, dsf y) {
+  const dsf s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, s.l + x.l + y.l);
+}
+__device__ __forceinline__ dsf ds_sub(dsf x, dsf y) { return ds_add(x, {-y.h, -y.l}); }
+__device__ __forceinline__ dsf ds_mul(dsf x, dsf y) {
+  const dsf p = two_prod(x.h, y.h);
+  return fast_two_sum(p.h, p.l + (x.h * y.l + x.l * y.h));
+}
+__device__ __forceinline__ dsf ds_of(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
 template <typename S>
 __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
                          Lattice la, const int* perm, double* gd, int refine) {
@@ -562,7 +659,7 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
   int* sperm = reinterpret_cast<int*>(smem_raw);
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  if (!refine) {  // sperm holds the inverse permutation
+  if (!refine || sizeof(S) != 4) {  // sperm holds the inverse permutation
     for (int r = threadIdx.x; r < N; r += blockDim.x) sperm[perm[(size_t)mat * N + r]] = r;
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
@@ -570,42 +667,43 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
     return;
   }
   const size_t perm_bytes = ((N * sizeof(int) + 15) / 16) * 16;
-  double* diag = reinterpret_cast<double*>(smem_raw + perm_bytes);  // N: Re a_jj
-  cpx<S>* rows = reinterpret_cast<cpx<S>*>(smem_raw + perm_bytes + (size_t)N * sizeof(double));
+  dsf* adiag = reinterpret_cast<dsf*>(smem_raw + perm_bytes);  // N: Re A_jj as double-float
+  cpx<S>* rows = reinterpret_cast<cpx<S>*>(smem_raw + perm_bytes + (size_t)N * sizeof(dsf));
   cpx<S>* x = rows + (size_t)warp * N;
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
     sperm[r] = perm[(size_t)mat * N + r];
-    diag[r] = la.mu - site_energy(la, r, sg);
+    adiag[r] = ds_of(la.mu - site_energy(la, r, sg));
   }
   __syncthreads();
-  const double w = (2.0 * n + 1.0) * kPi * la.T, t = la.t;
+  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const int dxs = 32 / L, dys = 32 % L;  // advance of (x, y) when j grows by 32
   for (int i = blockIdx.x * nwarps + warp; i < N; i += gridDim.x * nwarps) {
     for (int r = lane; r < N; r += 32)
       x[sperm[r]] = {re[(size_t)i * ldm + r], im[(size_t)i * ldm + r]};
     __syncwarp();
-    double ar = 0.0, ai = 0.0;
-    for (int y = lane; y < L; y += 32) {
-      const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
-      for (int xx = 0; xx < L; ++xx) {
-        const int xp = (xx + 1 == L) ? 0 : xx + 1, xm = (xx == 0) ? L - 1 : xx - 1;
-        const int j = xx * L + y;
-        const cpx<S> vj = x[j], v1 = x[xp * L + y], v2 = x[xm * L + y];
-        const cpx<S> v3 = x[xx * L + yp], v4 = x[xx * L + ym];
-        const double dr = diag[j];
-        const double xjr = (double)vj.re, xji = (double)vj.im;
-        double yr = dr * xjr - w * xji, yi = dr * xji + w * xjr;  // a_jj x_j
-        yr += t * ((double)v1.re + (double)v2.re + (double)v3.re + (double)v4.re);
-        yi += t * ((double)v1.im + (double)v2.im + (double)v3.im + (double)v4.im);
-        ar += xjr * yr - xji * yi;
-        ai += xjr * yi + xji * yr;
-      }
+    dsf acc = {0.f, 0.f};
+    int xx = lane / L, yy = lane - (lane / L) * L;
+    for (int j = lane; j < N; j += 32) {
+      const int jx = (xx + 1 == L) ? yy : j + L;
+      const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
+      const float a = (float)x[j].re, bq = (float)x[j].im;
+      const float ax = (float)x[jx].re, bx = (float)x[jx].im;
+      const float ay = (float)x[jy].re, by = (float)x[jy].im;
+      const dsf q = ds_sub(two_prod(a, a), two_prod(bq, bq));   // Re x_j^2
+      const dsf ab = two_prod(a, bq);                            // Im x_j^2 / 2
+      const dsf u = ds_add(ds_sub(two_prod(a, ax), two_prod(bq, bx)),
+                           ds_sub(two_prod(a, ay), two_prod(bq, by)));
+      const dsf e = ds_add(ds_sub(ds_mul(adiag[j], q), ds_mul(w2, ab)), ds_mul(t2, u));
+      acc = ds_add(acc, e);
+      yy += dys;
+      xx += dxs;
+      if (yy >= L) { yy -= L; xx += 1; }
     }
+    double qsum = (double)acc.h + (double)acc.l;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      ar += __shfl_xor_sync(0xffffffffu, ar, off);
-      ai += __shfl_xor_sync(0xffffffffu, ai, off);
-    }
-    if (lane == 0) gd[(size_t)b * N + i] = sg * (2.0 * (double)x[i].re - ar);
+    for (int off = 16; off > 0; off >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, off);
+    if (lane == 0) gd[(size_t)b * N + i] = sg * (2.0 * (double)x[i].re - qsum);
     __syncwarp();
   }
 }
@@ -719,7 +817,7 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int cnt, cudaStre
   const size_t perm_bytes = ((N * sizeof(int) + 15) / 16) * 16;
   prof_begin(e, kRefine, s);
   if (e.refine) {
-    const size_t fixed = perm_bytes + (size_t)N * sizeof(double);
+    const size_t fixed = perm_bytes + (size_t)N * 2 * sizeof(float);
     const size_t row_bytes = (size_t)N * sizeof(cpx<S>);
     const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (kRefineSmem - fixed) / row_bytes));
     const int gx = std::max(1, std::min((N + warps - 1) / warps, 32));
@@ -754,7 +852,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     const int kb = std::min(nb, N - k0);
     const int kend = k0 + kb;
     if (pivoted) {
-      const size_t sm = sizeof(cpx<C>) * (size_t)(N - k0) * kb;
+      const size_t sm = sizeof(cpx<C>) * (size_t)(N - k0) * (kb + 1);
       prof_begin(e, kPanel, s);
       k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
                                                     k0, kb, b0, e.ld, piv, perm, e.flags);
@@ -769,12 +867,19 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kSwap, s);
       SCA_LAUNCH_CHECK("swap");
     }
-    {
-      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * kb + kb);
-      prof_begin(e, pivoted ? kTrinv : kPanel, s);
+    if (pivoted) {
+      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * (kb + 1) + kb);
+      prof_begin(e, kTrinv, s);
       k_diag_inv<S, C, 512><<<cnt, 512, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
-                                                  nb, b0, e.ld, Tinv, pivoted ? 0 : 1, e.flags);
-      prof_end(e, pivoted ? kTrinv : kPanel, s);
+                                                  nb, b0, e.ld, Tinv, 0, e.flags);
+      prof_end(e, kTrinv, s);
+      SCA_LAUNCH_CHECK("diag");
+    } else {
+      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * kb + 2 * kb);
+      prof_begin(e, kPanel, s);
+      k_diag_gj<S, C, 512><<<cnt, 512, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
+                                                 nb, b0, e.ld, Tinv, e.flags);
+      prof_end(e, kPanel, s);
       SCA_LAUNCH_CHECK("diag");
     }
     if (!want_grad && kend == N) break;  // LU: nothing trails the last pivot block
@@ -793,7 +898,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     }
     prof_begin(e, kUpdate, s);
     if (tcg) {
-      sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s);
+      sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s, nb);
       if (st != SCA_OK) return st;
     } else {
       dim3 grid((N - c0 + 63) / 64, (N - r0 + 63) / 64, cnt);
@@ -817,8 +922,10 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
   for (int b0 = 0; b0 < e.B; b0 += e.chunk) {
     const int cnt = std::min(e.chunk, e.B - b0);
     prof_begin(e, kAssemble, s);
-    k_assemble<S><<<dim3(N, cnt), 256, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, b0, la,
-                                               e.ld, e.perm);
+    err = cudaMemsetAsync(M, 0, (size_t)cnt * e.mat_stride * sizeof(S), s);
+    if (err != cudaSuccess) return cuda_fail(err, "assemble zero fill");
+    k_assemble<S><<<dim3((N + 127) / 128, cnt), 128, 0, s>>>(M, e.ldm, e.mat_stride,
+                                                              e.plane_stride, b0, la, e.ld, e.perm);
     prof_end(e, kAssemble, s);
     SCA_LAUNCH_CHECK("assemble");
     // blocks [0, piv_blocks) need pivoting (lowest frequencies), the rest are dominant
@@ -832,7 +939,8 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       sp = e.side;
     }
     sca_status st;
-    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb_piv, false, want_grad, sp)) != SCA_OK)
+    const bool tcp = e.tc && tc_piv_ok(e);
+    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb_piv, tcp, want_grad, sp)) != SCA_OK)
       return st;
     if (nd > 0 && (st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s)) != SCA_OK)
       return st;
@@ -853,11 +961,13 @@ sca_status set_smem_limits() {
   static bool done = false;
   if (done) return SCA_OK;
   cudaError_t err;
-  const int lim = 200 * 1024 + 1024;
+  const int lim = 226 * 1024;
   err = cudaFuncSetAttribute(k_panel_smem<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (err != cudaSuccess) return cuda_fail(err, "smem panel");
   err = cudaFuncSetAttribute(k_diag_inv<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (err != cudaSuccess) return cuda_fail(err, "smem diag");
+  err = cudaFuncSetAttribute(k_diag_gj<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (err != cudaSuccess) return cuda_fail(err, "smem diag gj");
   err = cudaFuncSetAttribute(k_prep_w<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (err != cudaSuccess) return cuda_fail(err, "smem prep");
   err = cudaFuncSetAttribute(k_refine<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRefineSmem);
@@ -891,14 +1001,15 @@ sca_status run_refine_resident(Engine& e, const double* d_phi, cudaStream_t s) {
 
 sca_status run_assemble_only(Engine& e, const double* d_phi, int b0, int count, cudaStream_t s) {
   const Lattice la = make_lattice(e, d_phi);
+  const size_t S = e.fp64 ? 8 : 4;
+  cudaError_t err = cudaMemsetAsync(e.M, 0, (size_t)count * e.mat_stride * S, s);
+  if (err != cudaSuccess) return cuda_fail(err, "assemble zero fill");
   if (e.fp64)
-    k_assemble<double><<<dim3(e.N, count), 256, 0, s>>>(static_cast<double*>(e.M), e.ldm,
-                                                         e.mat_stride, e.plane_stride, b0, la,
-                                                         e.ld, e.perm);
+    k_assemble<double><<<dim3((e.N + 127) / 128, count), 128, 0, s>>>(
+        static_cast<double*>(e.M), e.ldm, e.mat_stride, e.plane_stride, b0, la, e.ld, e.perm);
   else
-    k_assemble<float><<<dim3(e.N, count), 256, 0, s>>>(static_cast<float*>(e.M), e.ldm,
-                                                        e.mat_stride, e.plane_stride, b0, la,
-                                                        e.ld, e.perm);
+    k_assemble<float><<<dim3((e.N + 127) / 128, count), 128, 0, s>>>(
+        static_cast<float*>(e.M), e.ldm, e.mat_stride, e.plane_stride, b0, la, e.ld, e.perm);
   SCA_LAUNCH_CHECK("assemble");
   return SCA_OK;
 }

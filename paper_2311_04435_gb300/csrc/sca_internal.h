@@ -114,6 +114,7 @@ bool tc_supported();
 sca_status tc_prepare(Engine& e);
 void tc_release(Engine& e);
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
-                     cudaStream_t s);
+                     cudaStream_t s, int nbk);
+bool tc_piv_ok(const Engine& e);  // tensor-core maps exist for the pivoted group's width
 
 }  // namespace sca

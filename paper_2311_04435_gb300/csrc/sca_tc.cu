@@ -38,7 +38,11 @@ constexpr int kKS = 16;            // K per pipeline stage (SWIZZLE_64B rows of 
 constexpr int kStages = 2;
 constexpr int kTileBytes = kBM * kKS * 4;             // one 128 x 16 float plane: 8 KB
 constexpr int kStageBytes = 10 * kTileBytes;          // 4 F planes + 6 W planes: 80 KB
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr int kEpiCols = 32;                          // complex columns per epilogue chunk
+constexpr int kEpiPlaneBytes = kBM * kEpiCols * 4;     // 128 x 32 floats, 16 KB
+constexpr int kEpiBufBytes = 2 * kEpiPlaneBytes;       // re + im planes
+constexpr int kEpiBufs = 2;
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBufs * kEpiBufBytes + 1024 + 256;
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;                   // 2 accumulators x 256 columns
 constexpr long long kWaitCycles = 4000000000ll;       // ~2 s at 2 GHz
@@ -95,6 +99,38 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Barrier over the 128 epilogue threads that also ANDs a predicate: every thread leaves with
+// the same decision, so no thread can be left waiting at the next named barrier.
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)(v ? 1 : 0))
+      : "memory");
+  return r != 0;
 }
 
 // Shared-memory matrix descriptor (tcgen05), K-major operand with 64-byte swizzle:
@@ -175,17 +211,19 @@ __constant__ int kWPlaneOfSlot[6] = {4, 0, 1, 5, 2, 3};
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmW,
-                TcArgs a) {
+                const __grid_constant__ CUtensorMap tmM, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  unsigned char* epi = smem + kStages * kStageBytes;  // kEpiBufs x (re, im) staging, 128B swizzle
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi + kEpiBufs * kEpiBufBytes);
   uint64_t* full = bars;                 // [kStages]
   uint64_t* empty = bars + kStages;      // [kStages]
   uint64_t* tfull = bars + 2 * kStages;  // [2]
   uint64_t* tempty = tfull + 2;          // [2]
   uint64_t* mdone = tempty + 2;          // [1] all MMAs of this CTA completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  uint64_t* efull = mdone + 1;           // [kEpiBufs] staging tile of M landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(efull + kEpiBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,6 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
     mbar_init(mdone, 1);
+    for (int b = 0; b < kEpiBufs; ++b) mbar_init(&efull[b], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -290,63 +329,103 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 2..5)
+    // M is streamed through shared memory in 128 x 32 complex chunks: one thread issues the
+    // TMA load of the next chunk while all 128 threads update the current one (thread = row,
+    // 128-byte swizzled rows, conflict-free 16-byte accesses), then TMA stores it back.
     const int q = warp & 3;              // TMEM lane quarter this warp may access
-    const int row_in_tile = q * 32 + lane;
+    const int row = q * 32 + lane;       // row of the tile owned by this thread
+    const bool leader = (warp == 2 && lane == 0);
+    const int nchunk = kBNc / kEpiCols;
     int iter = 0;
-    for (int t = blockIdx.x; t < a.tiles; t += gridDim.x, ++iter) {
-      const int buf = iter & 1;
-      const uint32_t use = (uint32_t)(iter >> 1);
-      if (!mbar_wait(&tfull[buf], use & 1, abort_flag)) break;
-      tc_fence_after();
+    uint32_t eph[kEpiBufs] = {0, 0};
+    bool pending[kEpiBufs] = {false, false};  // leader: load issued, not yet consumed
+    int ebuf = 0;
+    bool ok = true;
+    // issue the load of chunk c of tile t into staging buffer eb
+    auto issue_load = [&](int t, int c, int eb) {
       const int mat = t / (a.tiles_m * a.tiles_n);
       const int rem = t - mat * a.tiles_m * a.tiles_n;
       const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
-      const int i = a.r0 + tm * kBM + row_in_tile;
+      const int x = a.c0 + tn * kBNc + c * kEpiCols, y = a.r0 + tm * kBM;
+      bulk_wait_read0();  // the store that last read this buffer has finished reading it
+      pending[eb] = true;
+      mbar_expect_tx(&efull[eb], kEpiBufBytes);
+      unsigned char* st = epi + eb * kEpiBufBytes;
+      tma_load_3d(st, &tmM, &efull[eb], x, y, (a.mat0 + mat) * 2 + 0);
+      tma_load_3d(st + kEpiPlaneBytes, &tmM, &efull[eb], x, y, (a.mat0 + mat) * 2 + 1);
+    };
+    if (leader && (int)blockIdx.x < a.tiles) issue_load(blockIdx.x, 0, 0);
+    for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++iter) {
+      const int buf = iter & 1;
+      const uint32_t use = (uint32_t)(iter >> 1);
+      const int mat = t / (a.tiles_m * a.tiles_n);
+      const int rem = t - mat * a.tiles_m * a.tiles_n;
+      const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+      const int i = a.r0 + tm * kBM + row;
       const int j0 = a.c0 + tn * kBNc;
-      float* re = a.M + (long long)mat * a.mat_stride;
-      float* im = re + a.plane_stride;
-      const bool row_ok = i < a.N;
       const bool rowk = a.gj && i >= a.k0 && i < a.k0 + a.kb;
+      if (!epi_all(mbar_wait(&tfull[buf], use & 1, abort_flag))) { ok = false; break; }
+      tc_fence_after();
       const uint32_t tbase = tmem_base + (uint32_t)(buf * 256) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-      for (int cc = 0; cc < kBNc; cc += 32) {
+      for (int c = 0; c < nchunk; ++c) {
+        const int eb = ebuf;
+        // prefetch the next chunk (of this tile, or the first of the next tile)
+        if (leader) {
+          const int tn2 = (c + 1 < nchunk) ? t : t + (int)gridDim.x;
+          if (tn2 < a.tiles) issue_load(tn2, (c + 1 < nchunk) ? c + 1 : 0, eb ^ 1);
+        }
         uint32_t cr[32], ci[32];
-        tmem_ld32(tbase + (uint32_t)cc, cr);
-        tmem_ld32(tbase + (uint32_t)(kBNc + cc), ci);
+        tmem_ld32(tbase + (uint32_t)(c * kEpiCols), cr);
+        tmem_ld32(tbase + (uint32_t)(kBNc + c * kEpiCols), ci);
         tmem_ld_wait();
-        if (row_ok) {
-          const long long o = (long long)i * a.ldm + j0 + cc;
-          const bool colk = a.gj && (j0 + cc < a.k0 + a.kb) && (j0 + cc + 32 > a.k0);
-          if (!rowk && !colk && j0 + cc + 32 <= a.N) {
-            float4* pr = reinterpret_cast<float4*>(re + o);
-            float4* pi = reinterpret_cast<float4*>(im + o);
+        if (!epi_all(mbar_wait(&efull[eb], eph[eb], abort_flag))) { ok = false; break; }
+        pending[eb] = false;
+        eph[eb] ^= 1;
+        unsigned char* st = epi + eb * kEpiBufBytes;
+        const int jc = j0 + c * kEpiCols;
+        const bool colk = a.gj && (jc < a.k0 + a.kb) && (jc + kEpiCols > a.k0);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              float4 vr = pr[e], vi = pi[e];
-              vr.x -= __uint_as_float(cr[4 * e + 0]); vr.y -= __uint_as_float(cr[4 * e + 1]);
-              vr.z -= __uint_as_float(cr[4 * e + 2]); vr.w -= __uint_as_float(cr[4 * e + 3]);
-              vi.x -= __uint_as_float(ci[4 * e + 0]); vi.y -= __uint_as_float(ci[4 * e + 1]);
-              vi.z -= __uint_as_float(ci[4 * e + 2]); vi.w -= __uint_as_float(ci[4 * e + 3]);
-              pr[e] = vr;
-              pi[e] = vi;
-            }
-          } else {
+        for (int k = 0; k < 8; ++k) {
+          const int off = row * 128 + ((k ^ (row & 7)) << 4);
+          float4* pr = reinterpret_cast<float4*>(st + off);
+          float4* pi = reinterpret_cast<float4*>(st + kEpiPlaneBytes + off);
+          float4 vr = *pr, vi = *pi;
+          if (rowk || colk) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int j = j0 + cc + e;
-              if (j < a.N) {
-                const bool keep = !(rowk || (a.gj && j >= a.k0 && j < a.k0 + a.kb));
-                const float mr = keep ? re[o + e] : 0.f, mi = keep ? im[o + e] : 0.f;
-                re[o + e] = mr - __uint_as_float(cr[e]);
-                im[o + e] = mi - __uint_as_float(ci[e]);
-              }
+            for (int e = 0; e < 4; ++e) {
+              const int j = jc + 4 * k + e;
+              const bool keep = !(rowk || (j >= a.k0 && j < a.k0 + a.kb));
+              if (!keep) { (&vr.x)[e] = 0.f; (&vi.x)[e] = 0.f; }
             }
           }
+          vr.x -= __uint_as_float(cr[4 * k + 0]); vr.y -= __uint_as_float(cr[4 * k + 1]);
+          vr.z -= __uint_as_float(cr[4 * k + 2]); vr.w -= __uint_as_float(cr[4 * k + 3]);
+          vi.x -= __uint_as_float(ci[4 * k + 0]); vi.y -= __uint_as_float(ci[4 * k + 1]);
+          vi.z -= __uint_as_float(ci[4 * k + 2]); vi.w -= __uint_as_float(ci[4 * k + 3]);
+          *pr = vr;
+          *pi = vi;
         }
+        fence_proxy_async();
+        epi_bar();
+        if (leader) {
+          const int y = a.r0 + tm * kBM;
+          tma_store_3d(&tmM, st, jc, y, (a.mat0 + mat) * 2 + 0);
+          tma_store_3d(&tmM, st + kEpiPlaneBytes, jc, y, (a.mat0 + mat) * 2 + 1);
+          bulk_commit();
+        }
+        ebuf ^= 1;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
+    if (leader) {
+      bulk_wait_all();  // every store of this CTA has completed
+      // loads issued but not consumed (only after an abort): wait, bounded, until they land
+      volatile int drain_abort = 0;
+      for (int b2 = 0; b2 < kEpiBufs; ++b2)
+        if (pending[b2]) (void)mbar_wait(&efull[b2], eph[b2], &drain_abort);
     }
   }
   __syncthreads();
@@ -382,20 +461,37 @@ EncodeTiledFn encode_fn() {
 }
 
 struct TcMaps {
-  CUtensorMap F, W;
+  CUtensorMap F, W;    // rank-nb factors, K extent nb
+  CUtensorMap Fp, Wp;  // rank-nb factors, K extent nb_piv (pivoted group)
+  CUtensorMap M;       // the blocks, for the epilogue
+  bool piv_ok = false;
   int sms = 0;
 };
 
-// 3-D map over [blocks*planes][N rows][nb] floats, box 16 x 128 x 1, 64-byte swizzle.
-bool make_map(CUtensorMap* m, void* base, int nb, int N, long long zdim) {
+// 3-D map over [blocks*planes][N rows][nbk] floats, box 16 x 128 x 1, 64-byte swizzle.
+bool make_fw_map(CUtensorMap* m, void* base, int nbk, int N, long long zdim) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)nb, (cuuint64_t)N, (cuuint64_t)zdim};
-  cuuint64_t strides[2] = {(cuuint64_t)nb * 4, (cuuint64_t)N * nb * 4};
+  cuuint64_t dims[3] = {(cuuint64_t)nbk, (cuuint64_t)N, (cuuint64_t)zdim};
+  cuuint64_t strides[2] = {(cuuint64_t)nbk * 4, (cuuint64_t)N * nbk * 4};
   cuuint32_t box[3] = {(cuuint32_t)kKS, (cuuint32_t)kBM, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D map over the block planes [blocks*2][N rows][N cols] (row stride ldm), box 32 x 128 x 1,
+// 128-byte swizzle: the epilogue's staging tile.
+bool make_m_map(CUtensorMap* m, void* base, int N, int ldm, long long plane_stride, long long z) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)z};
+  cuuint64_t strides[2] = {(cuuint64_t)ldm * 4, (cuuint64_t)plane_stride * 4};
+  cuuint32_t box[3] = {(cuuint32_t)kEpiCols, (cuuint32_t)kBM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -420,11 +516,21 @@ sca_status tc_prepare(Engine& e) {
   TcMaps* t = new TcMaps();
   std::memset(&t->F, 0, sizeof(t->F));
   std::memset(&t->W, 0, sizeof(t->W));
+  std::memset(&t->Fp, 0, sizeof(t->Fp));
+  std::memset(&t->Wp, 0, sizeof(t->Wp));
+  std::memset(&t->M, 0, sizeof(t->M));
   const long long zf = (long long)e.chunk * (long long)(e.fw_mat / e.fw_plane);
-  if (!make_map(&t->F, e.F, e.nb, e.N, zf) || !make_map(&t->W, e.W, e.nb, e.N, zf)) {
+  if (!make_fw_map(&t->F, e.F, e.nb, e.N, zf) || !make_fw_map(&t->W, e.W, e.nb, e.N, zf) ||
+      !make_m_map(&t->M, e.M, e.N, e.ldm, (long long)e.plane_stride, 2ll * e.chunk)) {
     delete t;
-    set_error("cuTensorMapEncodeTiled failed for the rank-nb factors");
+    set_error("cuTensorMapEncodeTiled failed for the tensor-core update");
     return SCA_ECUDA;
+  }
+  if (e.nb_piv % kKS == 0) {
+    const size_t fwp = (size_t)e.N * e.nb_piv;
+    const long long zp = (long long)e.chunk * (long long)(e.fw_mat / fwp);
+    t->piv_ok = make_fw_map(&t->Fp, e.F, e.nb_piv, e.N, zp) &&
+                make_fw_map(&t->Wp, e.W, e.nb_piv, e.N, zp);
   }
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -446,11 +552,16 @@ void tc_release(Engine& e) {
   e.tmap = nullptr;
 }
 
+bool tc_piv_ok(const Engine& e) {
+  const TcMaps* t = static_cast<const TcMaps*>(e.tmap);
+  return t && t->piv_ok;
+}
+
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
-                     cudaStream_t s) {
+                     cudaStream_t s, int nbk) {
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
-  if (!t) {
-    set_error("tcgen05 update used before tc_prepare");
+  if (!t || (nbk != e.nb && !(nbk == e.nb_piv && t->piv_ok))) {
+    set_error("tcgen05 update used before tc_prepare or with an unsupported K extent");
     return SCA_ENOSTATE;
   }
   TcArgs a;
@@ -460,7 +571,7 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.ldm = e.ldm;
   a.mat_stride = (long long)e.mat_stride;
   a.plane_stride = (long long)e.plane_stride;
-  a.nb = e.nb;
+  a.nb = nbk;
   a.r0 = r0;
   a.c0 = c0;
   a.k0 = k0;
@@ -469,11 +580,12 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
   a.tiles_n = (e.N - c0 + kBNc - 1) / kBNc;
   a.tiles = a.tiles_m * a.tiles_n * cnt;
-  a.fplanes = a.wplanes = (int)(e.fw_mat / e.fw_plane);
+  a.fplanes = a.wplanes = (int)(e.fw_mat / ((size_t)e.N * nbk));
   a.err = e.flags;
   if (a.tiles <= 0) return SCA_OK;
   const int grid = std::min(a.tiles, t->sms);
-  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, a);
+  const bool pv = (nbk != e.nb);
+  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(pv ? t->Fp : t->F, pv ? t->Wp : t->W, t->M, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 update launch");
