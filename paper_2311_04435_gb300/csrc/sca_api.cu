@@ -91,10 +91,10 @@ sca_status plan(const sca_params& p, Engine& e) {
   if (const char* v = std::getenv("SCA_PIVOT_ALL"))
     if (std::atoi(v) != 0) e.piv_blocks = e.B;
   // Width of the pivoted group's shared-memory panel: N x (nb_piv + 1) complex values
-  // (rows padded by one) within 224 KB.
+  // (rows padded by one) within 220 KB.
   const size_t cbytes = e.fp64 ? 16 : 8;
   int nbp = 1;
-  while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2 + 1) * cbytes <= 224 * 1024) nbp *= 2;
+  while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2 + 1) * cbytes <= 220 * 1024) nbp *= 2;
   e.nb_piv = nbp;
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;
@@ -112,6 +112,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   bytes += (size_t)e.chunk * e.mat_stride * S;           // blocks
   bytes += 2 * (size_t)e.chunk * e.fw_mat * S;            // F, W
   bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
+  if (e.tc) bytes += (size_t)e.chunk * 6 * e.nb * e.nb * 4;  // -T^T split planes
   bytes += 2 * (size_t)e.chunk * e.N * sizeof(int);       // piv, perm
   bytes += (size_t)e.B * sizeof(double) * (1 + e.N);      // ld, gd
   bytes += (size_t)e.N * sizeof(double) * 7 + 256;        // eps, phi, m, v, g, in, misc
@@ -152,7 +153,6 @@ sca_status allocate(Engine& e) {
   SCA_ALLOC(e.d_g, (size_t)e.N * sizeof(double), "g");
   SCA_ALLOC(e.d_status, 8 * sizeof(double), "status");
   SCA_ALLOC(e.d_omega, 8 * sizeof(double), "omega");
-#undef SCA_ALLOC
   cudaError_t err = cudaMallocHost((void**)&e.h_status, 8 * sizeof(double));
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMallocHost"); }
   err = cudaMemset(e.flags, 0, 16);
@@ -162,7 +162,9 @@ sca_status allocate(Engine& e) {
   if (err == cudaSuccess) err = cudaMemset(e.F, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err == cudaSuccess) err = cudaMemset(e.W, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
+  if (e.tc) SCA_ALLOC(e.tt, (size_t)e.chunk * 6 * e.nb * e.nb * sizeof(float), "T planes");
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
+#undef SCA_ALLOC
   err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming);
@@ -235,12 +237,13 @@ void release(Engine& e) {
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   e.side = nullptr;
   e.ev_fork = e.ev_join = nullptr;
-  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.piv, e.perm, e.flags, e.ld, e.gd, e.eps_extra,
-                  e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
+  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.piv, e.perm, e.flags, e.ld, e.gd,
+                  e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_status) cudaFreeHost(e.h_status);
   e.M = e.F = e.W = e.Tinv = nullptr;
+  e.tt = nullptr;
   e.piv = e.perm = e.flags = nullptr;
   e.ld = e.gd = e.eps_extra = e.d_phi = e.d_m = e.d_v = e.d_g = e.d_status = e.d_omega = nullptr;
   e.h_status = nullptr;

@@ -84,6 +84,24 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
   if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
 }
 
+
+// sum_k 0.5 ln(mag2[k]) over k < n: logs in parallel, then summed by thread 0 in index order
+// (deterministic); returns the sum to thread 0 only.  Flags non-positive / non-finite moduli.
+template <int NT>
+__device__ double logdet_sum(double* mag2, int n, int* flags) {
+  for (int k = threadIdx.x; k < n; k += NT) {
+    const double m = mag2[k];
+    const bool ok = (m > 0.0) && isfinite(m);
+    if (!ok) atomicOr(flags, 1);
+    mag2[k] = 0.5 * log(ok ? m : 1.0);
+  }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) s += mag2[k];
+  return s;
+}
+
 // ---------------------------------------------------------------------- swap
 // Applies the panel's interchanges, in order, to the columns outside the panel
 // (columns >= jstart only).
@@ -124,6 +142,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   __shared__ double red_v[NT / 32];
   __shared__ int red_i[NT / 32];
   __shared__ int s_p;
+  __shared__ double piv2[256];
   const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = N - k0;
   S* re = M + mat * mat_stride;
@@ -134,7 +153,6 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     P[r * ps + c] = {(C)re[o], (C)im[o]};
   }
   __syncthreads();
-  double ldacc = 0.0;
   for (int c = 0; c < kb; ++c) {
     double best = -1.0;
     int bi = m;
@@ -181,13 +199,9 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     }
     __syncthreads();
     const cpx<C> d = P[c * ps + c];
-    const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
-    const bool ok = (mag2 > 0.0) && isfinite(mag2);
-    if (tid == 0) {
-      if (!ok) atomicOr(flags, 1);
-      ldacc += 0.5 * log(ok ? mag2 : 1.0);
-    }
-    const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+    const C m2 = d.re * d.re + d.im * d.im;
+    const cpx<C> inv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
+    if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
     for (int r = c + 1 + tid; r < m; r += NT) {
       const cpx<C> l = cmul(P[r * ps + c], inv);
       P[r * ps + c] = l;
@@ -205,7 +219,10 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     re[o] = (S)P[r * ps + c].re;
     im[o] = (S)P[r * ps + c].im;
   }
-  if (tid == 0) ld[b0 + mat] += ldacc;
+  {
+    const double s = logdet_sum<NT>(piv2, kb, flags);
+    if (tid == 0) ld[b0 + mat] += s;
+  }
 }
 
 // ---------------------------------------------------------------- diag block
@@ -234,16 +251,12 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
   }
   __syncthreads();
   if (factor) {
-    double ldacc = 0.0;
+    __shared__ double piv2[128];
     for (int c = 0; c < kb; ++c) {
       const cpx<C> d = A[c * as + c];
-      const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
-      const bool ok = (mag2 > 0.0) && isfinite(mag2);
-      if (tid == 0) {
-        if (!ok) atomicOr(flags, 1);
-        ldacc += 0.5 * log(ok ? mag2 : 1.0);
-      }
-      const cpx<C> inv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+      const C m2 = d.re * d.re + d.im * d.im;
+      const cpx<C> inv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
+      if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
       for (int r = c + 1 + tid; r < kb; r += NT) A[r * as + c] = cmul(A[r * as + c], inv);
       __syncthreads();
       const int w = kb - c - 1;
@@ -255,7 +268,8 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
       }
       __syncthreads();
     }
-    if (tid == 0) ld[b0 + mat] += ldacc;
+    const double s = logdet_sum<NT>(piv2, kb, flags);
+    if (tid == 0) ld[b0 + mat] += s;
   }
   // inv(U11) in place: column j gets inv(U[0:j,0:j]) * U[0:j, j] * (-1/u_jj).
   for (int j = 0; j < kb; ++j) {
@@ -313,65 +327,136 @@ __global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat
 
 // ------------------------------------------------------- dominant pivot block
 // T = inv(M_KK) for a strictly diagonally dominant pivot block (no interchanges needed, see
-// k_diag_inv) by in-place Gauss-Jordan in shared memory: kb sweeps, each updating the whole
-// kb x kb block in parallel.  ld[b] += sum ln|pivot| (the pivots of the LU).  Writes T to
-// Tinv slot 0 (nb x nb, zero padded).
+// k_diag_inv) by in-place Gauss-Jordan, the block held in registers: thread (r0, j) owns
+// column j, rows r0, r0 + RS, ... (RS = NT / kb row groups); each of the kb sweeps exchanges
+// only the pivot row and column through shared memory.  ld[b] += sum ln|pivot| (the pivots of
+// the LU).  Writes T to Tinv slot 0 (nb x nb, zero padded) and, if TT != null, the split planes
+// of W_T[j][k] = -T[k][j] for the tensor-core product F = M[:, K] T
+// (planes re_hi, im_hi, re_lo, im_lo, -im_hi, -im_lo; kb x kb per block, K-contiguous).
 template <typename S, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_stride,
                                                 size_t plane_stride, int k0, int kb, int nb,
-                                                int b0, double* ld, cpx<C>* Tinv, int* flags) {
-  extern __shared__ unsigned char smem_raw[];
-  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
-  cpx<C>* prow = A + kb * kb;                        // scaled pivot row
-  cpx<C>* pcol = prow + kb;                          // pivot column
-  __shared__ cpx<C> s_dinv;
+                                                int b0, double* ld, cpx<C>* Tinv, float* TT,
+                                                int* flags) {
+  // The block is padded to KB x KB with the identity (pivots 1: no effect on ln|det|; the
+  // padded inverse is diag(T, I)), so the thread -> (row, column) map is compile-time:
+  // column j = tid % KB, rows r = tid / KB + q * RS.
+  constexpr int KB = sizeof(C) == 8 ? 64 : 128;
+  constexpr int RS = NT / KB;
+  constexpr int MAXR = KB / RS;
+  __shared__ cpx<C> prow[KB], pcol[KB];
+  __shared__ double piv2[KB];
   const int mat = blockIdx.x, tid = threadIdx.x;
+  const int j = tid % KB, rg = tid / KB;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  for (int e = tid; e < kb * kb; e += NT) {
-    const int r = e / kb, c = e - r * kb;
-    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    A[e] = {(C)re[o], (C)im[o]};
+  cpx<C> a[MAXR];
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) {
+    const int r = rg + q * RS;
+    if (r < kb && j < kb) {
+      const size_t o = (size_t)(k0 + r) * ldm + k0 + j;
+      a[q] = {(C)re[o], (C)im[o]};
+    } else {
+      a[q] = {(C)(r == j ? 1 : 0), (C)0};
+    }
   }
-  __syncthreads();
-  double ldacc = 0.0;
-  for (int c = 0; c < kb; ++c) {
-    if (tid == 0) {
-      const cpx<C> d = A[c * kb + c];
-      const double mag2 = (double)d.re * d.re + (double)d.im * d.im;
-      const bool ok = (mag2 > 0.0) && isfinite(mag2);
-      if (!ok) atomicOr(flags, 1);
-      ldacc += 0.5 * log(ok ? mag2 : 1.0);
-      s_dinv = {ok ? (C)(d.re / mag2) : (C)0, ok ? (C)(-d.im / mag2) : (C)0};
+  for (int c = 0; c < KB; ++c) {
+    // the owners of row c and of column c publish them
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      if (rg + q * RS == c) prow[j] = a[q];
+      if (j == c) pcol[rg + q * RS] = a[q];
     }
     __syncthreads();
-    const cpx<C> dinv = s_dinv;
-    for (int j = tid; j < kb; j += NT) {
-      prow[j] = cmul(A[c * kb + j], dinv);
-      pcol[j] = A[j * kb + c];
-    }
-    __syncthreads();
-    for (int e = tid; e < kb * kb; e += NT) {
-      const int r = e / kb, j = e - r * kb;
-      if (r == c) {
-        A[e] = (j == c) ? dinv : prow[j];
-      } else if (j == c) {
-        const cpx<C> q = cmul(pcol[r], dinv);
-        A[e] = {-q.re, -q.im};
-      } else {
-        const cpx<C> l = pcol[r], u = prow[j];
-        A[e].re -= l.re * u.re - l.im * u.im;
-        A[e].im -= l.re * u.im + l.im * u.re;
-      }
+    const cpx<C> d = pcol[c];
+    const C m2 = d.re * d.re + d.im * d.im;
+    const cpx<C> dinv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
+    if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
+    // u_j = prow_j / d (j != c), u_c = 1/d; new = (r == c) ? u_j : (j == c ? 0 : a) - pcol_r u_j
+    const bool jc = (j == c);
+    const cpx<C> u = jc ? dinv : cmul(prow[j], dinv);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const cpx<C> l = pcol[rg + q * RS];
+      cpx<C> v = jc ? cpx<C>{(C)0, (C)0} : a[q];
+      v.re -= l.re * u.re - l.im * u.im;
+      v.im -= l.re * u.im + l.im * u.re;
+      a[q] = (rg + q * RS == c) ? u : v;
     }
     __syncthreads();
   }
-  if (tid == 0) ld[b0 + mat] += ldacc;
+  {
+    const double s = logdet_sum<NT>(piv2, kb, flags);  // padded pivots are 1
+    if (tid == 0) ld[b0 + mat] += s;
+  }
   cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
-  for (int e = tid; e < nb * nb; e += NT) {
-    const int i = e / nb, j = e - i * nb;
-    T[e] = (i < kb && j < kb) ? A[i * kb + j] : cpx<C>{(C)0, (C)0};
+  const size_t P = (size_t)nb * nb;  // one plane of W_T (nb x nb, K-contiguous)
+  float* tt = TT ? TT + (size_t)mat * 6 * P : nullptr;
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) {
+    const int r = rg + q * RS;
+    if (r >= nb || j >= nb) continue;
+    const bool in = r < kb && j < kb;
+    const cpx<C> v = in ? a[q] : cpx<C>{(C)0, (C)0};
+    T[(size_t)r * nb + j] = v;
+    if (tt) {  // W_T[j][r] = -T[r][j], split for TF32
+      float* o = tt + (size_t)j * nb + r;
+      const float fr = -(float)v.re, fi = -(float)v.im;
+      const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
+      const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
+      o[0] = hr; o[P] = hi; o[2 * P] = fr - hr; o[3 * P] = fi - hi;
+      o[4 * P] = -hi; o[5 * P] = -(fi - hi);
+    }
   }
+}
+
+// Split copy of the pivot columns for the tensor-core product F = M[:, K] T:
+// Fs[i][k] = split(M[i][k0 + k]) (planes re_hi, im_hi, re_lo, im_lo; N x nb, zero for k >= kb).
+template <typename S>
+__global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride,
+                             int k0, int kb, int nb, float* Fs, size_t fs_plane, size_t fs_mat) {
+  const int mat = blockIdx.y;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)N * nb) return;
+  const int i = (int)(e / nb), k = (int)(e - (size_t)i * nb);
+  const S* re = M + mat * mat_stride;
+  const S* im = re + plane_stride;
+  float fr = 0.f, fi = 0.f;
+  if (k < kb) {
+    fr = (float)re[(size_t)i * ldm + k0 + k];
+    fi = (float)im[(size_t)i * ldm + k0 + k];
+  }
+  const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
+  const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
+  float* o = Fs + (size_t)mat * fs_mat + e;
+  o[0] = hr; o[fs_plane] = hi; o[2 * fs_plane] = fr - hr; o[3 * fs_plane] = fi - hi;
+}
+
+// F planes for the update from the tensor-core product Fp = M[:, K] T (planar re, im; N x nb):
+// rows outside K take Fp, rows in K (Gauss-Jordan) take -T, columns >= kb are zero.
+template <typename C>
+__global__ void k_split_f(const float* Fp, size_t fp_plane, size_t fp_mat, const cpx<C>* Tinv,
+                          int N, int k0, int kb, int nb, int r_begin, int gj, float* F,
+                          size_t fw_plane, size_t fw_mat) {
+  const int mat = blockIdx.y;
+  const size_t e = (size_t)r_begin * nb + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)N * nb) return;
+  const int i = (int)(e / nb), c = (int)(e - (size_t)i * nb);
+  float vr = 0.f, vi = 0.f;
+  if (c < kb) {
+    if (gj && i >= k0 && i < k0 + kb) {
+      const cpx<C> t = Tinv[(size_t)mat * 2 * nb * nb + (size_t)(i - k0) * nb + c];
+      vr = -(float)t.re; vi = -(float)t.im;
+    } else {
+      vr = Fp[(size_t)mat * fp_mat + e];
+      vi = Fp[(size_t)mat * fp_mat + fp_plane + e];
+    }
+  }
+  const float hr = __uint_as_float(__float_as_uint(vr) & 0xffffe000u);
+  const float hi = __uint_as_float(__float_as_uint(vi) & 0xffffe000u);
+  float* o = F + (size_t)mat * fw_mat + e;
+  o[0] = hr; o[fw_plane] = hi; o[2 * fw_plane] = vr - hr; o[3 * fw_plane] = vi - hi;
 }
 
 // ---------------------------------------------------------------------- prep
@@ -875,10 +960,10 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("diag");
     } else {
-      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * kb + 2 * kb);
       prof_begin(e, kPanel, s);
-      k_diag_gj<S, C, 512><<<cnt, 512, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
-                                                 nb, b0, e.ld, Tinv, e.flags);
+      float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
+      k_diag_gj<S, C, 1024><<<cnt, 1024, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
+                                                  kb, nb, b0, e.ld, Tinv, TT, e.flags);
       prof_end(e, kPanel, s);
       SCA_LAUNCH_CHECK("diag");
     }
@@ -886,9 +971,25 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     const int r0 = want_grad ? 0 : kend, c0 = want_grad ? 0 : kend;
     {
       prof_begin(e, kPrep, s);
-      k_prep_f<S, C><<<dim3((N - r0 + 63) / 64, cnt), 256, 0, s>>>(
-          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, fw_plane, e.fw_mat, r0,
-          want_grad ? 1 : 0, pivoted ? 1 : 0, split);
+      if (tcg && !pivoted && nb == e.nb && e.tt) {
+        // F = M[:, K] T on the tensor cores (scratch: the W planes, rewritten below)
+        const size_t tot = (size_t)N * nb;
+        k_split_cols<S><<<dim3((unsigned)((tot + 255) / 256), cnt), 256, 0, s>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
+            fw_plane, e.fw_mat);
+        SCA_LAUNCH_CHECK("split cols");
+        sca_status st = tc_prep(e, m0, cnt, r0, s);
+        if (st != SCA_OK) return st;
+        const size_t rem = (size_t)(N - r0) * nb;
+        k_split_f<C><<<dim3((unsigned)((rem + 255) / 256), cnt), 256, 0, s>>>(
+            reinterpret_cast<const float*>(W) + 4 * fw_plane, fw_plane, e.fw_mat, Tinv, N, k0, kb,
+            nb, r0, want_grad ? 1 : 0, reinterpret_cast<float*>(F), fw_plane, e.fw_mat);
+        SCA_LAUNCH_CHECK("split f");
+      } else {
+        k_prep_f<S, C><<<dim3((N - r0 + 63) / 64, cnt), 256, 0, s>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, fw_plane, e.fw_mat,
+            r0, want_grad ? 1 : 0, pivoted ? 1 : 0, split);
+      }
       const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
       k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
@@ -928,6 +1029,10 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
                                                               e.plane_stride, b0, la, e.ld, e.perm);
     prof_end(e, kAssemble, s);
     SCA_LAUNCH_CHECK("assemble");
+    if (e.tc) {
+      sca_status st0 = tc_reset_counters(e, s);
+      if (st0 != SCA_OK) return st0;
+    }
     // blocks [0, piv_blocks) need pivoting (lowest frequencies), the rest are dominant
     const int np = std::max(0, std::min(cnt, e.piv_blocks - b0));
     const int nd = cnt - np;
@@ -956,22 +1061,30 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
   return SCA_OK;
 }
 
+// Dynamic shared-memory limit of a kernel: the device's opt-in maximum per block minus the
+// kernel's static shared memory.
+template <typename K>
+cudaError_t allow_max_smem(K* kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, kernel);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+  return err;
+}
+
 template <typename S, typename C>
 sca_status set_smem_limits() {
   static bool done = false;
   if (done) return SCA_OK;
   cudaError_t err;
-  const int lim = 226 * 1024;
-  err = cudaFuncSetAttribute(k_panel_smem<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (err != cudaSuccess) return cuda_fail(err, "smem panel");
-  err = cudaFuncSetAttribute(k_diag_inv<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (err != cudaSuccess) return cuda_fail(err, "smem diag");
-  err = cudaFuncSetAttribute(k_diag_gj<S, C, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (err != cudaSuccess) return cuda_fail(err, "smem diag gj");
-  err = cudaFuncSetAttribute(k_prep_w<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (err != cudaSuccess) return cuda_fail(err, "smem prep");
-  err = cudaFuncSetAttribute(k_refine<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRefineSmem);
-  if (err != cudaSuccess) return cuda_fail(err, "smem refine");
+  if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
+  if ((err = allow_max_smem(k_diag_inv<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem diag");
+  if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
+  if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
   done = true;
   return SCA_OK;
 }

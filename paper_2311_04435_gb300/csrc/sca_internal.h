@@ -40,6 +40,7 @@ struct Engine {
   void* F = nullptr;        // chunk x 2 planes x N x nb (x2 hi/lo for tc)
   void* W = nullptr;        // same, W^T
   void* Tinv = nullptr;     // chunk x 2 x nb x nb complex (compute type)
+  float* tt = nullptr;      // chunk x 6 x nb x nb: -T^T split planes (tensor-core prep)
   int* piv = nullptr;       // chunk x N
   int* perm = nullptr;      // chunk x N
   int* flags = nullptr;     // 1 int: nonfinite / singular
@@ -58,6 +59,8 @@ struct Engine {
   struct Profiler* prof = nullptr;  // per-kernel event timing (sca_profile_enable)
   cudaStream_t side = nullptr;      // stream of the pivoted group (runs beside the rest)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
+  int tc_next = 0;
 };
 
 // Kernel kinds for per-launch timing.
@@ -115,6 +118,9 @@ sca_status tc_prepare(Engine& e);
 void tc_release(Engine& e);
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
                      cudaStream_t s, int nbk);
-bool tc_piv_ok(const Engine& e);  // tensor-core maps exist for the pivoted group's width
+bool tc_piv_ok(const Engine& e);
+sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's launches  // tensor-core maps exist for the pivoted group's width
+// F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
+sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
 
 }  // namespace sca

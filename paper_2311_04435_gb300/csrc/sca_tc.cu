@@ -32,6 +32,9 @@
 namespace sca {
 namespace {
 
+}  // namespace
+constexpr int kCounters = 1024;    // tile counters per pass (one per tensor-core launch)
+namespace {
 constexpr int kBM = 128;           // F rows per tile
 constexpr int kBNc = 128;          // complex W columns per tile (real MMA N = 256)
 constexpr int kKS = 16;            // K per pipeline stage (SWIZZLE_64B rows of 64 bytes)
@@ -42,6 +45,7 @@ constexpr int kEpiCols = 32;                          // complex columns per epi
 constexpr int kEpiPlaneBytes = kBM * kEpiCols * 4;     // 128 x 32 floats, 16 KB
 constexpr int kEpiBufBytes = 2 * kEpiPlaneBytes;       // re + im planes
 constexpr int kEpiBufs = 2;
+constexpr int kRing = 4;                               // tile-id ring (producer -> MMA, epilogue)
 constexpr int kSmemBytes = kStages * kStageBytes + kEpiBufs * kEpiBufBytes + 1024 + 256;
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;                   // 2 accumulators x 256 columns
@@ -198,6 +202,8 @@ struct TcArgs {
   int tiles_m, tiles_n, tiles;         // per block, and total
   int fplanes, wplanes;                // planes per block in the F / W tensor maps
   int mat0;                            // workspace slot of the first block
+  int m_zmul, m_zoff;                  // output map plane index: (mat0+mat)*m_zmul + m_zoff + p
+  int* counter;                        // tile counter (zero before the launch)
   int* err;                            // device error word (bit 1: wait time-out)
 };
 
@@ -223,7 +229,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tempty = tfull + 2;          // [2]
   uint64_t* mdone = tempty + 2;          // [1] all MMAs of this CTA completed
   uint64_t* efull = mdone + 1;           // [kEpiBufs] staging tile of M landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(efull + kEpiBufs);
+  uint64_t* rfull = efull + kEpiBufs;    // [kRing] tile id published
+  uint64_t* rempty = rfull + kRing;      // [kRing] tile id read by the MMA thread and 4 warps
+  int* ring = reinterpret_cast<int*>(rempty + kRing);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ring + kRing);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -232,6 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
     mbar_init(mdone, 1);
     for (int b = 0; b < kEpiBufs; ++b) mbar_init(&efull[b], 1);
+    for (int r = 0; r < kRing; ++r) { mbar_init(&rfull[r], 1); mbar_init(&rempty[r], 5); }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -255,7 +265,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int last_parity[kStages];
       for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
-      for (int t = blockIdx.x; t < a.tiles && !*abort_flag; t += gridDim.x) {
+      int rslot = 0;
+      uint32_t rphase = 0;
+      while (true) {
+        // claim the next tile and publish it to the MMA thread and the epilogue
+        int t = *abort_flag ? -1 : atomicAdd(a.counter, 1);
+        if (t >= a.tiles) t = -1;
+        if (!mbar_wait(&rempty[rslot], rphase ^ 1, abort_flag)) break;
+        ring[rslot] = t;
+        mbar_arrive(&rfull[rslot]);
+        if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
+        if (t < 0) break;
         const int mat = t / (a.tiles_m * a.tiles_n);
         const int rem = t - mat * a.tiles_m * a.tiles_n;
         const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
@@ -285,8 +305,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int iter = 0;
-      for (int t = blockIdx.x; t < a.tiles && !*abort_flag; t += gridDim.x, ++iter) {
+      int rslot = 0;
+      uint32_t rphase = 0;
+      for (int iter = 0;; ++iter) {
+        if (!mbar_wait(&rfull[rslot], rphase, abort_flag)) break;
+        const int t = ring[rslot];
+        mbar_arrive(&rempty[rslot]);
+        if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
+        if (t < 0) break;
         const int buf = iter & 1;
         const uint32_t use = (uint32_t)(iter >> 1);  // times this buffer was used before
         if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag)) break;
@@ -351,11 +377,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       pending[eb] = true;
       mbar_expect_tx(&efull[eb], kEpiBufBytes);
       unsigned char* st = epi + eb * kEpiBufBytes;
-      tma_load_3d(st, &tmM, &efull[eb], x, y, (a.mat0 + mat) * 2 + 0);
-      tma_load_3d(st + kEpiPlaneBytes, &tmM, &efull[eb], x, y, (a.mat0 + mat) * 2 + 1);
+      const int zb = (a.mat0 + mat) * a.m_zmul + a.m_zoff;
+      tma_load_3d(st, &tmM, &efull[eb], x, y, zb);
+      tma_load_3d(st + kEpiPlaneBytes, &tmM, &efull[eb], x, y, zb + 1);
     };
-    if (leader && (int)blockIdx.x < a.tiles) issue_load(blockIdx.x, 0, 0);
-    for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x, ++iter) {
+    int rslot = 0;
+    uint32_t rphase = 0;
+    int prefetched = -1;  // tile whose chunk 0 is already loading into staging buffer ebuf
+    while (ok) {
+      if (!epi_all(mbar_wait(&rfull[rslot], rphase, abort_flag))) { ok = false; break; }
+      const int t = ring[rslot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rempty[rslot]);
+      if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
+      if (t < 0) break;
+      if (leader && prefetched != t) issue_load(t, 0, ebuf);
       const int buf = iter & 1;
       const uint32_t use = (uint32_t)(iter >> 1);
       const int mat = t / (a.tiles_m * a.tiles_n);
@@ -372,8 +408,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int eb = ebuf;
         // prefetch the next chunk (of this tile, or the first of the next tile)
         if (leader) {
-          const int tn2 = (c + 1 < nchunk) ? t : t + (int)gridDim.x;
-          if (tn2 < a.tiles) issue_load(tn2, (c + 1 < nchunk) ? c + 1 : 0, eb ^ 1);
+          if (c + 1 < nchunk) {
+            issue_load(t, c + 1, eb ^ 1);
+          } else {
+            // the next tile's first chunk, if the producer has already published it
+            prefetched = -1;
+            if (mbar_try(&rfull[rslot], rphase)) {
+              const int t2 = ring[rslot];
+              if (t2 >= 0) { issue_load(t2, 0, eb ^ 1); prefetched = t2; }
+            }
+          }
         }
         uint32_t cr[32], ci[32];
         tmem_ld32(tbase + (uint32_t)(c * kEpiCols), cr);
@@ -410,8 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         epi_bar();
         if (leader) {
           const int y = a.r0 + tm * kBM;
-          tma_store_3d(&tmM, st, jc, y, (a.mat0 + mat) * 2 + 0);
-          tma_store_3d(&tmM, st + kEpiPlaneBytes, jc, y, (a.mat0 + mat) * 2 + 1);
+          const int zb = (a.mat0 + mat) * a.m_zmul + a.m_zoff;
+          tma_store_3d(&tmM, st, jc, y, zb);
+          tma_store_3d(&tmM, st + kEpiPlaneBytes, jc, y, zb + 1);
           bulk_commit();
         }
         ebuf ^= 1;
@@ -419,6 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
+      ++iter;
     }
     if (leader) {
       bulk_wait_all();  // every store of this CTA has completed
@@ -464,6 +510,8 @@ struct TcMaps {
   CUtensorMap F, W;    // rank-nb factors, K extent nb
   CUtensorMap Fp, Wp;  // rank-nb factors, K extent nb_piv (pivoted group)
   CUtensorMap M;       // the blocks, for the epilogue
+  CUtensorMap TT;      // -T^T split planes (nb x nb per block): B of F = M[:, K] T
+  CUtensorMap FP;      // planar F = M[:, K] T (W scratch planes 4, 5): output of that product
   bool piv_ok = false;
   int sms = 0;
 };
@@ -481,8 +529,22 @@ bool make_fw_map(CUtensorMap* m, void* base, int nbk, int N, long long zdim) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 3-D map over the block planes [blocks*2][N rows][N cols] (row stride ldm), box 32 x 128 x 1,
-// 128-byte swizzle: the epilogue's staging tile.
+// 3-D map over [z][rows][cols] floats (row stride ld), box 32 x 128 x 1, 128-byte swizzle: the
+// epilogue's staging tile.
+bool make_m_map_rows(CUtensorMap* m, void* base, int cols, int rows, int ld, long long zstride,
+                     long long z) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)z};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)zstride * 4};
+  cuuint32_t box[3] = {(cuuint32_t)kEpiCols, (cuuint32_t)kBM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The block planes [blocks*2][N rows][N cols] (row stride ldm).
 bool make_m_map(CUtensorMap* m, void* base, int N, int ldm, long long plane_stride, long long z) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -496,6 +558,14 @@ bool make_m_map(CUtensorMap* m, void* base, int N, int ldm, long long plane_stri
 }
 
 }  // namespace
+
+sca_status tc_reset_counters(Engine& e, cudaStream_t s) {
+  e.tc_next = 0;
+  if (!e.tc_counters) return SCA_OK;
+  cudaError_t err = cudaMemsetAsync(e.tc_counters, 0, kCounters * sizeof(int), s);
+  if (err != cudaSuccess) return cuda_fail(err, "tile counters");
+  return SCA_OK;
+}
 
 bool tc_supported() {
   int dev = 0, major = 0, minor = 0;
@@ -526,6 +596,18 @@ sca_status tc_prepare(Engine& e) {
     set_error("cuTensorMapEncodeTiled failed for the tensor-core update");
     return SCA_ECUDA;
   }
+  {
+    // F = M[:, K] T on the tensor cores: A = split pivot columns (W scratch planes 0-3, same
+    // map as W), B = -T^T planes, output planar into W scratch planes 4, 5.
+    const long long ztt = (long long)e.chunk * 6;
+    bool ok = !e.tt || (make_fw_map(&t->TT, e.tt, e.nb, e.nb, ztt) &&
+                        make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf));
+    if (!ok) {
+      delete t;
+      set_error("cuTensorMapEncodeTiled failed for the tensor-core prep product");
+      return SCA_ECUDA;
+    }
+  }
   if (e.nb_piv % kKS == 0) {
     const size_t fwp = (size_t)e.N * e.nb_piv;
     const long long zp = (long long)e.chunk * (long long)(e.fw_mat / fwp);
@@ -541,11 +623,19 @@ sca_status tc_prepare(Engine& e) {
     delete t;
     return cuda_fail(err, "tcgen05 update set-up");
   }
+  err = cudaMalloc((void**)&e.tc_counters, kCounters * sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(e.tc_counters, 0, kCounters * sizeof(int));
+  if (err != cudaSuccess) {
+    delete t;
+    return cuda_fail(err, "tile counters");
+  }
   e.tmap = t;
   return SCA_OK;
 }
 
 void tc_release(Engine& e) {
+  if (e.tc_counters) cudaFree(e.tc_counters);
+  e.tc_counters = nullptr;
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
   if (!t) return;
   delete t;
@@ -581,8 +671,15 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.tiles_n = (e.N - c0 + kBNc - 1) / kBNc;
   a.tiles = a.tiles_m * a.tiles_n * cnt;
   a.fplanes = a.wplanes = (int)(e.fw_mat / ((size_t)e.N * nbk));
+  a.m_zmul = 2;
+  a.m_zoff = 0;
   a.err = e.flags;
   if (a.tiles <= 0) return SCA_OK;
+  if (e.tc_next >= kCounters) {
+    set_error("too many tensor-core launches in one pass");
+    return SCA_EINVAL;
+  }
+  a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, t->sms);
   const bool pv = (nbk != e.nb);
   k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(pv ? t->Fp : t->F, pv ? t->Wp : t->W, t->M, a);
@@ -592,5 +689,46 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   return SCA_OK;
 }
 
+
+sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t || !e.tt) {
+    set_error("tensor-core prep used before tc_prepare");
+    return SCA_ENOSTATE;
+  }
+  TcArgs a;
+  a.M = nullptr;
+  a.N = e.N;
+  a.ldm = e.nb;
+  a.mat_stride = 0;
+  a.plane_stride = 0;
+  a.nb = e.nb;
+  a.r0 = r0;
+  a.c0 = 0;
+  a.k0 = 0;
+  a.kb = 1 << 30;  // every output element masked: the result is -sum F W
+  a.gj = 1;
+  a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
+  a.tiles_n = (e.nb + kBNc - 1) / kBNc;
+  a.tiles = a.tiles_m * a.tiles_n * cnt;
+  a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W scratch planes 0-3
+  a.wplanes = 6;                             // B: -T^T planes
+  a.mat0 = m0;
+  a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: W scratch planes 4, 5
+  a.m_zoff = 4;
+  a.err = e.flags;
+  if (a.tiles <= 0) return SCA_OK;
+  if (e.tc_next >= kCounters) {
+    set_error("too many tensor-core launches in one pass");
+    return SCA_EINVAL;
+  }
+  a.counter = e.tc_counters + e.tc_next++;
+  const int grid = std::min(a.tiles, t->sms);
+  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
+  return SCA_OK;
+}
 
 }  // namespace sca

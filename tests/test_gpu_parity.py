@@ -50,7 +50,7 @@ CASES = [
     (4, 16, 0.0, 0.0),     # 16x16 blocks
     (6, 7, 0.7, 0.1),      # 36: ragged single panel
     (10, 5, 0.5, 0.0),     # 100: 3 full panels + ragged 4
-    (12, 4, 1.0, -0.2),    # 144: 4.5 panels
+    (12, 10, 1.0, -0.2),   # 144: 4.5 panels; 6 pivoted + 14 dominant blocks
     (14, 3, 0.5, 0.0),     # 196
 ]
 
@@ -76,11 +76,12 @@ def test_blocks_logdet_and_diag_match_oracle(prec, L, nw, delta, mu):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_larger_block_20x20_matches_oracle(prec):
-    p = api.Params(20, 2, U=6.0, T=0.1, delta=0.5, prec=prec)
+    """400 x 400 blocks: pivoted (n < 6) and dominant (n >= 6) groups, ragged last panel."""
+    p = api.Params(20, 8, U=6.0, T=0.1, delta=0.5, prec=prec)
     phi = inputs.seed_phi(0, p.N)
     with api.Context(p) as c:
         ld, gd = c.blocks(phi, grad=True)
-    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, list(range(4)))
+    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, list(range(16)))
     t = tol(prec)
     assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
     assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
