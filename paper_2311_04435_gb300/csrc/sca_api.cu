@@ -253,19 +253,7 @@ void release(Engine& e) {
 
 using namespace sca;
 
-struct sca_ctx {
-  Engine e;
-  cudaStream_t own = nullptr;     // the context's stream
-  cudaStream_t stream = nullptr;  // stream in use (own or the caller's, sca_set_stream)
-  double* d_in = nullptr;  // N doubles: host-supplied phi
-  sca_adam adam{};
-  bool adam_ready = false;
-  int32_t step = 0;
-  bool kept = false;  // inverses of every block resident from sca_forward_dev
-  const double* kept_phi = nullptr;  // the d_phi that forward was given
-};
-
-namespace {
+namespace sca {
 
 sca_status sync_status(sca_ctx* c, cudaStream_t s) {
   cudaError_t err = cudaMemcpyAsync(c->e.h_status, c->e.d_status, 8 * sizeof(double),
@@ -309,7 +297,7 @@ AdamStep adam_step_args(const sca_adam& a, int32_t step) {
   return as;
 }
 
-}  // namespace
+}  // namespace sca
 
 extern "C" {
 
@@ -516,8 +504,11 @@ sca_status sca_adam_init(sca_ctx* c, const sca_adam* adam, const double* phi0_ho
   return SCA_OK;
 }
 
+}  // extern "C"
+
+namespace sca {
 // Enqueues `n` Adam iterations (gradient + gated update) without synchronising.
-static sca_status enqueue_adam(sca_ctx* c, int32_t n) {
+sca_status enqueue_adam(sca_ctx* c, int32_t n) {
   c->kept = false;
   for (int32_t k = 0; k < n; ++k) {
     const AdamStep as = adam_step_args(c->adam, c->step + 1);
@@ -529,6 +520,19 @@ static sca_status enqueue_adam(sca_ctx* c, int32_t n) {
   }
   return SCA_OK;
 }
+
+// Omega and max|g| at the current phi (no update), synchronised into h_status.
+sca_status final_eval(sca_ctx* c) {
+  sca_status st = run_blocks(c->e, c->e.d_phi, true, c->stream);
+  if (st != SCA_OK) return st;
+  if ((st = run_reduce(c->e, c->e.d_phi, c->e.d_omega, c->e.d_g, nullptr, c->stream)) != SCA_OK)
+    return st;
+  if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+  return check_finite(c);
+}
+}  // namespace sca
+
+extern "C" {
 
 sca_status sca_adam_step(sca_ctx* c, int32_t nsteps, double* omega, double* gmax) {
   if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }

@@ -124,3 +124,22 @@ sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
 
 }  // namespace sca
+
+struct sca_ctx {
+  sca::Engine e;
+  cudaStream_t own = nullptr;     // the context's stream
+  cudaStream_t stream = nullptr;  // stream in use (own or the caller's, sca_set_stream)
+  double* d_in = nullptr;         // N doubles: host-supplied phi
+  sca_adam adam{};
+  bool adam_ready = false;
+  int32_t step = 0;
+  bool kept = false;              // inverses of every block resident from sca_forward_dev
+  const double* kept_phi = nullptr;
+};
+
+namespace sca {
+sca_status sync_status(sca_ctx* c, cudaStream_t s);  // status -> pinned host, synchronise
+sca_status check_finite(sca_ctx* c);                 // status -> SCA_ENONFINITE / ETIMEOUT
+sca_status enqueue_adam(sca_ctx* c, int32_t n);      // n gated Adam iterations, no sync
+sca_status final_eval(sca_ctx* c);                   // Omega, max|g| at phi (synchronised)
+}  // namespace sca

@@ -1,0 +1,87 @@
+"""Serving loop (sca_server_*): continuous batching of mixed-size solve requests.
+
+Each request's result must be the same alone (sca_solve) and in the mix, bit for bit; the
+admission respects the slot count and the HBM budget; bookkeeping errors are reported.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2311_04435_gb300 import _lib, api
+
+pytestmark = pytest.mark.gpu
+
+
+def _wait(srv, rid, N, timeout=300.0):
+    t0 = time.time()
+    while True:
+        r = srv.poll(rid, N)
+        if r is not None:
+            return r
+        if time.time() - t0 > timeout:
+            raise TimeoutError(rid)
+        time.sleep(0.005)
+
+
+REQS = [
+    (api.Params(4, 16, U=6.0, T=0.1, prec="fp64"), api.AdamConfig(lr=0.02, grad_tol=1e-5, max_steps=400, seed=1)),
+    (api.Params(6, 8, U=4.0, T=0.2, delta=0.5, prec="fp32"), api.AdamConfig(lr=0.02, grad_tol=1e-5, max_steps=300, seed=2)),
+    (api.Params(8, 6, U=3.0, T=0.3, delta=1.0, prec="3xtf32"), api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=150, seed=3)),
+    (api.Params(12, 10, U=5.0, T=0.1, delta=0.3, prec="3xtf32"), api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=40, seed=4)),
+    (api.Params(4, 4, U=2.0, T=0.5, prec="fp64"), api.AdamConfig(lr=0.05, grad_tol=1e-3, max_steps=1000, seed=5)),
+    (api.Params(10, 5, U=7.0, T=0.15, delta=1.5, prec="fp32"), api.AdamConfig(lr=0.02, grad_tol=1e-6, max_steps=60, seed=6)),
+]
+
+
+def test_results_identical_alone_and_in_the_mix():
+    alone = [api.solve(p, a) for p, a in REQS]
+    with api.Server(hbm_budget_bytes=8 << 30, max_slots=3) as srv:
+        ids = [srv.submit(p, a) for p, a in REQS]
+        mixed = [_wait(srv, rid, p.N) for rid, (p, _) in zip(ids, REQS)]
+        times = [srv.times(rid) for rid in ids]
+    for (p, a), x, y in zip(REQS, alone, mixed):
+        assert x.steps == y.steps
+        assert np.array_equal(x.phi, y.phi)
+        assert x.omega == y.omega and x.gmax == y.gmax
+        assert y.gmax < a.grad_tol or y.steps == a.max_steps
+    # at most 3 requests between admission and completion at any time
+    events = sorted([(t[1], 1) for t in times] + [(t[3], -1) for t in times], key=lambda e: (e[0], e[1]))
+    live = peak = 0
+    for _, d in events:
+        live += d
+        peak = max(peak, live)
+    assert peak <= 3
+    for t in times:
+        assert 0 <= t[0] <= t[1] <= t[2] <= t[3]
+
+
+def test_budget_limits_concurrency():
+    p = api.Params(8, 8, U=4.0, T=0.2, prec="fp32")
+    a = api.AdamConfig(lr=0.02, grad_tol=0.0, max_steps=80, seed=7)
+    b = api.workspace_bytes(p)
+    with api.Server(hbm_budget_bytes=2 * b + b // 2, max_slots=8) as srv:
+        ids = [srv.submit(p, api.AdamConfig(**{**a.__dict__, "seed": 7 + k})) for k in range(5)]
+        for rid in ids:
+            _wait(srv, rid, p.N)
+        times = [srv.times(rid) for rid in ids]
+    events = sorted([(t[1], 1) for t in times] + [(t[3], -1) for t in times], key=lambda e: (e[0], e[1]))
+    live = peak = 0
+    for _, d in events:
+        live += d
+        peak = max(peak, live)
+    assert peak <= 2
+    # admission in arrival order
+    admits = [t[1] for t in times]
+    assert admits == sorted(admits)
+
+
+def test_over_budget_and_unknown_ids():
+    p = api.Params(20, 64, U=4.0, T=0.1, prec="fp64")
+    with api.Server(hbm_budget_bytes=1 << 20, max_slots=2) as srv:
+        with pytest.raises(_lib.SCAError, match="SCA_EBUDGET"):
+            srv.submit(p, api.AdamConfig())
+        with pytest.raises(_lib.SCAError, match="SCA_ENOTFOUND"):
+            srv.poll(12345)
+        with pytest.raises(_lib.SCAError, match="SCA_EINVAL"):
+            srv.submit(api.Params(3, 4, U=4.0, T=0.1), api.AdamConfig())
