@@ -24,6 +24,7 @@ thread_local std::string t_err;
 void set_error(const std::string& msg) { t_err = msg; }
 
 sca_status cuda_fail(cudaError_t e, const char* where) {
+  (void)cudaGetLastError();  // a failed call also records itself as the thread's last error
   set_error(std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
   return SCA_ECUDA;
 }
@@ -165,6 +166,7 @@ sca_status allocate(Engine& e) {
   if (e.tc) SCA_ALLOC(e.tt, (size_t)e.chunk * 6 * e.nb * e.nb * sizeof(float), "T planes");
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
 #undef SCA_ALLOC
+  if ((st = fused_prepare(e)) != SCA_OK) { release(e); return st; }
   err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming);
@@ -232,6 +234,7 @@ void prof_free(Engine& e) {
 void release(Engine& e) {
   prof_free(e);
   tc_release(e);
+  fused_release(e);
   if (e.side) { cudaStreamSynchronize(e.side); cudaStreamDestroy(e.side); }
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
@@ -510,6 +513,18 @@ namespace sca {
 // Enqueues `n` Adam iterations (gradient + gated update) without synchronising.
 sca_status enqueue_adam(sca_ctx* c, int32_t n) {
   c->kept = false;
+  if (fused_eligible(c->e)) {  // small blocks: up to kMaxFusedSteps iterations per launch
+    while (n > 0) {
+      const int32_t k = std::min<int32_t>(n, kMaxFusedSteps);
+      AdamStep st[kMaxFusedSteps];
+      for (int32_t j = 0; j < k; ++j) st[j] = adam_step_args(c->adam, c->step + 1 + j);
+      sca_status r = run_fused_adam(c->e, k, st, true, c->stream);
+      if (r != SCA_OK) return r;
+      c->step += k;
+      n -= k;
+    }
+    return SCA_OK;
+  }
   for (int32_t k = 0; k < n; ++k) {
     const AdamStep as = adam_step_args(c->adam, c->step + 1);
     sca_status st = run_blocks(c->e, c->e.d_phi, true, c->stream);

@@ -22,36 +22,13 @@
 #include <cstring>
 
 #include "sca_internal.h"
+#include "sca_device.cuh"
 
 namespace sca {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 constexpr size_t kRefineSmem = 208 * 1024;
-
-template <typename C>
-struct cpx {
-  C re, im;
-};
-
-template <typename C>
-__device__ __forceinline__ cpx<C> cmul(cpx<C> a, cpx<C> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
-}
-
-struct Lattice {
-  int L, N;
-  double t, delta_eff, mu, T;
-  const double* phi;
-  const double* eps_extra;
-};
-
-__device__ __forceinline__ double site_energy(const Lattice& la, int i, int sg) {
-  const int x = i / la.L, y = i - x * la.L;
-  const double s = ((x + y) & 1) ? -1.0 : 1.0;
-  return -s * la.delta_eff + (la.eps_extra ? la.eps_extra[i] : 0.0) - sg * la.phi[i];
-}
 
 // ------------------------------------------------------------------ assemble
 // A_b = (i w_n + mu) I - H_sigma(phi), b = 2n + s (Eq. 1 hopping: +t off-diagonal per bond,
@@ -82,24 +59,6 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
     perm[(size_t)mat * N + i] = i;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
-}
-
-
-// sum_k 0.5 ln(mag2[k]) over k < n: logs in parallel, then summed by thread 0 in index order
-// (deterministic); returns the sum to thread 0 only.  Flags non-positive / non-finite moduli.
-template <int NT>
-__device__ double logdet_sum(double* mag2, int n, int* flags) {
-  for (int k = threadIdx.x; k < n; k += NT) {
-    const double m = mag2[k];
-    const bool ok = (m > 0.0) && isfinite(m);
-    if (!ok) atomicOr(flags, 1);
-    mag2[k] = 0.5 * log(ok ? m : 1.0);
-  }
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < n; ++k) s += mag2[k];
-  return s;
 }
 
 // ---------------------------------------------------------------------- swap
@@ -704,36 +663,6 @@ __global__ void __launch_bounds__(256)
 // and summed in double-float (TwoSum) arithmetic on the FP32 pipes; the float64 result is
 // formed once per row.  One warp per row, the row scattered into natural order in shared
 // memory, a_j cached per CTA as a double-float pair.
-struct dsf {
-  float h, l;
-};
-__device__ __forceinline__ dsf two_prod(float a, float b) {
-  const float p = a * b;
-  return {p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ dsf two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ dsf fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ dsf ds_add(dsf x, dsf y) {
-  const dsf s = two_sum(x.h, y.h);
-  return fast_two_sum(s.h, s.l + x.l + y.l);
-}
-__device__ __forceinline__ dsf ds_sub(dsf x, dsf y) { return ds_add(x, {-y.h, -y.l}); }
-__device__ __forceinline__ dsf ds_mul(dsf x, dsf y) {
-  const dsf p = two_prod(x.h, y.h);
-  return fast_two_sum(p.h, p.l + (x.h * y.l + x.l * y.h));
-}
-__device__ __forceinline__ dsf ds_of(double v) {
-  const float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
-
 template <typename S>
 __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
                          Lattice la, const int* perm, double* gd, int refine) {

@@ -11,6 +11,8 @@
 
 namespace sca {
 
+constexpr int kMaxFusedSteps = 16;  // Adam iterations per fused persistent launch
+
 // Counts every kernel launched through the library (sca_kernel_launches()).
 extern std::atomic<uint64_t> g_launches;
 
@@ -61,6 +63,9 @@ struct Engine {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
   int tc_next = 0;
+  int fused_grid = 0;               // CTAs of the fused small-block kernel (0: not eligible)
+  size_t fused_smem = 0;
+  unsigned* fused_bar = nullptr;    // grid-barrier counter and generation
 };
 
 // Kernel kinds for per-launch timing.
@@ -108,6 +113,13 @@ sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d
 
 // Assembled blocks (for sca_debug_assemble).
 sca_status run_assemble_only(Engine& e, const double* d_phi, int b0, int count, cudaStream_t s);
+
+// Fused persistent Adam kernel for small blocks (sca_fused.cu).
+sca_status fused_prepare(Engine& e);
+void fused_release(Engine& e);
+bool fused_eligible(const Engine& e);
+sca_status run_fused_adam(Engine& e, int nsteps, const AdamStep* steps, bool do_adam,
+                          cudaStream_t s);
 
 // Seeded start field on the device.
 sca_status run_seed_phi(double* d_phi, int N, uint64_t seed, cudaStream_t s);

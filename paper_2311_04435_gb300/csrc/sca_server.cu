@@ -44,6 +44,7 @@ struct Request {
   std::vector<double> phi;
   double omega = 0, gmax = 0;
   int32_t steps = 0;
+  std::string error;  // message of the failure, if any
 };
 
 }  // namespace
@@ -71,6 +72,7 @@ struct sca_server {
 };
 
 void sca_server::finish(Request* r, sca_status st) {
+  if (st != SCA_OK) r->error = sca_last_error();
   if (r->ctx) {
     sca_destroy(r->ctx);
     r->ctx = nullptr;
@@ -240,7 +242,7 @@ sca_status sca_poll(sca_server* s, uint64_t req_id, double* phi_out, double* ome
   Request* r = it->second;
   if (r->state != 2) return SCA_EPENDING;
   if (r->status != SCA_OK) {
-    sca::set_error("request failed");
+    sca::set_error("request " + std::to_string(req_id) + " failed: " + r->error);
     return r->status;
   }
   if (phi_out) std::copy(r->phi.begin(), r->phi.end(), phi_out);

@@ -228,3 +228,27 @@ def test_pivot_free_blocks_match_forced_pivoting(prec, monkeypatch):
     assert np.max(np.abs(gd_a - gd_b)) <= t["g"] * max(1.0, np.abs(gd_b).max())
     o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, list(range(2 * p.n_omega)))
     assert np.allclose(ld_a, o_ld, rtol=t["ld"], atol=t["ld"])
+
+
+@pytest.mark.parametrize("L,nw,prec", [(4, 16, "fp64"), (8, 12, "fp64"), (6, 10, "fp32"), (12, 8, "3xtf32")])
+def test_fused_persistent_adam_matches_blocked_path_and_oracle(L, nw, prec, monkeypatch):
+    """Small blocks run Adam in one cooperative launch per 16 iterations (blocks in shared
+    memory, grid barriers); it must track the blocked multi-launch path and the oracle."""
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=0.4, prec=prec)
+    ad = api.AdamConfig(lr=0.01, seed=11)
+    steps = 40
+    with api.Context(p) as c:
+        c.adam_init(ad)
+        om_f, gm_f = c.adam_step(steps)
+        phi_f = c.phi()
+    monkeypatch.setenv("SCA_FUSED", "0")
+    with api.Context(p) as c:
+        c.adam_init(ad)
+        om_b, gm_b = c.adam_step(steps)
+        phi_b = c.phi()
+    phi_o, k, _, _, oh, gh = oracle.adam_run(oparams(p), lr=0.01, max_steps=steps, seed=11,
+                                             history=True)
+    t = 1e-10 if prec == "fp64" else 1e-6
+    assert np.max(np.abs(phi_f - phi_b)) < t
+    assert np.max(np.abs(phi_f - phi_o)) < t
+    assert om_f == pytest.approx(oh[steps - 1], rel=1e-10 if prec == "fp64" else 1e-6)
