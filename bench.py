@@ -119,6 +119,10 @@ def peaks():
 # Nominal dense ratios (tf32 1.1 PF vs bf16 2.25 PF per GPU) and the CUDA-core rates measured
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
+# DRAM traffic of one dominant-group update launch per block (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on a 16-block 40x40 capture: 729 MB; traffic grows with the blocks).
+# Valid for the tensor-core kernel as captured (profiles/update_tc_dominant_40x40.md).
+UPDATE_TC_BYTES_PER_BLOCK_N1600 = 729.0e6 / 16
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
@@ -136,6 +140,20 @@ def roofline_for(prec: str, achieved_tflops: float, traffic):
     return {"bound": bound, "achieved": round(achieved_tflops, 3), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved_tflops / peak, 4), "traffic": traffic,
             "kernel": "update (rank-nb Gauss-Jordan contraction)", "peak_source": note}
+
+
+def aggregate_replicas(ms_local: float, steps: int, world: int):
+    """Max of the timed region over ranks and the job-wide throughput (replicas: every rank
+    processes `steps` steps of its own problem)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
 
 
 def run_ours(args):
@@ -178,24 +196,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1)
     launches = api.kernel_launches() - l0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate_replicas(e0.elapsed_time(e1), args.steps, world)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
 
     # ---------------- per-kernel durations (CUDA events on the launching stream)
     ctx.profile(True)
     ctx.adam_step(1)
     prof = ctx.profile_read()
     ctx.profile(False)
+    # dominant kernel: the rank-nb update of the diagonally dominant blocks; its algorithmic
+    # flops per step are 8 N^2 kb per block per elimination step, summing to 8 N^3 per block
     upd_ms, upd_n = prof["update"]
-    flops_step = api.flops_per_grad(params)
-    achieved = flops_step / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    n_dom = 2 * wl.n_omega - api.pivoted_blocks(params)
+    flops_dom = 8.0 * float(params.N) ** 3 * n_dom
+    achieved = flops_dom / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    traffic = None
+    if prec == "3xtf32" and params.N == 1600:
+        traffic = round(UPDATE_TC_BYTES_PER_BLOCK_N1600 * n_dom, 0)  # bytes per launch
     per_kernel = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
     ctx.close()
 
@@ -258,7 +276,7 @@ def run_ours(args):
                        "final_omega": om, "final_gmax": gm},
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": roofline_for(prec, achieved, None),
+            "roofline": roofline_for(prec, achieved, traffic),
             "kernels_ms_one_step": per_kernel,
             "fp64_path": fp64,
             "clocks": clk,

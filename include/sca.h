@@ -254,11 +254,18 @@ sca_status sca_grad_noalloc_dev(const sca_params* params, const double* d_phi, d
  * stream before returning. */
 sca_status sca_set_stream(sca_ctx* ctx, void* stream);
 
+/* Bound of every device-side spin wait issued for this context (grid barriers of the fused
+ * small-block kernel), in SM clock cycles; 0 restores the default (4e9, about 2 s).  A wait
+ * that runs out makes the call return SCA_ETIMEOUT; the context stays usable. */
+sca_status sca_set_wait_limit(sca_ctx* ctx, int64_t cycles);
+
 /* Per-kernel timing.  While enabled, every launch of the context is bracketed by CUDA
  * events on the stream it is launched on, and the elapsed times are accumulated per kernel
- * kind when the calling API function synchronises.  Kinds: 0 assemble, 1 panel, 2 swap,
- * 3 trinv, 4 prep, 5 update (rank-nb contraction), 6 refine (adjoint diag(G)),
- * 7 reduce (+Adam).  Enabling resets the counters.  Timing adds a small host overhead per
+ * kind when the calling API function synchronises.  Kinds: 0 assemble, 1 pivoted panel,
+ * 2 row interchanges, 3 pivot-block inverse of the pivoted group, 4 rank-nb factors,
+ * 5 rank-nb update of the dominant blocks (the dominant contraction), 6 refine (adjoint
+ * diag(G)), 7 reduce (+Adam), 8 pivot-block inverse of the dominant blocks, 9 rank-nb update
+ * of the pivoted group, 10 fused small-block Adam launch.  Enabling resets the counters.  Timing adds a small host overhead per
  * launch; keep it off when measuring throughput. */
 sca_status sca_profile_enable(sca_ctx* ctx, int32_t enable);
 sca_status sca_profile_read(sca_ctx* ctx, int32_t kind, double* total_ms, uint64_t* launches);
@@ -266,6 +273,10 @@ sca_status sca_profile_read(sca_ctx* ctx, int32_t kind, double* total_ms, uint64
 /* Algorithmic floating-point operations of one gradient evaluation (all blocks, real flops,
  * complex multiply-add = 8): 8 N^3 per block for the Gauss-Jordan inversion. */
 double sca_flops_per_grad(const sca_params* params);
+
+/* Number of blocks that need partial pivoting (omega_n <= 4|t|, the lowest frequencies); the
+ * remaining blocks are strictly diagonally dominant by columns. */
+int32_t sca_pivoted_blocks(const sca_params* params);
 
 /* ------------------------------------------------------------------ misc -- */
 

@@ -69,9 +69,11 @@ SIGNATURES = [
     ("sca_server_destroy", None, [_vp]),
     ("sca_grad_noalloc_dev", ctypes.c_int, [_PP, _vp, _vp, _vp, _vp]),
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("sca_profile_enable", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_profile_read", ctypes.c_int, [_vp, ctypes.c_int32, _dp, _u64p]),
     ("sca_flops_per_grad", ctypes.c_double, [_PP]),
+    ("sca_pivoted_blocks", ctypes.c_int32, [_PP]),
     ("sca_last_error", ctypes.c_char_p, []),
     ("sca_version", ctypes.c_char_p, []),
     ("sca_kernel_launches", ctypes.c_uint64, []),

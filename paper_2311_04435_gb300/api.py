@@ -73,6 +73,10 @@ def flops_per_grad(params: Params) -> float:
     return float(_lib.lib().sca_flops_per_grad(ctypes.byref(params.c())))
 
 
+def pivoted_blocks(params: Params) -> int:
+    return int(_lib.lib().sca_pivoted_blocks(ctypes.byref(params.c())))
+
+
 def kernel_launches() -> int:
     return int(_lib.lib().sca_kernel_launches())
 
@@ -203,12 +207,17 @@ class Context:
                                           ctypes.c_void_p(grad_t.data_ptr()), self._stream()))
 
     # ---- streams and per-kernel timing
-    KINDS = ["assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce"]
+    KINDS = ["assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
+             "update_piv", "fused"]
 
     def set_stream(self, stream=None):
         """Enqueue on a torch.cuda.Stream (or raw handle); None restores the own stream."""
         h = None if stream is None else getattr(stream, "cuda_stream", stream)
         check(_lib.lib().sca_set_stream(self._h, ctypes.c_void_p(h) if h else None))
+
+    def set_wait_limit(self, cycles: int = 0):
+        """Bound (SM cycles) of device-side spin waits; 0 restores the default."""
+        check(_lib.lib().sca_set_wait_limit(self._h, int(cycles)))
 
     def profile(self, enable: bool = True):
         check(_lib.lib().sca_profile_enable(self._h, 1 if enable else 0))

@@ -155,7 +155,9 @@ sca_status allocate(Engine& e) {
   SCA_ALLOC(e.d_status, 8 * sizeof(double), "status");
   SCA_ALLOC(e.d_omega, 8 * sizeof(double), "omega");
   cudaError_t err = cudaMallocHost((void**)&e.h_status, 8 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMallocHost((void**)&e.h_flags, sizeof(int));
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMallocHost"); }
+  *e.h_flags = 0;
   err = cudaMemset(e.flags, 0, 16);
   if (err == cudaSuccess) err = cudaMemset(e.d_status, 0, 8 * sizeof(double));
   if (err == cudaSuccess) err = cudaMemset(e.d_m, 0, (size_t)e.N * sizeof(double));
@@ -245,6 +247,8 @@ void release(Engine& e) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_status) cudaFreeHost(e.h_status);
+  if (e.h_flags) cudaFreeHost(e.h_flags);
+  e.h_flags = nullptr;
   e.M = e.F = e.W = e.Tinv = nullptr;
   e.tt = nullptr;
   e.piv = e.perm = e.flags = nullptr;
@@ -261,6 +265,8 @@ namespace sca {
 sca_status sync_status(sca_ctx* c, cudaStream_t s) {
   cudaError_t err = cudaMemcpyAsync(c->e.h_status, c->e.d_status, 8 * sizeof(double),
                                     cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(c->e.h_flags, c->e.flags, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_fail(err, "status read-back");
   prof_collect(c->e);
@@ -268,8 +274,8 @@ sca_status sync_status(sca_ctx* c, cudaStream_t s) {
 }
 
 sca_status check_finite(sca_ctx* c) {
-  if (((int)c->e.h_status[6]) & 2) {
-    set_error("a bounded device-side wait in the tensor-core update ran out");
+  if ((((int)c->e.h_status[6]) & 2) || (*c->e.h_flags & 2)) {
+    set_error("a bounded device-side wait ran out");
     return SCA_ETIMEOUT;
   }
   if (c->e.h_status[4] != 0.0) {
@@ -652,6 +658,12 @@ sca_status sca_set_stream(sca_ctx* c, void* stream) {
   return SCA_OK;
 }
 
+sca_status sca_set_wait_limit(sca_ctx* c, int64_t cycles) {
+  if (!c || cycles < 0) { set_error("bad context or wait limit"); return SCA_EINVAL; }
+  c->e.wait_cycles = cycles ? (long long)cycles : 4000000000ll;
+  return SCA_OK;
+}
+
 sca_status sca_profile_enable(sca_ctx* c, int32_t enable) {
   if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
   if (!c->e.prof) {
@@ -679,6 +691,13 @@ double sca_flops_per_grad(const sca_params* p) {
   if (!p) return 0.0;
   const double N = (double)p->L * p->L;
   return 8.0 * N * N * N * 2.0 * p->n_omega;
+}
+
+int32_t sca_pivoted_blocks(const sca_params* p) {
+  if (validate(p) != SCA_OK) return -1;
+  Engine e;
+  plan(*p, e);
+  return e.piv_blocks;
 }
 
 const char* sca_last_error(void) { return t_err.c_str(); }

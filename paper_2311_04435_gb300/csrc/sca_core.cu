@@ -889,11 +889,11 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("diag");
     } else {
-      prof_begin(e, kPanel, s);
+      prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
       k_diag_gj<S, C, 1024><<<cnt, 1024, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
                                                   kb, nb, b0, e.ld, Tinv, TT, e.flags);
-      prof_end(e, kPanel, s);
+      prof_end(e, kDiag, s);
       SCA_LAUNCH_CHECK("diag");
     }
     if (!want_grad && kend == N) break;  // LU: nothing trails the last pivot block
@@ -926,7 +926,8 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kPrep, s);
       SCA_LAUNCH_CHECK("prep");
     }
-    prof_begin(e, kUpdate, s);
+    const int ukind = pivoted ? kUpdatePiv : kUpdate;
+    prof_begin(e, ukind, s);
     if (tcg) {
       sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s, nb);
       if (st != SCA_OK) return st;
@@ -936,7 +937,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
                                             fw_plane, e.fw_mat, r0, c0, k0, kb, want_grad ? 1 : 0);
       SCA_LAUNCH_CHECK("update");
     }
-    prof_end(e, kUpdate, s);
+    prof_end(e, ukind, s);
   }
   return SCA_OK;
 }

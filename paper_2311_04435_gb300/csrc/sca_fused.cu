@@ -24,7 +24,6 @@ namespace sca {
 namespace {
 
 constexpr int FT = 512;                            // threads per CTA
-constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 struct FusedArgs {
   int L, N, B, ksteps, do_adam;
@@ -33,6 +32,7 @@ struct FusedArgs {
   double *phi, *m, *v, *g, *gd, *ld, *status;
   unsigned* bar;  // [0] arrivals, [1] generation
   int* flags;
+  long long wait_cycles;
   double beta1, beta2, eps, grad_tol;
   double step[kMaxFusedSteps], sbc2[kMaxFusedSteps];
 };
@@ -55,7 +55,7 @@ __device__ bool grid_sync(const FusedArgs& a) {
       const long long t0 = clock64();
       while (*gen == g0) {
         if (*(volatile int*)a.flags & 2) { ok = 0; break; }
-        if (clock64() - t0 > kBarrierCycles) {
+        if (clock64() - t0 > a.wait_cycles) {
           atomicOr(a.flags, 2);
           ok = 0;
           break;
@@ -368,6 +368,7 @@ sca_status run_fused_adam(Engine& e, int nsteps, const AdamStep* steps, bool do_
   a.status = e.d_status;
   a.bar = e.fused_bar;
   a.flags = e.flags;
+  a.wait_cycles = e.wait_cycles;
   a.beta1 = steps ? steps[0].beta1 : 0.0;
   a.beta2 = steps ? steps[0].beta2 : 0.0;
   a.eps = steps ? steps[0].eps : 0.0;
@@ -381,9 +382,9 @@ sca_status run_fused_adam(Engine& e, int nsteps, const AdamStep* steps, bool do_
   if (err != cudaSuccess) return cuda_fail(err, "fused reset");
   void* args[] = {&a};
   auto kern = e.fp64 ? (void*)k_fused<double> : (void*)k_fused<float>;
-  prof_begin(e, kUpdate, s);
+  prof_begin(e, kFused, s);
   err = cudaLaunchCooperativeKernel(kern, dim3(e.fused_grid), dim3(FT), args, e.fused_smem, s);
-  prof_end(e, kUpdate, s);
+  prof_end(e, kFused, s);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (err != cudaSuccess) return cuda_fail(err, "fused launch");
   return SCA_OK;

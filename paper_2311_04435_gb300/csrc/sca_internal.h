@@ -66,10 +66,18 @@ struct Engine {
   int fused_grid = 0;               // CTAs of the fused small-block kernel (0: not eligible)
   size_t fused_smem = 0;
   unsigned* fused_bar = nullptr;    // grid-barrier counter and generation
+  long long wait_cycles = 4000000000ll;  // bound of device-side spin waits
+  int* h_flags = nullptr;           // pinned copy of the flags word
 };
 
 // Kernel kinds for per-launch timing.
-enum KernelKind { kAssemble = 0, kPanel, kSwap, kTrinv, kPrep, kUpdate, kRefine, kReduce, kKinds };
+enum KernelKind {
+  kAssemble = 0, kPanel, kSwap, kTrinv, kPrep, kUpdate, kRefine, kReduce,
+  kDiag,       // inverse of a dominant pivot block (Gauss-Jordan in registers)
+  kUpdatePiv,  // rank-nb update of the pivoted group
+  kFused,      // fused small-block Adam launch
+  kKinds
+};
 
 // Event bracketing of launches while profiling is on (no-ops otherwise).
 struct Profiler {

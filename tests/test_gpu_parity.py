@@ -252,3 +252,19 @@ def test_fused_persistent_adam_matches_blocked_path_and_oracle(L, nw, prec, monk
     assert np.max(np.abs(phi_f - phi_b)) < t
     assert np.max(np.abs(phi_f - phi_o)) < t
     assert om_f == pytest.approx(oh[steps - 1], rel=1e-10 if prec == "fp64" else 1e-6)
+
+
+def test_device_wait_timeout_is_reported_and_context_survives():
+    """Failure detection without a fault: a 1-cycle bound on the fused kernel's grid barrier
+    makes the waiting CTAs give up; the call returns SCA_ETIMEOUT (no hang) and the context
+    works again once the default bound is restored."""
+    p = api.Params(4, 64, U=6.0, T=0.1)  # 128 blocks -> many CTAs meeting at the barrier
+    with api.Context(p) as c:
+        c.adam_init(api.AdamConfig(lr=0.01, seed=0))
+        c.set_wait_limit(1)
+        with pytest.raises(Exception, match="SCA_ETIMEOUT"):
+            c.adam_step(2)
+        c.set_wait_limit(0)
+        c.adam_init(api.AdamConfig(lr=0.01, seed=0))
+        om, gm = c.adam_step(3)
+        assert np.isfinite(om) and np.isfinite(gm)
