@@ -119,10 +119,11 @@ def peaks():
 # Nominal dense ratios (tf32 1.1 PF vs bf16 2.25 PF per GPU) and the CUDA-core rates measured
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
-# DRAM traffic of one dominant-group update launch per block (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on a 16-block 40x40 capture: 729 MB; traffic grows with the blocks).
-# Valid for the tensor-core kernel as captured (profiles/update_tc_dominant_40x40.md).
-UPDATE_TC_BYTES_PER_BLOCK_N1600 = 729.0e6 / 16
+# DRAM traffic of one symmetric dominant-group update launch, per block (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 launches of one gradient
+# on a 16-block 40x40 case, divided by 16; traffic grows with the blocks).  None until
+# captured for the kernel as it stands.
+UPDATE_TC_BYTES_PER_BLOCK_N1600 = None
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
@@ -205,14 +206,18 @@ def run_ours(args):
     ctx.adam_step(1)
     prof = ctx.profile_read()
     ctx.profile(False)
-    # dominant kernel: the rank-nb update of the diagonally dominant blocks; its algorithmic
-    # flops per step are 8 N^2 kb per block per elimination step, summing to 8 N^3 per block
+    # dominant kernel: the rank-nb update of the diagonally dominant blocks.  On the tensor
+    # cores those blocks are updated symmetrically (they are complex symmetric and never
+    # pivoted): the algorithmic flops are 8 kb per lower-triangle entry per elimination step,
+    # 4 N^2 (N + 1) per block; the full update (CUDA cores, or SCA_SYM=0) needs 8 N^3.
     upd_ms, upd_n = prof["update"]
     n_dom = 2 * wl.n_omega - api.pivoted_blocks(params)
-    flops_dom = 8.0 * float(params.N) ** 3 * n_dom
+    N = float(params.N)
+    sym = prec == "3xtf32" and os.environ.get("SCA_SYM", "1") != "0"
+    flops_dom = (4.0 * N * N * (N + 1.0) if sym else 8.0 * N ** 3) * n_dom
     achieved = flops_dom / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
     traffic = None
-    if prec == "3xtf32" and params.N == 1600:
+    if sym and params.N == 1600 and UPDATE_TC_BYTES_PER_BLOCK_N1600:
         traffic = round(UPDATE_TC_BYTES_PER_BLOCK_N1600 * n_dom, 0)  # bytes per launch
     per_kernel = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
     ctx.close()

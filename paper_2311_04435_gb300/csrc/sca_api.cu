@@ -96,6 +96,8 @@ sca_status plan(const sca_params& p, Engine& e) {
   const size_t cbytes = e.fp64 ? 16 : 8;
   int nbp = 1;
   while (nbp * 2 <= e.nb && (size_t)e.N * (nbp * 2 + 1) * cbytes <= 220 * 1024) nbp *= 2;
+  // narrower than nb: the outer panel is factorised in sub-panels of at most 16 columns
+  if (nbp < e.nb) nbp = std::min(nbp, 16);
   e.nb_piv = nbp;
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;

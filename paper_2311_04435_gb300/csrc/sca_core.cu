@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "sca_internal.h"
@@ -59,6 +60,87 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
     perm[(size_t)mat * N + i] = i;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
+}
+
+// --------------------------------------------------------- panel-local update
+// Two-level blocking of the pivoted group: an outer panel of width kbo is factorised by
+// shared-memory sub-panels of width kbi; after each sub-panel [s0, s0+kbi) the rest of the outer
+// panel (columns [s0+kbi, c_end)) is brought up to date as in a right-looking LU:
+//   U12 = inv(L11) A12  (rows [s0, s0+kbi))       then    A22 -= L21 U12  (rows >= s0+kbi).
+// k_trsm_u12: one CTA per block, one thread per column of A12 (forward substitution with the
+// unit-lower L11 held in shared memory), U12 written in place.
+template <typename S, typename C>
+__global__ void k_trsm_u12(S* M, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
+                           int c_end) {
+  __shared__ cpx<C> Ls[16][17];
+  const int mat = blockIdx.x;
+  S* re = M + mat * mat_stride;
+  S* im = re + plane_stride;
+  for (int e = threadIdx.x; e < kbi * kbi; e += blockDim.x) {
+    const int r = e / kbi, c = e - r * kbi;
+    const size_t o = (size_t)(s0 + r) * ldm + s0 + c;
+    Ls[r][c] = {(C)re[o], (C)im[o]};
+  }
+  __syncthreads();
+  const int nc = c_end - (s0 + kbi);
+  for (int cc = threadIdx.x; cc < nc; cc += blockDim.x) {
+    const int col = s0 + kbi + cc;
+    cpx<C> u[16];
+    for (int r = 0; r < kbi; ++r) {
+      const size_t o = (size_t)(s0 + r) * ldm + col;
+      cpx<C> s = {(C)re[o], (C)im[o]};
+      for (int k = 0; k < r; ++k) {
+        const cpx<C> t = cmul(Ls[r][k], u[k]);
+        s.re -= t.re;
+        s.im -= t.im;
+      }
+      u[r] = s;
+      re[o] = (S)s.re;
+      im[o] = (S)s.im;
+    }
+  }
+}
+
+// k_gemm_panel: A22[r][c] -= sum_k L21[r][k] U12[k][c] for rows r >= s0+kbi (64 per CTA),
+// columns [s0+kbi, c_end), K = kbi <= 16; U12 staged in shared memory.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256)
+    k_gemm_panel(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
+                 int c_end) {
+  constexpr int NCMAX = sizeof(C) == 8 ? 64 : 128;
+  __shared__ cpx<C> Us[16][NCMAX];
+  __shared__ cpx<C> Ls[64][17];
+  const int mat = blockIdx.y;
+  const int c0 = s0 + kbi, nc = c_end - c0;
+  const int r0 = c0 + blockIdx.x * 64;
+  S* re = M + mat * mat_stride;
+  S* im = re + plane_stride;
+  for (int e = threadIdx.x; e < kbi * nc; e += 256) {
+    const int k = e / nc, c = e - k * nc;
+    const size_t o = (size_t)(s0 + k) * ldm + c0 + c;
+    Us[k][c] = {(C)re[o], (C)im[o]};
+  }
+  for (int e = threadIdx.x; e < 64 * kbi; e += 256) {
+    const int r = e / kbi, k = e - r * kbi;
+    const int gr = r0 + r;
+    Ls[r][k] = (gr < N) ? cpx<C>{(C)re[(size_t)gr * ldm + s0 + k], (C)im[(size_t)gr * ldm + s0 + k]}
+                        : cpx<C>{(C)0, (C)0};
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * nc; e += 256) {
+    const int r = e / nc, c = e - r * nc;
+    const int gr = r0 + r;
+    if (gr >= N) continue;
+    const size_t o = (size_t)gr * ldm + c0 + c;
+    cpx<C> a = {(C)re[o], (C)im[o]};
+    for (int k = 0; k < kbi; ++k) {
+      const cpx<C> l = Ls[r][k], u = Us[k][c];
+      a.re -= l.re * u.re - l.im * u.im;
+      a.im -= l.re * u.im + l.im * u.re;
+    }
+    re[o] = (S)a.re;
+    im[o] = (S)a.im;
+  }
 }
 
 // ---------------------------------------------------------------------- swap
@@ -299,11 +381,13 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
                                                 int* flags) {
   // The block is padded to KB x KB with the identity (pivots 1: no effect on ln|det|; the
   // padded inverse is diag(T, I)), so the thread -> (row, column) map is compile-time:
-  // column j = tid % KB, rows r = tid / KB + q * RS.
+  // column j = tid % KB, rows r = tid / KB + q * RS.  The owners of row / column c + 1
+  // publish them into the other half of a double buffer right after their own update of
+  // sweep c, so each sweep needs a single barrier.
   constexpr int KB = sizeof(C) == 8 ? 64 : 128;
   constexpr int RS = NT / KB;
-  constexpr int MAXR = KB / RS;
-  __shared__ cpx<C> prow[KB], pcol[KB];
+  constexpr int MAXR = (KB + RS - 1) / RS;
+  __shared__ cpx<C> prow[2][KB], pcol[2][KB];
   __shared__ double piv2[KB];
   const int mat = blockIdx.x, tid = threadIdx.x;
   const int j = tid % KB, rg = tid / KB;
@@ -320,28 +404,35 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
       a[q] = {(C)(r == j ? 1 : 0), (C)0};
     }
   }
-  for (int c = 0; c < KB; ++c) {
-    // the owners of row c and of column c publish them
+  // publish row / column 0
 #pragma unroll
-    for (int q = 0; q < MAXR; ++q) {
-      if (rg + q * RS == c) prow[j] = a[q];
-      if (j == c) pcol[rg + q * RS] = a[q];
-    }
-    __syncthreads();
-    const cpx<C> d = pcol[c];
+  for (int q = 0; q < MAXR; ++q) {
+    const int r = rg + q * RS;
+    if (r == 0) prow[0][j] = a[q];
+    if (j == 0 && r < KB) pcol[0][r] = a[q];
+  }
+  __syncthreads();
+  for (int c = 0; c < KB; ++c) {
+    const int cb = c & 1, nbuf = cb ^ 1;
+    const cpx<C> d = pcol[cb][c];
     const C m2 = d.re * d.re + d.im * d.im;
     const cpx<C> dinv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
     if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
     // u_j = prow_j / d (j != c), u_c = 1/d; new = (r == c) ? u_j : (j == c ? 0 : a) - pcol_r u_j
     const bool jc = (j == c);
-    const cpx<C> u = jc ? dinv : cmul(prow[j], dinv);
+    const cpx<C> u = jc ? dinv : cmul(prow[cb][j], dinv);
 #pragma unroll
     for (int q = 0; q < MAXR; ++q) {
-      const cpx<C> l = pcol[rg + q * RS];
+      const int r = rg + q * RS;
+      if (r >= KB) continue;
+      const cpx<C> l = pcol[cb][r];
       cpx<C> v = jc ? cpx<C>{(C)0, (C)0} : a[q];
       v.re -= l.re * u.re - l.im * u.im;
       v.im -= l.re * u.im + l.im * u.re;
-      a[q] = (rg + q * RS == c) ? u : v;
+      a[q] = (r == c) ? u : v;
+      // publish the next pivot row / column from the freshly updated values
+      if (r == c + 1) prow[nbuf][j] = a[q];
+      if (j == c + 1) pcol[nbuf][r] = a[q];
     }
     __syncthreads();
   }
@@ -374,9 +465,10 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
 // Fs[i][k] = split(M[i][k0 + k]) (planes re_hi, im_hi, re_lo, im_lo; N x nb, zero for k >= kb).
 template <typename S>
 __global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride,
-                             int k0, int kb, int nb, float* Fs, size_t fs_plane, size_t fs_mat) {
+                             int k0, int kb, int nb, float* Fs, size_t fs_plane, size_t fs_mat,
+                             int r_begin) {
   const int mat = blockIdx.y;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)r_begin * nb + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (size_t)N * nb) return;
   const int i = (int)(e / nb), k = (int)(e - (size_t)i * nb);
   const S* re = M + mat * mat_stride;
@@ -390,6 +482,70 @@ __global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size
   const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
   float* o = Fs + (size_t)mat * fs_mat + e;
   o[0] = hr; o[fs_plane] = hi; o[2 * fs_plane] = fr - hr; o[3 * fs_plane] = fi - hi;
+}
+
+// Symmetric dominant blocks.  A_{n,sigma} is complex symmetric and the dominant blocks are
+// never pivoted, so after sweeping the index set S the tableau satisfies
+// M_ij = eps_ij M_ji with eps_ij = -1 when exactly one of i, j is in S, +1 otherwise.  The
+// tensor-core update then computes only the tiles on or below the diagonal; reads that would
+// touch an upper tile are redirected to the transposed lower entry with that sign.
+
+// Split copy of the pivot columns for swept rows i < k0: M[i][k0 + k] = -M[k0 + k][i]
+// (row block K, column i: a lower-triangle entry), transposed through shared memory.
+template <typename S>
+__global__ void k_split_cols_swept(const S* M, int ldm, size_t mat_stride, size_t plane_stride,
+                                   int k0, int kb, int nb, float* Fs, size_t fs_plane,
+                                   size_t fs_mat) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int mat = blockIdx.z;
+  const int i0 = blockIdx.x * 32, kk0 = blockIdx.y * 32;
+  const S* re = M + mat * mat_stride;
+  const S* im = re + plane_stride;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
+  for (int k = ty; k < 32; k += 8) {
+    const int gk = kk0 + k, gi = i0 + tx;
+    const bool in = gk < kb && gi < k0;
+    tr[k][tx] = in ? -(float)re[(size_t)(k0 + gk) * ldm + gi] : 0.f;
+    ti[k][tx] = in ? -(float)im[(size_t)(k0 + gk) * ldm + gi] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = i0 + r, gk = kk0 + tx;
+    if (gi >= k0 || gk >= nb) continue;
+    const float fr = tr[tx][r], fi = ti[tx][r];
+    const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
+    const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
+    float* o = Fs + (size_t)mat * fs_mat + (size_t)gi * nb + gk;
+    o[0] = hr; o[fs_plane] = hi; o[2 * fs_plane] = fr - hr; o[3 * fs_plane] = fi - hi;
+  }
+}
+
+// Completes the fully swept (symmetric) inverse: M[i][j] = M[j][i] for i < j, 32x32 tiles
+// through shared memory.
+template <typename S>
+__global__ void k_mirror(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride) {
+  __shared__ S tr[32][33], ti[32][33];
+  const int mat = blockIdx.z;
+  const int bi = blockIdx.y, bj = blockIdx.x;  // destination tile (bi, bj), bi <= bj
+  if (bi > bj) return;
+  S* re = M + mat * mat_stride;
+  S* im = re + plane_stride;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {  // source: tile (bj, bi), rows bj*32 + r
+    const int gr = bj * 32 + r, gc = bi * 32 + tx;
+    if (gr < N && gc < N) {
+      tr[r][tx] = re[(size_t)gr * ldm + gc];
+      ti[r][tx] = im[(size_t)gr * ldm + gc];
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = bi * 32 + r, gj = bj * 32 + tx;
+    if (gi < N && gj < N && gi < gj) {
+      re[(size_t)gi * ldm + gj] = tr[tx][r];
+      im[(size_t)gi * ldm + gj] = ti[tx][r];
+    }
+  }
 }
 
 // F planes for the update from the tensor-core product Fp = M[:, K] T (planar re, im; N x nb):
@@ -547,7 +703,8 @@ __global__ void __launch_bounds__(256)
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_prep_w(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
-             int nb, S* W, size_t fw_plane, size_t fw_mat, int c_begin, int gj, int split) {
+             int nb, S* W, size_t fw_plane, size_t fw_mat, int c_begin, int gj, int split,
+             int sym) {
   extern __shared__ unsigned char smem_raw[];
   S* tr = reinterpret_cast<S*>(smem_raw);  // [nb][65]
   S* ti = tr + (size_t)nb * 65;
@@ -555,12 +712,23 @@ __global__ void __launch_bounds__(256)
   const int j0 = c_begin + blockIdx.x * 64;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  for (int e = threadIdx.x; e < nb * 64; e += 256) {
-    const int c = e >> 6, jj = e & 63;
-    const int j = j0 + jj;
-    const bool in = c < kb && j < N;
-    tr[c * 65 + jj] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
-    ti[c * 65 + jj] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+  if (sym && j0 >= k0 + kb) {
+    // columns past K sit in upper tiles: M[K][j] = M[j][K] (both unswept)
+    for (int e = threadIdx.x; e < nb * 64; e += 256) {
+      const int jj = e / nb, c = e - jj * nb;
+      const int j = j0 + jj;
+      const bool in = c < kb && j < N;
+      tr[c * 65 + jj] = in ? re[(size_t)j * ldm + k0 + c] : (S)0;
+      ti[c * 65 + jj] = in ? im[(size_t)j * ldm + k0 + c] : (S)0;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nb * 64; e += 256) {
+      const int c = e >> 6, jj = e & 63;
+      const int j = j0 + jj;
+      const bool in = c < kb && j < N;
+      tr[c * 65 + jj] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
+      ti[c * 65 + jj] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+    }
   }
   __syncthreads();
   S* out = W + (size_t)mat * fw_mat;
@@ -862,24 +1030,44 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   int* perm = e.perm + (size_t)m0 * N;
   const size_t fw_plane = (size_t)N * nb;
   const int split = tcg ? 1 : 0;
+  // dominant blocks on the tensor cores: symmetric updates (lower tiles only)
+  bool sym = tcg && !pivoted && e.tt != nullptr;
+  if (const char* v = std::getenv("SCA_SYM"))
+    if (std::atoi(v) == 0) sym = false;
   for (int k0 = 0; k0 < N; k0 += nb) {
     const int kb = std::min(nb, N - k0);
     const int kend = k0 + kb;
     if (pivoted) {
-      const size_t sm = sizeof(cpx<C>) * (size_t)(N - k0) * (kb + 1);
-      prof_begin(e, kPanel, s);
-      k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
-                                                    k0, kb, b0, e.ld, piv, perm, e.flags);
-      prof_end(e, kPanel, s);
-      SCA_LAUNCH_CHECK("panel");
+      // outer panel [k0, kend) factorised by shared-memory sub-panels of width nbi
+      const int nbi = std::min(e.nb_piv, kb);
+      for (int s0 = k0; s0 < kend; s0 += nbi) {
+        const int kbi = std::min(nbi, kend - s0);
+        const size_t sm = sizeof(cpx<C>) * (size_t)(N - s0) * (kbi + 1);
+        prof_begin(e, kPanel, s);
+        k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
+                                                      s0, kbi, b0, e.ld, piv, perm, e.flags);
+        prof_end(e, kPanel, s);
+        SCA_LAUNCH_CHECK("panel");
+        if (!want_grad && s0 + kbi == N) break;
+        const int jstart = want_grad ? 0 : k0;
+        const int ncols = N - jstart;
+        prof_begin(e, kSwap, s);
+        k_swap<S><<<dim3((ncols + 255) / 256, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
+                                                                   e.plane_stride, s0, kbi, jstart,
+                                                                   piv);
+        prof_end(e, kSwap, s);
+        SCA_LAUNCH_CHECK("swap");
+        if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
+          prof_begin(e, kTrinv, s);
+          k_trsm_u12<S, C><<<cnt, 128, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, s0, kbi,
+                                                kend);
+          k_gemm_panel<S, C><<<dim3((N - s0 - kbi + 63) / 64, cnt), 256, 0, s>>>(
+              M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, kend);
+          prof_end(e, kTrinv, s);
+          SCA_LAUNCH_CHECK("panel update");
+        }
+      }
       if (!want_grad && kend == N) break;
-      const int jstart = want_grad ? 0 : kend;
-      const int ncols = N - jstart;
-      prof_begin(e, kSwap, s);
-      k_swap<S><<<dim3((ncols + 255) / 256, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
-                                                                 e.plane_stride, k0, kb, jstart, piv);
-      prof_end(e, kSwap, s);
-      SCA_LAUNCH_CHECK("swap");
     }
     if (pivoted) {
       const size_t sm = sizeof(cpx<C>) * ((size_t)kb * (kb + 1) + kb);
@@ -891,8 +1079,8 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     } else {
       prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
-      k_diag_gj<S, C, 1024><<<cnt, 1024, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
-                                                  kb, nb, b0, e.ld, Tinv, TT, e.flags);
+      k_diag_gj<S, C, 768><<<cnt, 768, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
+                                                kb, nb, b0, e.ld, Tinv, TT, e.flags);
       prof_end(e, kDiag, s);
       SCA_LAUNCH_CHECK("diag");
     }
@@ -902,11 +1090,18 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_begin(e, kPrep, s);
       if (tcg && !pivoted && nb == e.nb && e.tt) {
         // F = M[:, K] T on the tensor cores (scratch: the W planes, rewritten below)
-        const size_t tot = (size_t)N * nb;
+        const int rs = sym ? std::max(r0, k0) : r0;  // swept rows come from row block K
+        const size_t tot = (size_t)(N - rs) * nb;
         k_split_cols<S><<<dim3((unsigned)((tot + 255) / 256), cnt), 256, 0, s>>>(
             M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
-            fw_plane, e.fw_mat);
+            fw_plane, e.fw_mat, rs);
         SCA_LAUNCH_CHECK("split cols");
+        if (sym && r0 < k0) {
+          k_split_cols_swept<S><<<dim3((k0 - r0 + 31) / 32, (nb + 31) / 32, cnt), 256, 0, s>>>(
+              M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
+              fw_plane, e.fw_mat);
+          SCA_LAUNCH_CHECK("split cols swept");
+        }
         sca_status st = tc_prep(e, m0, cnt, r0, s);
         if (st != SCA_OK) return st;
         const size_t rem = (size_t)(N - r0) * nb;
@@ -922,14 +1117,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
       k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
-          want_grad ? 1 : 0, split);
+          want_grad ? 1 : 0, split, sym ? 1 : 0);
       prof_end(e, kPrep, s);
       SCA_LAUNCH_CHECK("prep");
     }
     const int ukind = pivoted ? kUpdatePiv : kUpdate;
     prof_begin(e, ukind, s);
     if (tcg) {
-      sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s, nb);
+      sca_status st = tc_update(e, m0, cnt, k0, kb, r0, c0, want_grad, s, nb, sym);
       if (st != SCA_OK) return st;
     } else {
       dim3 grid((N - c0 + 63) / 64, (N - r0 + 63) / 64, cnt);
@@ -938,6 +1133,13 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       SCA_LAUNCH_CHECK("update");
     }
     prof_end(e, ukind, s);
+  }
+  if (sym && want_grad) {  // the fully swept inverse is symmetric: fill the upper tiles
+    const int nt = (N + 31) / 32;
+    prof_begin(e, kPrep, s);
+    k_mirror<S><<<dim3(nt, nt, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride);
+    prof_end(e, kPrep, s);
+    SCA_LAUNCH_CHECK("mirror");
   }
   return SCA_OK;
 }
@@ -974,8 +1176,7 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       sp = e.side;
     }
     sca_status st;
-    const bool tcp = e.tc && tc_piv_ok(e);
-    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb_piv, tcp, want_grad, sp)) != SCA_OK)
+    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
       return st;
     if (nd > 0 && (st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s)) != SCA_OK)
       return st;

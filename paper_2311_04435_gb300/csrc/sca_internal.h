@@ -137,8 +137,7 @@ bool tc_supported();
 sca_status tc_prepare(Engine& e);
 void tc_release(Engine& e);
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
-                     cudaStream_t s, int nbk);
-bool tc_piv_ok(const Engine& e);
+                     cudaStream_t s, int nbk, bool sym = false);
 sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's launches  // tensor-core maps exist for the pivoted group's width
 // F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);

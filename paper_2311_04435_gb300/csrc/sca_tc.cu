@@ -204,8 +204,28 @@ struct TcArgs {
   int mat0;                            // workspace slot of the first block
   int m_zmul, m_zoff;                  // output map plane index: (mat0+mat)*m_zmul + m_zoff + p
   int* counter;                        // tile counter (zero before the launch)
+  int sym;                             // lower-triangle tiles only (tiles_m == tiles_n)
+  int per_block;                       // tiles per block
   int* err;                            // device error word (bit 1: wait time-out)
 };
+
+// Tile t -> (block, tile row, tile column).  With `sym` only tiles on or below the diagonal
+// exist (the dominant blocks stay symmetric up to sign, see the host code): rem ->
+// (i, j) with rem = i (i + 1) / 2 + j, j <= i.
+__device__ __forceinline__ void decode_tile(const TcArgs& a, int t, int& mat, int& tm, int& tn) {
+  mat = t / a.per_block;
+  const int rem = t - mat * a.per_block;
+  if (!a.sym) {
+    tm = rem / a.tiles_n;
+    tn = rem - tm * a.tiles_n;
+    return;
+  }
+  int i = (int)((sqrtf(8.0f * (float)rem + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= rem) ++i;
+  while (i * (i + 1) / 2 > rem) --i;
+  tm = i;
+  tn = rem - i * (i + 1) / 2;
+}
 
 // Shared-memory stage layout (each slot one 128 x 16 float plane, 8 KB, 1024-aligned):
 //   0 F_re_hi  1 F_im_hi  2 F_re_lo  3 F_im_lo
@@ -276,9 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(&rfull[rslot]);
         if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
         if (t < 0) break;
-        const int mat = t / (a.tiles_m * a.tiles_n);
-        const int rem = t - mat * a.tiles_m * a.tiles_n;
-        const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+        int mat, tm, tn;
+        decode_tile(a, t, mat, tm, tn);
         const int frow = a.r0 + tm * kBM, wrow = a.c0 + tn * kBNc;
         for (int ks = 0; ks < ksteps; ++ks) {
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
@@ -369,9 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     // issue the load of chunk c of tile t into staging buffer eb
     auto issue_load = [&](int t, int c, int eb) {
-      const int mat = t / (a.tiles_m * a.tiles_n);
-      const int rem = t - mat * a.tiles_m * a.tiles_n;
-      const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+      int mat, tm, tn;
+      decode_tile(a, t, mat, tm, tn);
       const int x = a.c0 + tn * kBNc + c * kEpiCols, y = a.r0 + tm * kBM;
       bulk_wait_read0();  // the store that last read this buffer has finished reading it
       pending[eb] = true;
@@ -394,9 +412,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (leader && prefetched != t) issue_load(t, 0, ebuf);
       const int buf = iter & 1;
       const uint32_t use = (uint32_t)(iter >> 1);
-      const int mat = t / (a.tiles_m * a.tiles_n);
-      const int rem = t - mat * a.tiles_m * a.tiles_n;
-      const int tm = rem / a.tiles_n, tn = rem - tm * a.tiles_n;
+      int mat, tm, tn;
+      decode_tile(a, t, mat, tm, tn);
       const int i = a.r0 + tm * kBM + row;
       const int j0 = a.c0 + tn * kBNc;
       const bool rowk = a.gj && i >= a.k0 && i < a.k0 + a.kb;
@@ -508,11 +525,9 @@ EncodeTiledFn encode_fn() {
 
 struct TcMaps {
   CUtensorMap F, W;    // rank-nb factors, K extent nb
-  CUtensorMap Fp, Wp;  // rank-nb factors, K extent nb_piv (pivoted group)
   CUtensorMap M;       // the blocks, for the epilogue
   CUtensorMap TT;      // -T^T split planes (nb x nb per block): B of F = M[:, K] T
   CUtensorMap FP;      // planar F = M[:, K] T (W scratch planes 4, 5): output of that product
-  bool piv_ok = false;
   int sms = 0;
 };
 
@@ -586,8 +601,6 @@ sca_status tc_prepare(Engine& e) {
   TcMaps* t = new TcMaps();
   std::memset(&t->F, 0, sizeof(t->F));
   std::memset(&t->W, 0, sizeof(t->W));
-  std::memset(&t->Fp, 0, sizeof(t->Fp));
-  std::memset(&t->Wp, 0, sizeof(t->Wp));
   std::memset(&t->M, 0, sizeof(t->M));
   const long long zf = (long long)e.chunk * (long long)(e.fw_mat / e.fw_plane);
   if (!make_fw_map(&t->F, e.F, e.nb, e.N, zf) || !make_fw_map(&t->W, e.W, e.nb, e.N, zf) ||
@@ -607,12 +620,6 @@ sca_status tc_prepare(Engine& e) {
       set_error("cuTensorMapEncodeTiled failed for the tensor-core prep product");
       return SCA_ECUDA;
     }
-  }
-  if (e.nb_piv % kKS == 0) {
-    const size_t fwp = (size_t)e.N * e.nb_piv;
-    const long long zp = (long long)e.chunk * (long long)(e.fw_mat / fwp);
-    t->piv_ok = make_fw_map(&t->Fp, e.F, e.nb_piv, e.N, zp) &&
-                make_fw_map(&t->Wp, e.W, e.nb_piv, e.N, zp);
   }
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -642,15 +649,10 @@ void tc_release(Engine& e) {
   e.tmap = nullptr;
 }
 
-bool tc_piv_ok(const Engine& e) {
-  const TcMaps* t = static_cast<const TcMaps*>(e.tmap);
-  return t && t->piv_ok;
-}
-
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
-                     cudaStream_t s, int nbk) {
+                     cudaStream_t s, int nbk, bool sym) {
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
-  if (!t || (nbk != e.nb && !(nbk == e.nb_piv && t->piv_ok))) {
+  if (!t || nbk != e.nb) {
     set_error("tcgen05 update used before tc_prepare or with an unsupported K extent");
     return SCA_ENOSTATE;
   }
@@ -669,7 +671,9 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.gj = gj ? 1 : 0;
   a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
   a.tiles_n = (e.N - c0 + kBNc - 1) / kBNc;
-  a.tiles = a.tiles_m * a.tiles_n * cnt;
+  a.sym = (sym && r0 == c0) ? 1 : 0;
+  a.per_block = a.sym ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  a.tiles = a.per_block * cnt;
   a.fplanes = a.wplanes = (int)(e.fw_mat / ((size_t)e.N * nbk));
   a.m_zmul = 2;
   a.m_zoff = 0;
@@ -681,8 +685,7 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, t->sms);
-  const bool pv = (nbk != e.nb);
-  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(pv ? t->Fp : t->F, pv ? t->Wp : t->W, t->M, a);
+  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 update launch");
@@ -710,7 +713,9 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   a.gj = 1;
   a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
   a.tiles_n = (e.nb + kBNc - 1) / kBNc;
-  a.tiles = a.tiles_m * a.tiles_n * cnt;
+  a.sym = 0;
+  a.per_block = a.tiles_m * a.tiles_n;
+  a.tiles = a.per_block * cnt;
   a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W scratch planes 0-3
   a.wplanes = 6;                             // B: -T^T planes
   a.mat0 = m0;

@@ -268,3 +268,28 @@ def test_device_wait_timeout_is_reported_and_context_survives():
         c.adam_init(api.AdamConfig(lr=0.01, seed=0))
         om, gm = c.adam_step(3)
         assert np.isfinite(om) and np.isfinite(gm)
+
+
+@pytest.mark.gpu
+def test_symmetric_update_matches_full_update(monkeypatch):
+    """The dominant blocks' lower-triangle (symmetric) tensor-core update gives the same
+    log-dets, diag(G) and gradient as the full update, and both match the oracle.  400 x 400
+    blocks span four tiles per side with a ragged last one."""
+    p = api.Params(20, 10, U=4.0, T=0.1, delta=0.5, prec="3xtf32")
+    phi = inputs.seed_phi(3, p.N)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCA_SYM", flag)
+        with api.Context(p) as c:
+            ld, gd = c.blocks(phi, grad=True)
+            om_lu = c.potential(phi)
+            om, g = c.grad(phi)
+        res[flag] = (ld, gd, om_lu, om, g)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol("3xtf32")
+    for ld, gd, om_lu, om, g in res.values():
+        assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+        assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+        assert om == pytest.approx(o_om, rel=t["om"]) and om_lu == pytest.approx(o_om, rel=t["om"])
+        assert np.max(np.abs(g - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
+    assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 2 * t["g"] * max(1.0, np.abs(o_gd).max())
