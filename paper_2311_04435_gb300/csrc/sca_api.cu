@@ -19,6 +19,10 @@ std::atomic<uint64_t> g_launches{0};
 
 namespace {
 thread_local std::string t_err;
+
+// SMs the dominant group's persistent tensor-core launches leave free while the pivoted
+// group runs beside them on its own (high-priority) stream.
+constexpr int kDefaultSmReserve = 8;
 }
 
 void set_error(const std::string& msg) { t_err = msg; }
@@ -171,7 +175,17 @@ sca_status allocate(Engine& e) {
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
 #undef SCA_ALLOC
   if ((st = fused_prepare(e)) != SCA_OK) { release(e); return st; }
-  err = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking);
+  if (e.tc && e.piv_blocks > 0) {
+    // SMs kept free for the pivoted group (SCA_SM_RESERVE overrides the default)
+    int r = kDefaultSmReserve;
+    if (const char* v = std::getenv("SCA_SM_RESERVE")) r = std::atoi(v);
+    e.sm_reserve = std::max(0, std::min(r, tc_sms(e) / 2));
+  }
+  {  // the pivoted group is the latency-bound chain: its stream takes the highest priority
+    int least = 0, greatest = 0;
+    err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&e.side, cudaStreamNonBlocking, greatest);
+  }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }

@@ -890,6 +890,56 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
   }
 }
 
+// The same refinement for unpivoted blocks (X = R, no permutation): each warp reads its row
+// straight from the inverse, the bond partners x_{j+L} and x_{j+1} come through L1, and only
+// the double-float a_j sit in shared memory, so the kernel runs at full occupancy and is
+// bound by the single read of the inverses.  The arithmetic and its order per row are those
+// of k_refine.
+constexpr int kRefineRowsPerCta = 32;
+__global__ void __launch_bounds__(256)
+    k_refine_direct(const float* __restrict__ M, int ldm, size_t mat_stride, size_t plane_stride,
+                    int b0, Lattice la, double* __restrict__ gd) {
+  extern __shared__ unsigned char smem_raw[];
+  dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
+  const int N = la.N, L = la.L;
+  const int mat = blockIdx.y, b = b0 + mat, n = b >> 1, sg = (b & 1) ? -1 : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = ds_of(la.mu - site_energy(la, r, sg));
+  __syncthreads();
+  const float* re0 = M + mat * mat_stride;
+  const float* im0 = re0 + plane_stride;
+  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const int dxs = 32 / L, dys = 32 % L;
+  const int i_end = min(N, (int)(blockIdx.x + 1) * kRefineRowsPerCta);
+  for (int i = blockIdx.x * kRefineRowsPerCta + warp; i < i_end; i += 8) {
+    const float* re = re0 + (size_t)i * ldm;
+    const float* im = im0 + (size_t)i * ldm;
+    dsf acc = {0.f, 0.f};
+    int xx = lane / L, yy = lane - (lane / L) * L;
+    for (int j = lane; j < N; j += 32) {
+      const int jx = (xx + 1 == L) ? yy : j + L;
+      const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
+      const float a = re[j], bq = im[j];
+      const float ax = re[jx], bx = im[jx];
+      const float ay = re[jy], by = im[jy];
+      const dsf q = ds_sub(two_prod(a, a), two_prod(bq, bq));
+      const dsf ab = two_prod(a, bq);
+      const dsf u = ds_add(ds_sub(two_prod(a, ax), two_prod(bq, bx)),
+                           ds_sub(two_prod(a, ay), two_prod(bq, by)));
+      const dsf e = ds_add(ds_sub(ds_mul(adiag[j], q), ds_mul(w2, ab)), ds_mul(t2, u));
+      acc = ds_add(acc, e);
+      yy += dys;
+      xx += dxs;
+      if (yy >= L) { yy -= L; xx += 1; }
+    }
+    double qsum = (double)acc.h + (double)acc.l;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, off);
+    if (lane == 0) gd[(size_t)b * N + i] = sg * (2.0 * (double)re[i] - qsum);
+  }
+}
+
 // -------------------------------------------------------------- reduce/Adam
 // Omega = sum_i phi_i^2/U - 2T sum_b ld_b ; g_i = 2 phi_i/U - 2T sum_b gd[b, i] (b ascending);
 // then, if Adam is on and max|g| >= grad_tol, the update of phi in PyTorch's order
@@ -992,26 +1042,42 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
     if (err__ != cudaSuccess) return cuda_fail(err__, where);     \
   } while (0)
 
+// diag(G) of the workspace slots m0 .. m0+cnt-1 (global blocks b0 + m0 ..): pivoted blocks
+// through the permutation (k_refine), unpivoted ones by the direct kernel.
 template <typename S>
-sca_status launch_refine(Engine& e, const Lattice& la, int b0, int cnt, cudaStream_t s) {
+sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, cudaStream_t s) {
+  if (cnt <= 0) return SCA_OK;
   const int N = e.N;
-  S* M = static_cast<S*>(e.M);
+  S* M = static_cast<S*>(e.M) + (size_t)m0 * e.mat_stride;
+  const int* perm = e.perm + (size_t)m0 * N;
+  const int bg = b0 + m0;
   const size_t perm_bytes = ((N * sizeof(int) + 15) / 16) * 16;
   prof_begin(e, kRefine, s);
-  if (e.refine) {
-    const size_t fixed = perm_bytes + (size_t)N * 2 * sizeof(float);
-    const size_t row_bytes = (size_t)N * sizeof(cpx<S>);
-    const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (kRefineSmem - fixed) / row_bytes));
-    const int gx = std::max(1, std::min((N + warps - 1) / warps, 32));
-    k_refine<S><<<dim3(gx, cnt), warps * 32, fixed + warps * row_bytes, s>>>(
-        M, e.ldm, e.mat_stride, e.plane_stride, b0, la, e.perm, e.gd, 1);
+  if (e.refine && sizeof(S) == 4) {
+    const int np = std::max(0, std::min(cnt, e.piv_blocks - bg));
+    if (np > 0) {
+      const size_t fixed = perm_bytes + (size_t)N * 2 * sizeof(float);
+      const size_t row_bytes = (size_t)N * sizeof(cpx<S>);
+      const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (kRefineSmem - fixed) / row_bytes));
+      const int gx = std::max(1, std::min((N + warps - 1) / warps, 32));
+      k_refine<S><<<dim3(gx, np), warps * 32, fixed + warps * row_bytes, s>>>(
+          M, e.ldm, e.mat_stride, e.plane_stride, bg, la, perm, e.gd, 1);
+      SCA_LAUNCH_CHECK("refine");
+    }
+    if (cnt > np) {
+      const int gx = (N + kRefineRowsPerCta - 1) / kRefineRowsPerCta;
+      k_refine_direct<<<dim3(gx, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
+          reinterpret_cast<const float*>(M) + (size_t)np * e.mat_stride, e.ldm, e.mat_stride,
+          e.plane_stride, bg + np, la, e.gd);
+      SCA_LAUNCH_CHECK("refine direct");
+    }
   } else {
     const int gx = std::max(1, std::min((N + 255) / 256, 16));
     k_refine<S><<<dim3(gx, cnt), 256, perm_bytes, s>>>(M, e.ldm, e.mat_stride, e.plane_stride,
-                                                       b0, la, e.perm, e.gd, 0);
+                                                       bg, la, perm, e.gd, 0);
+    SCA_LAUNCH_CHECK("refine");
   }
   prof_end(e, kRefine, s);
-  SCA_LAUNCH_CHECK("refine");
   return SCA_OK;
 }
 
@@ -1176,16 +1242,25 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       sp = e.side;
     }
     sca_status st;
+    // While both groups run, the dominant group's persistent tensor-core launches leave
+    // sm_reserve SMs to the pivoted group's kernels.
+    e.tc_cap = 0;
     if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
       return st;
-    if (nd > 0 && (st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s)) != SCA_OK)
-      return st;
+    if (fork && e.sm_reserve > 0 && e.tmap) e.tc_cap = tc_sms(e) - e.sm_reserve;
+    st = nd > 0 ? run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s) : SCA_OK;
+    e.tc_cap = 0;
+    if (st != SCA_OK) return st;
     if (fork) {
+      if (want_grad && refine_stage) {  // each group refines its own blocks on its stream
+        if ((st = launch_refine<S>(e, la, b0, 0, np, sp)) != SCA_OK) return st;
+        if ((st = launch_refine<S>(e, la, b0, np, nd, s)) != SCA_OK) return st;
+      }
       if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "join");
       if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "join");
     }
-    if (want_grad && refine_stage) {
-      sca_status st2 = launch_refine<S>(e, la, b0, cnt, s);
+    if (want_grad && refine_stage && !fork) {
+      sca_status st2 = launch_refine<S>(e, la, b0, 0, cnt, s);
       if (st2 != SCA_OK) return st2;
     }
   }
@@ -1239,8 +1314,8 @@ sca_status run_refine_resident(Engine& e, const double* d_phi, cudaStream_t s) {
     return SCA_ENOSTATE;
   }
   const Lattice la = make_lattice(e, d_phi);
-  if (e.fp64) return launch_refine<double>(e, la, 0, e.B, s);
-  return launch_refine<float>(e, la, 0, e.B, s);
+  if (e.fp64) return launch_refine<double>(e, la, 0, 0, e.B, s);
+  return launch_refine<float>(e, la, 0, 0, e.B, s);
 }
 
 sca_status run_assemble_only(Engine& e, const double* d_phi, int b0, int count, cudaStream_t s) {

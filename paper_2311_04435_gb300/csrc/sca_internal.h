@@ -63,6 +63,8 @@ struct Engine {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
   int tc_next = 0;
+  int tc_cap = 0;                   // CTA cap of the next tensor-core launches (0: one per SM)
+  int sm_reserve = 0;               // SMs the dominant group leaves to the pivoted group
   int fused_grid = 0;               // CTAs of the fused small-block kernel (0: not eligible)
   size_t fused_smem = 0;
   unsigned* fused_bar = nullptr;    // grid-barrier counter and generation
@@ -138,6 +140,7 @@ sca_status tc_prepare(Engine& e);
 void tc_release(Engine& e);
 sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0, bool gj,
                      cudaStream_t s, int nbk, bool sym = false);
+int tc_sms(const Engine& e);  // CTAs of an uncapped tensor-core launch (one per SM)
 sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's launches  // tensor-core maps exist for the pivoted group's width
 // F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);

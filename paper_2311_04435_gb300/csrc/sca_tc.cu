@@ -640,6 +640,11 @@ sca_status tc_prepare(Engine& e) {
   return SCA_OK;
 }
 
+int tc_sms(const Engine& e) {
+  const TcMaps* t = static_cast<const TcMaps*>(e.tmap);
+  return t ? t->sms : 0;
+}
+
 void tc_release(Engine& e) {
   if (e.tc_counters) cudaFree(e.tc_counters);
   e.tc_counters = nullptr;
@@ -684,7 +689,7 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
     return SCA_EINVAL;
   }
   a.counter = e.tc_counters + e.tc_next++;
-  const int grid = std::min(a.tiles, t->sms);
+  const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
   k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
@@ -728,7 +733,7 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
     return SCA_EINVAL;
   }
   a.counter = e.tc_counters + e.tc_next++;
-  const int grid = std::min(a.tiles, t->sms);
+  const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
   k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
