@@ -82,6 +82,9 @@ def lib():
             l.orc_blocks_sample.argtypes = [P, dp, dp, ctypes.c_int, ip, dp, dp]
             l.orc_blocks_sample.restype = ctypes.c_int
             l.orc_seed_phi.argtypes = [ctypes.c_uint64, ctypes.c_int, dp]
+            for fn in (l.orc_dos, l.orc_dos_eig):
+                fn.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp]
+                fn.restype = ctypes.c_int
             l.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             l.orc_splitmix64.restype = ctypes.c_uint64
             l.orc_adam_run.argtypes = [P, dp, ctypes.POINTER(Adam), dp, dp, dp, ip, dp, dp]
@@ -190,6 +193,22 @@ def blocks_sample(p: Params, phi, blocks, eps_extra=None):
     if rc != 0:
         raise FloatingPointError("oracle: singular block")
     return ld, gd
+
+
+def dos(p: Params, phi, sigma: int, w, eta: float, eps_extra=None, route: str = "lu"):
+    """rho_sigma(w) = -(1/(pi N)) Im Tr [(w + i eta + mu) - H_sigma(phi)]^{-1} at the
+    frequencies w (the DOS equation of Sec. II); route "lu" (dense pivoted LU and inverse
+    columns) or "eig" (Jacobi eigenvalues, a sum of Lorentzians)."""
+    N = p.L * p.L
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(len(w))
+    fn = lib().orc_dos if route == "lu" else lib().orc_dos_eig
+    rc = fn(ctypes.byref(p), _dp(ee), _dp(phi), int(sigma), len(w), _dp(w), float(eta), _dp(out))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular resolvent")
+    return out
 
 
 def seed_phi(seed: int, N: int) -> np.ndarray:

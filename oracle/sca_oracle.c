@@ -344,6 +344,70 @@ int orc_omega_grad_eig(const orc_params* p, const double* eps_extra, const doubl
   return 0;
 }
 
+/* ------------------------------------------------ density of states ----- */
+
+/* Density of states of spin sigma at the field phi (Sec. II, the equation after Eq. 2, with
+ * H_SCA = H_sigma(phi)):
+ *     rho_sigma(w) = -(1/(pi N)) Im Tr [(w + i eta + mu) I - H_sigma]^{-1},
+ * the trace normalised per site (the paper prints the resolvent without naming the trace;
+ * the per-site normalisation makes rho integrate to 1 over w).  LU route: each resolvent is
+ * the dense complex LU with partial pivoting and the inverse column by column, as in
+ * orc_block.  rho_out[k] for the count frequencies w[k], OpenMP over k. */
+int orc_dos(const orc_params* p, const double* eps_extra, const double* phi, int sigma,
+            int count, const double* w, double eta, double* rho_out) {
+  const int N = p->L * p->L;
+  double* H = (double*)malloc(sizeof(double) * (size_t)N * N);
+  orc_hamiltonian(p, eps_extra, phi, sigma, H);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (int k = 0; k < count; ++k) {
+    zc* A = (zc*)malloc(sizeof(zc) * (size_t)N * N);
+    int* piv = (int*)malloc(sizeof(int) * N);
+    zc* x = (zc*)malloc(sizeof(zc) * N);
+    const zc z = w[k] + p->mu + I * eta;
+    for (size_t q = 0; q < (size_t)N * N; ++q) A[q] = -H[q];
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + i] += z;
+    double ld = 0.0;
+    if (orc_zgetrf(N, A, piv, &ld) != 0) {
+      bad = 1;
+    } else {
+      double tr = 0.0;
+      for (int j = 0; j < N; ++j) {
+        lu_solve_unit(N, A, piv, j, x);
+        tr += cimag(x[j]);
+      }
+      rho_out[k] = -tr / (M_PI * N);
+    }
+    free(A); free(piv); free(x);
+  }
+  free(H);
+  return bad ? -1 : 0;
+}
+
+/* The same density of states by the eigenvalue route: H_sigma = V diag(e) V^T (Jacobi), so
+ * Tr [z - H]^{-1} = sum_a 1 / (z - e_a) and
+ *     rho_sigma(w) = (1/(pi N)) sum_a eta / ((w + mu - e_a)^2 + eta^2),
+ * a sum of Lorentzians of unit weight. */
+int orc_dos_eig(const orc_params* p, const double* eps_extra, const double* phi, int sigma,
+                int count, const double* w, double eta, double* rho_out) {
+  const int N = p->L * p->L;
+  double* H = (double*)malloc(sizeof(double) * (size_t)N * N);
+  double* V = (double*)malloc(sizeof(double) * (size_t)N * N);
+  double* e = (double*)malloc(sizeof(double) * N);
+  orc_hamiltonian(p, eps_extra, phi, sigma, H);
+  orc_jacobi(N, H, e, V);
+  for (int k = 0; k < count; ++k) {
+    double acc = 0.0;
+    for (int a = 0; a < N; ++a) {
+      const double d = w[k] + p->mu - e[a];
+      acc += eta / (d * d + eta * eta);
+    }
+    rho_out[k] = acc / (M_PI * N);
+  }
+  free(H); free(V); free(e);
+  return 0;
+}
+
 /* ------------------------------------------------------ seeded phi0 ------ */
 
 static uint64_t splitmix64_mix(uint64_t z) {

@@ -298,3 +298,68 @@ def test_adam_from_neel_reaches_closed_form_minimum():
     assert gm < 1e-6
     assert np.allclose(phi * s, res.x, atol=1e-6)
     assert om / (L * L) == pytest.approx(res.fun, rel=1e-10)
+
+
+# ------------------------------------------------------- density of states ---
+
+def dos_staggered(L, D, w, eta, mu=0.0, t=1.0):
+    """rho(w) for hopping plus staggered on-site -s_i D: the N eigenvalues are
+    +-sqrt(eps_k^2 + D^2), each pair counted once per (k, k+(pi,pi)), i.e. half a pair per k."""
+    e = np.sqrt(bz_eps(L, t) ** 2 + D * D)
+    w = np.asarray(w)[:, None] + mu
+    lor = eta / ((w - e) ** 2 + eta * eta) + eta / ((w + e) ** 2 + eta * eta)
+    return 0.5 * lor.sum(axis=1) / (np.pi * L * L)
+
+
+@pytest.mark.parametrize("L,delta,ionic,mu", [(2, 0.0, 0, 0.0), (4, 0.7, 0, 0.0), (6, 1.2, 1, 0.3)])
+def test_dos_closed_form_phi0(L, delta, ionic, mu):
+    """DOS equation of Sec. II at phi = 0: a sum of Lorentzians at +-sqrt(eps_k^2 + Delta^2)."""
+    p = oracle.make_params(L, 1, U=4.0, T=0.1, delta=delta, mu=mu, ionic=ionic)
+    w = np.linspace(-7.0, 7.0, 29)
+    ref = dos_staggered(L, delta_eff(delta, ionic), w, 0.2, mu=mu)
+    for sg in (1, -1):
+        got = oracle.dos(p, np.zeros(L * L), sg, w, 0.2)
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("sg", [1, -1])
+def test_dos_staggered_field_closed_form(sg):
+    """phi_i = phi s_i shifts the staggered potential to Delta + sigma phi per spin, so the
+    two spins see different gaps (the spin-split DOS of Fig. 3 and Fig. 6)."""
+    L, delta, phi0 = 4, 0.5, 1.3
+    p = oracle.make_params(L, 1, U=4.0, T=0.1, delta=delta)
+    w = np.linspace(-6.0, 6.0, 25)
+    got = oracle.dos(p, phi0 * sublattice(L), sg, w, 0.1)
+    ref = dos_staggered(L, delta + sg * phi0, w, 0.1)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+    other = oracle.dos(p, phi0 * sublattice(L), -sg, w, 0.1)
+    assert np.max(np.abs(other - got)) > 1e-3  # the spins differ
+
+
+def test_dos_lu_matches_eigen_route_disordered():
+    """Arbitrary phi plus random site energies (the disordered model): the LU route against
+    the Jacobi eigenvalue route."""
+    L = 6
+    p = oracle.make_params(L, 1, U=4.0, T=0.1, delta=0.8, mu=0.2)
+    phi = inputs.random_phi(11, L * L, 1.5)
+    ee = inputs.random_phi(12, L * L, 0.7)
+    w = np.linspace(-6.0, 6.0, 31)
+    for sg in (1, -1):
+        a = oracle.dos(p, phi, sg, w, 0.05, eps_extra=ee)
+        b = oracle.dos(p, phi, sg, w, 0.05, eps_extra=ee, route="eig")
+        assert np.allclose(a, b, rtol=1e-11, atol=1e-13)
+
+
+def test_dos_unit_weight():
+    """Each eigenvalue contributes a Lorentzian of unit weight: the integral of rho over
+    [-W, W] equals (1/(pi N)) sum_a [atan((W - e_a)/eta) + atan((W + e_a)/eta)]."""
+    L, eta, W = 2, 0.3, 40.0
+    p = oracle.make_params(L, 1, U=4.0, T=0.1, delta=0.6)
+    w = np.linspace(-W, W, 160001)
+    rho = oracle.dos(p, np.zeros(L * L), 1, w, eta)
+    integral = np.sum(0.5 * (rho[1:] + rho[:-1]) * np.diff(w))
+    e = np.sqrt(bz_eps(L) ** 2 + 0.36)
+    ev = np.concatenate([e, -e])
+    exact = 0.5 * np.sum(np.arctan((W - ev) / eta) + np.arctan((W + ev) / eta)) / (np.pi * L * L)
+    assert integral == pytest.approx(exact, rel=1e-8)
+    assert 0.99 < integral < 1.0
