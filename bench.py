@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--workload", default="ionic_40x40")
     ap.add_argument("--prec", default=None, help="fp32 | 3xtf32 (default: the fastest built)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 steps (0 = skip)")
+    ap.add_argument("--variant-steps", type=int, default=10,
+                    help="timed steps of the no-pivoting variant (0 = skip)")
+    ap.add_argument("--dos-points", type=int, default=128,
+                    help="real frequencies of the timed density of states (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
@@ -260,6 +264,45 @@ def run_ours(args):
                 "timed_steps": args.fp64_steps, "warmup": 1,
                 "mixed_over_fp64": round(ms64 / ms_per_step, 2)}
 
+    # ---------------- the same step without interchanges in any block (complex-symmetric
+    # elimination throughout; a variant beside the paper's pivoted LU, not the headline)
+    nopiv = None
+    if args.variant_steps > 0 and rank == 0 and api.pivoted_blocks(params) > 0:
+        cn = api.Context(params)
+        cn.set_stream(stream)
+        cn.set_pivoting("none")
+        cn.adam_init(adam)
+        cn.adam_step(1)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        omn, gmn = cn.adam_step(args.variant_steps)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        msn = a0.elapsed_time(a1) / args.variant_steps
+        cn.close()
+        nopiv = {"steps_per_s": round(1e3 / msn, 4), "ms_per_step": round(msn, 3),
+                 "timed_steps": args.variant_steps, "warmup": 1, "final_omega": omn,
+                 "final_gmax": gmn}
+
+    # ---------------- density of states at the final field (Sec. II): one batch of n_omega
+    # real frequencies per spin, every resolvent pivoted (eta < 4t)
+    dos = None
+    if args.dos_points > 0 and rank == 0:
+        cd = api.Context(params)
+        cd.set_stream(stream)
+        wgrid = np.linspace(-6.0, 6.0, args.dos_points)
+        phi_dos = inputs.seed_phi(wl.seed, params.N)
+        cd.dos(phi_dos, wgrid, 0.05)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rho = cd.dos(phi_dos, wgrid, 0.05)
+        dos_s = time.perf_counter() - t0
+        cd.close()
+        dos = {"points": int(args.dos_points), "eta": 0.05, "ms": round(dos_s * 1e3, 2),
+               "resolvents_per_s": round(2 * args.dos_points / dos_s, 2),
+               "rho_max": round(float(rho.max()), 6)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl)
@@ -284,6 +327,8 @@ def run_ours(args):
             "roofline": roofline_for(prec, achieved, traffic),
             "kernels_ms_one_step": per_kernel,
             "fp64_path": fp64,
+            "no_pivoting_variant": nopiv,
+            "dos": dos,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

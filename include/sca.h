@@ -259,6 +259,33 @@ sca_status sca_set_stream(sca_ctx* ctx, void* stream);
  * that runs out makes the call return SCA_ETIMEOUT; the context stays usable. */
 sca_status sca_set_wait_limit(sca_ctx* ctx, int64_t cycles);
 
+/* Density of states of both spins at the field phi (Sec. II, the equation after Eq. 2, with
+ * H_SCA = H_sigma(phi) and the trace taken per site):
+ *     rho_sigma(w) = -(1/(pi N)) Im Tr [(w + i eta + mu) I - H_sigma(phi)]^{-1}.
+ * phi_host: N doubles (host); w_host: n_w real frequencies (host, finite); eta > 0: the
+ * broadening.  rho_out (host, 2 n_w doubles): spin up (sigma = +1) at [0, n_w), spin down at
+ * [n_w, 2 n_w).  The resolvents go through the same batched elimination as the gradient, in
+ * batches of n_omega frequencies (the context's block slots), with partial pivoting unless
+ * eta > 4|t| or the context is set to SCA_PIVOT_NONE; the mixed precisions take Im G_ii from
+ * the float32 inverse without refinement.  Invalidates the inverses kept for
+ * sca_backward_dev.  SCA_EINVAL for bad arguments, SCA_ENONFINITE for a singular resolvent. */
+sca_status sca_dos(sca_ctx* ctx, const double* phi_host, const double* w_host, int32_t n_w,
+                   double eta, double* rho_out);
+
+/* Pivoting of the batched elimination of the A_{n,sigma} (Sec. II, Eq. 2).
+ *   SCA_PIVOT_PARTIAL (default): partial pivoting for the blocks whose column diagonal
+ *     dominance is not guaranteed (omega_n <= 4|t|); the remaining blocks provably keep their
+ *     diagonal pivots and skip the search.
+ *   SCA_PIVOT_NONE: every block is eliminated without interchanges, as a complex-symmetric
+ *     (LDL^T-type) elimination that updates one triangle on the tensor-core path.  The paper
+ *     has no such variant.  -i A_{n,sigma} has Hermitian part omega_n I > 0, so every leading
+ *     principal minor is nonzero and the elimination exists; its growth has no a-priori bound
+ *     and rises as omega_n falls (the largest growth met in tests is below 10, down to
+ *     T = 0.02).  The fused small-block path (N <= 144) always pivots.
+ * Applies from the next call on the context; any other mode is SCA_EINVAL. */
+typedef enum { SCA_PIVOT_PARTIAL = 0, SCA_PIVOT_NONE = 1 } sca_pivot;
+sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
+
 /* Per-kernel timing.  While enabled, every launch of the context is bracketed by CUDA
  * events on the stream it is launched on, and the elapsed times are accumulated per kernel
  * kind when the calling API function synchronises.  Kinds: 0 assemble, 1 pivoted panel,

@@ -70,6 +70,8 @@ SIGNATURES = [
     ("sca_grad_noalloc_dev", ctypes.c_int, [_PP, _vp, _vp, _vp, _vp]),
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
     ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),
+    ("sca_set_pivoting", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("sca_dos", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int32, ctypes.c_double, _dp]),
     ("sca_profile_enable", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_profile_read", ctypes.c_int, [_vp, ctypes.c_int32, _dp, _u64p]),
     ("sca_flops_per_grad", ctypes.c_double, [_PP]),

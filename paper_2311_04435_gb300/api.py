@@ -146,6 +146,17 @@ class Context:
         check(_lib.lib().sca_grad(self._h, _ptr(phi), ctypes.byref(om), _ptr(g)))
         return om.value, g
 
+    def dos(self, phi, w, eta: float):
+        """Density of states rho_sigma(w) = -(1/(pi N)) Im Tr[(w + i eta + mu) - H_sigma]^-1
+        (Sec. II): returns an array (2, len(w)), spin up first."""
+        self._bump()
+        phi = _f64(phi)
+        w = _f64(w)
+        assert phi.shape == (self.N,) and w.ndim == 1 and len(w) > 0
+        out = np.zeros(2 * len(w))
+        check(_lib.lib().sca_dos(self._h, _ptr(phi), _ptr(w), len(w), float(eta), _ptr(out)))
+        return out.reshape(2, len(w))
+
     def blocks(self, phi, grad: bool = True):
         """Per block b = 2n+s: ln|det A_b| and (grad) sigma_b Re G_b,ii."""
         self._bump()
@@ -218,6 +229,14 @@ class Context:
     def set_wait_limit(self, cycles: int = 0):
         """Bound (SM cycles) of device-side spin waits; 0 restores the default."""
         check(_lib.lib().sca_set_wait_limit(self._h, int(cycles)))
+
+    def set_pivoting(self, mode: str = "partial"):
+        """'partial': partial pivoting where diagonal dominance is not guaranteed (default);
+        'none': every block eliminated without interchanges (complex-symmetric elimination)."""
+        modes = {"partial": 0, "none": 1}
+        if mode not in modes:
+            raise ValueError(f"pivoting mode must be one of {sorted(modes)}")
+        check(_lib.lib().sca_set_pivoting(self._h, modes[mode]))
 
     def profile(self, enable: bool = True):
         check(_lib.lib().sca_profile_enable(self._h, 1 if enable else 0))

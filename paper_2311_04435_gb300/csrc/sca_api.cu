@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "sca_internal.h"
 
@@ -95,6 +96,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.piv_blocks = 2 * n_piv;
   if (const char* v = std::getenv("SCA_PIVOT_ALL"))
     if (std::atoi(v) != 0) e.piv_blocks = e.B;
+  e.piv_planned = e.piv_blocks;
   // Width of the pivoted group's shared-memory panel: N x (nb_piv + 1) complex values
   // (rows padded by one) within 220 KB.
   const size_t cbytes = e.fp64 ? 16 : 8;
@@ -121,7 +123,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
   if (e.tc) bytes += (size_t)e.chunk * 6 * e.nb * e.nb * 4;  // -T^T split planes
   bytes += 2 * (size_t)e.chunk * e.N * sizeof(int);       // piv, perm
-  bytes += (size_t)e.B * sizeof(double) * (1 + e.N);      // ld, gd
+  bytes += (size_t)e.B * sizeof(double) * (3 + e.N);      // ld, d_z, tr, gd
   bytes += (size_t)e.N * sizeof(double) * 7 + 256;        // eps, phi, m, v, g, in, misc
   e.bytes = bytes;
   return SCA_OK;
@@ -153,6 +155,8 @@ sca_status allocate(Engine& e) {
   SCA_ALLOC(e.perm, (size_t)e.chunk * e.N * sizeof(int), "perm");
   SCA_ALLOC(e.flags, 16, "flags");
   SCA_ALLOC(e.ld, (size_t)e.B * sizeof(double), "ld");
+  SCA_ALLOC(e.d_z, (size_t)e.B * sizeof(double), "DOS shifts");
+  SCA_ALLOC(e.tr, (size_t)e.B * sizeof(double), "traces");
   SCA_ALLOC(e.gd, (size_t)e.B * e.N * sizeof(double), "gd");
   SCA_ALLOC(e.d_phi, (size_t)e.N * sizeof(double), "phi");
   SCA_ALLOC(e.d_m, (size_t)e.N * sizeof(double), "m");
@@ -258,7 +262,7 @@ void release(Engine& e) {
   if (e.ev_join) cudaEventDestroy(e.ev_join);
   e.side = nullptr;
   e.ev_fork = e.ev_join = nullptr;
-  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.piv, e.perm, e.flags, e.ld, e.gd,
+  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.piv, e.perm, e.flags, e.ld, e.d_z, e.tr, e.gd,
                   e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -268,6 +272,7 @@ void release(Engine& e) {
   e.M = e.F = e.W = e.Tinv = nullptr;
   e.tt = nullptr;
   e.piv = e.perm = e.flags = nullptr;
+  e.d_z = e.tr = nullptr;
   e.ld = e.gd = e.eps_extra = e.d_phi = e.d_m = e.d_v = e.d_g = e.d_status = e.d_omega = nullptr;
   e.h_status = nullptr;
 }
@@ -469,6 +474,61 @@ sca_status sca_blocks(sca_ctx* c, const double* phi_host, double* ld, double* gd
   if (err != cudaSuccess) return cuda_fail(err, "block read-back");
   if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
   return check_finite(c);
+}
+
+sca_status sca_dos(sca_ctx* c, const double* phi_host, const double* w_host, int32_t n_w,
+                   double eta, double* rho_out) {
+  if (!c || !w_host || !rho_out || n_w < 1 || !(eta > 0.0) || !std::isfinite(eta)) {
+    set_error("sca_dos: need ctx, w and rho_out, n_w >= 1 and a finite eta > 0");
+    return SCA_EINVAL;
+  }
+  for (int32_t k = 0; k < n_w; ++k)
+    if (!std::isfinite(w_host[k])) {
+      set_error("sca_dos: non-finite frequency");
+      return SCA_EINVAL;
+    }
+  sca_status st = upload_phi(c, phi_host);
+  if (st != SCA_OK) return st;
+  Engine& e = c->e;
+  c->kept = false;
+  const int half = e.B / 2;
+  std::vector<double> hz((size_t)e.B), htr((size_t)e.B);
+  // Every resolvent has Im z = eta: columns are strictly diagonally dominant (and the
+  // elimination pivot-free) only when eta > 4|t|.
+  const int saved = e.piv_blocks;
+  const double thr = 4.0 * std::fabs(e.p.t) * (1.0 + 1e-3);
+  e.piv_blocks = (e.nopiv || eta > thr) ? 0 : e.B;
+  e.dos_mode = true;
+  for (int32_t k0 = 0; k0 < n_w && st == SCA_OK; k0 += half) {
+    const int cnt = std::min<int>(half, n_w - k0);
+    for (int n = 0; n < half; ++n) {  // a short last batch repeats its last frequency
+      hz[2 * n] = w_host[k0 + std::min(n, cnt - 1)] + e.p.mu;
+      hz[2 * n + 1] = eta;
+    }
+    cudaError_t err = cudaMemcpyAsync(e.d_z, hz.data(), sizeof(double) * e.B,
+                                      cudaMemcpyHostToDevice, c->stream);
+    if (err != cudaSuccess) { st = cuda_fail(err, "DOS shifts upload"); break; }
+    if ((st = run_blocks(e, c->d_in, true, c->stream, false)) != SCA_OK) break;
+    err = cudaMemcpyAsync(htr.data(), e.tr, sizeof(double) * e.B, cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e.h_flags, e.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) { st = cuda_fail(err, "DOS read-back"); break; }
+    prof_collect(e);
+    if (*e.h_flags != 0) {
+      set_error("sca_dos: a singular resolvent or a non-finite pivot");
+      st = SCA_ENONFINITE;
+      break;
+    }
+    for (int n = 0; n < cnt; ++n) {
+      rho_out[k0 + n] = -htr[2 * n] / (M_PI * e.N);
+      rho_out[n_w + k0 + n] = -htr[2 * n + 1] / (M_PI * e.N);
+    }
+  }
+  e.dos_mode = false;
+  e.piv_blocks = saved;
+  return st;
 }
 
 sca_status sca_debug_assemble(sca_ctx* c, const double* phi_host, int32_t b0, int32_t count,
@@ -677,6 +737,16 @@ sca_status sca_set_stream(sca_ctx* c, void* stream) {
 sca_status sca_set_wait_limit(sca_ctx* c, int64_t cycles) {
   if (!c || cycles < 0) { set_error("bad context or wait limit"); return SCA_EINVAL; }
   c->e.wait_cycles = cycles ? (long long)cycles : 4000000000ll;
+  return SCA_OK;
+}
+
+sca_status sca_set_pivoting(sca_ctx* c, int32_t mode) {
+  if (!c || (mode != SCA_PIVOT_PARTIAL && mode != SCA_PIVOT_NONE)) {
+    set_error("bad context or pivoting mode");
+    return SCA_EINVAL;
+  }
+  c->e.piv_blocks = (mode == SCA_PIVOT_NONE) ? 0 : c->e.piv_planned;
+  c->e.nopiv = (mode == SCA_PIVOT_NONE);
   return SCA_OK;
 }
 

@@ -41,7 +41,8 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
                            Lattice la, double* ld, int* perm) {
   const int mat = blockIdx.y, b = b0 + mat, n = b >> 1, sg = (b & 1) ? -1 : 1;
   const int N = la.N, L = la.L;
-  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const double w = la.zshift ? la.zshift[2 * n + 1] : (2.0 * n + 1.0) * kPi * la.T;
+  const double zr = la.zshift ? la.zshift[2 * n] : la.mu;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,7 +56,7 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
     re[row + jxm] += (S)la.t;
     re[row + jyp] += (S)la.t;
     re[row + jym] += (S)la.t;
-    re[row + i] = (S)(la.mu - site_energy(la, i, sg));
+    re[row + i] = (S)(zr - site_energy(la, i, sg));
     im[row + i] = (S)w;
     perm[(size_t)mat * N + i] = i;
   }
@@ -940,6 +941,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Im Tr G per block for the density of states: X_ii = R[i, sperm[i]] (sperm the inverse of
+// the column permutation of the pivoted elimination), summed in float64 in a fixed order.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_trace(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int N, const int* perm,
+            int b0, double* tr) {
+  extern __shared__ int sperm_dyn[];
+  __shared__ double part[256];
+  const int mat = blockIdx.x;
+  const S* im = M + mat * mat_stride + plane_stride;
+  for (int r = threadIdx.x; r < N; r += 256) sperm_dyn[perm[(size_t)mat * N + r]] = r;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += 256) s += (double)im[(size_t)i * ldm + sperm_dyn[i]];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tr[b0 + mat] = part[0];
+}
+
 // -------------------------------------------------------------- reduce/Adam
 // Omega = sum_i phi_i^2/U - 2T sum_b ld_b ; g_i = 2 phi_i/U - 2T sum_b gd[b, i] (b ascending);
 // then, if Adam is on and max|g| >= grad_tol, the update of phi in PyTorch's order
@@ -1032,6 +1056,7 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
   Lattice la;
   la.L = e.L; la.N = e.N; la.t = e.p.t; la.delta_eff = e.delta_eff; la.mu = e.p.mu; la.T = e.p.T;
   la.phi = d_phi; la.eps_extra = e.eps_extra;
+  la.zshift = e.dos_mode ? e.d_z : nullptr;
   return la;
 }
 
@@ -1252,14 +1277,20 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
     e.tc_cap = 0;
     if (st != SCA_OK) return st;
     if (fork) {
-      if (want_grad && refine_stage) {  // each group refines its own blocks on its stream
+      if (want_grad && refine_stage && !e.dos_mode) {  // each group refines its own blocks
         if ((st = launch_refine<S>(e, la, b0, 0, np, sp)) != SCA_OK) return st;
         if ((st = launch_refine<S>(e, la, b0, np, nd, s)) != SCA_OK) return st;
       }
       if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "join");
       if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "join");
     }
-    if (want_grad && refine_stage && !fork) {
+    if (want_grad && e.dos_mode) {
+      prof_begin(e, kRefine, s);
+      k_trace<S><<<cnt, 256, (size_t)N * sizeof(int), s>>>(M, e.ldm, e.mat_stride, e.plane_stride,
+                                                           N, e.perm, b0, e.tr);
+      prof_end(e, kRefine, s);
+      SCA_LAUNCH_CHECK("trace");
+    } else if (want_grad && refine_stage && !fork) {
       sca_status st2 = launch_refine<S>(e, la, b0, 0, cnt, s);
       if (st2 != SCA_OK) return st2;
     }

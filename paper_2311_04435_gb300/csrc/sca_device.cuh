@@ -22,6 +22,7 @@ struct Lattice {
   double t, delta_eff, mu, T;
   const double* phi;
   const double* eps_extra;
+  const double* zshift;  // null: z_n = mu + i omega_n; else z_n = zshift[2n] + i zshift[2n+1]
 };
 
 __device__ __forceinline__ double site_energy(const Lattice& la, int i, int sg) {

@@ -28,6 +28,7 @@ struct Engine {
   int L = 0, N = 0, B = 0;
   int nb = 0;            // Gauss-Jordan / LU block width (diagonally dominant blocks)
   int nb_piv = 0;        // block width of the pivoted group (shared-memory panel)
+  int piv_planned = 0;   // piv_blocks under partial pivoting
   int piv_blocks = 0;    // blocks b < piv_blocks need partial pivoting (omega_n <= 4|t|)
   int ldm = 0;           // row stride of a block plane (elements)
   int chunk = 0;         // blocks resident at once
@@ -47,6 +48,10 @@ struct Engine {
   int* perm = nullptr;      // chunk x N
   int* flags = nullptr;     // 1 int: nonfinite / singular
   double* ld = nullptr;     // B
+  double* d_z = nullptr;    // B: (re, im) of the DOS shifts w_k + mu + i eta (n < B/2)
+  double* tr = nullptr;     // B: Im Tr G per block (DOS)
+  bool nopiv = false;       // SCA_PIVOT_NONE: no block is pivoted
+  bool dos_mode = false;    // blocks use the shifts d_z and end in a trace, not a refine
   double* gd = nullptr;     // B x N
   double* eps_extra = nullptr;  // N or null
   double* d_phi = nullptr;  // N (Adam state)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2311_04435_gb300 import api, inputs
+from paper_2311_04435_gb300 import _lib, api, inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -293,3 +293,31 @@ def test_symmetric_update_matches_full_update(monkeypatch):
         assert om == pytest.approx(o_om, rel=t["om"]) and om_lu == pytest.approx(o_om, rel=t["om"])
         assert np.max(np.abs(g - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
     assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 2 * t["g"] * max(1.0, np.abs(o_gd).max())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_no_pivoting_matches_oracle(prec):
+    """Every block eliminated without interchanges (complex-symmetric elimination), including
+    the lowest frequencies (omega_0 = 0.157 < 4t, where the default path pivots), against the
+    oracle's partially pivoted LU.  400 x 400 blocks: four tiles per side, ragged last one."""
+    p = api.Params(20, 8, U=6.0, T=0.05, delta=0.5, prec=prec)
+    assert api.pivoted_blocks(p) > 0
+    phi = inputs.seed_phi(5, p.N)
+    with api.Context(p) as c:
+        with pytest.raises(ValueError):
+            c.set_pivoting("rook")
+        assert _lib.lib().sca_set_pivoting(c._h, 7) == 1  # SCA_EINVAL, context unchanged
+        c.set_pivoting("none")
+        ld, gd = c.blocks(phi, grad=True)
+        om_lu = c.potential(phi)
+        om, g = c.grad(phi)
+        c.set_pivoting("partial")
+        om_p, g_p = c.grad(phi)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+    assert om == pytest.approx(o_om, rel=t["om"]) and om_lu == pytest.approx(o_om, rel=t["om"])
+    assert om_p == pytest.approx(o_om, rel=t["om"])
+    for gg in (g, g_p):
+        assert np.max(np.abs(gg - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
