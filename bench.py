@@ -124,10 +124,10 @@ def peaks():
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 launches of one gradient
-# on a 16-block 40x40 case, divided by 16; traffic grows with the blocks).  None until
-# captured for the kernel as it stands.
-UPDATE_TC_BYTES_PER_BLOCK_N1600 = None
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over 8 update launches of a 16-block
+# 40x40 gradient: 434.0 MB per launch; traffic grows with the blocks).  The algorithmic bytes
+# are ~30 MB per block (lower-triangle tiles of M read and written, F and W planes once).
+UPDATE_TC_BYTES_PER_BLOCK_N1600 = 434.0e6 / 16
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
