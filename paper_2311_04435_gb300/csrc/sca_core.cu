@@ -491,36 +491,6 @@ __global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size
 // tensor-core update then computes only the tiles on or below the diagonal; reads that would
 // touch an upper tile are redirected to the transposed lower entry with that sign.
 
-// Split copy of the pivot columns for swept rows i < k0: M[i][k0 + k] = -M[k0 + k][i]
-// (row block K, column i: a lower-triangle entry), transposed through shared memory.
-template <typename S>
-__global__ void k_split_cols_swept(const S* M, int ldm, size_t mat_stride, size_t plane_stride,
-                                   int k0, int kb, int nb, float* Fs, size_t fs_plane,
-                                   size_t fs_mat) {
-  __shared__ float tr[32][33], ti[32][33];
-  const int mat = blockIdx.z;
-  const int i0 = blockIdx.x * 32, kk0 = blockIdx.y * 32;
-  const S* re = M + mat * mat_stride;
-  const S* im = re + plane_stride;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
-  for (int k = ty; k < 32; k += 8) {
-    const int gk = kk0 + k, gi = i0 + tx;
-    const bool in = gk < kb && gi < k0;
-    tr[k][tx] = in ? -(float)re[(size_t)(k0 + gk) * ldm + gi] : 0.f;
-    ti[k][tx] = in ? -(float)im[(size_t)(k0 + gk) * ldm + gi] : 0.f;
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int gi = i0 + r, gk = kk0 + tx;
-    if (gi >= k0 || gk >= nb) continue;
-    const float fr = tr[tx][r], fi = ti[tx][r];
-    const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
-    const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
-    float* o = Fs + (size_t)mat * fs_mat + (size_t)gi * nb + gk;
-    o[0] = hr; o[fs_plane] = hi; o[2 * fs_plane] = fr - hr; o[3 * fs_plane] = fi - hi;
-  }
-}
-
 // Completes the fully swept (symmetric) inverse: M[i][j] = M[j][i] for i < j, 32x32 tiles
 // through shared memory.
 template <typename S>
@@ -1177,22 +1147,28 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     }
     if (!want_grad && kend == N) break;  // LU: nothing trails the last pivot block
     const int r0 = want_grad ? 0 : kend, c0 = want_grad ? 0 : kend;
-    {
+    if (sym) {
+      // W^T planes first: they are also the A operand of the prep product, since the swept
+      // rows of M[:, K] are -W^T and the unswept ones +W^T (the sign rule above)
+      prof_begin(e, kPrep, s);
+      const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
+      k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
+          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
+          want_grad ? 1 : 0, split, 1);
+      SCA_LAUNCH_CHECK("prep w");
+      sca_status st = tc_prep_split(e, m0, cnt, r0, k0, kb, want_grad, s);
+      if (st != SCA_OK) return st;
+      prof_end(e, kPrep, s);
+    } else {
       prof_begin(e, kPrep, s);
       if (tcg && !pivoted && nb == e.nb && e.tt) {
         // F = M[:, K] T on the tensor cores (scratch: the W planes, rewritten below)
-        const int rs = sym ? std::max(r0, k0) : r0;  // swept rows come from row block K
+        const int rs = r0;
         const size_t tot = (size_t)(N - rs) * nb;
         k_split_cols<S><<<dim3((unsigned)((tot + 255) / 256), cnt), 256, 0, s>>>(
             M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
             fw_plane, e.fw_mat, rs);
         SCA_LAUNCH_CHECK("split cols");
-        if (sym && r0 < k0) {
-          k_split_cols_swept<S><<<dim3((k0 - r0 + 31) / 32, (nb + 31) / 32, cnt), 256, 0, s>>>(
-              M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
-              fw_plane, e.fw_mat);
-          SCA_LAUNCH_CHECK("split cols swept");
-        }
         sca_status st = tc_prep(e, m0, cnt, r0, s);
         if (st != SCA_OK) return st;
         const size_t rem = (size_t)(N - r0) * nb;
@@ -1208,7 +1184,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
       k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
-          want_grad ? 1 : 0, split, sym ? 1 : 0);
+          want_grad ? 1 : 0, split, 0);
       prof_end(e, kPrep, s);
       SCA_LAUNCH_CHECK("prep");
     }

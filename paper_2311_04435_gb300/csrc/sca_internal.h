@@ -149,6 +149,10 @@ int tc_sms(const Engine& e);  // CTAs of an uncapped tensor-core launch (one per
 sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's launches  // tensor-core maps exist for the pivoted group's width
 // F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
+// Prep product of the symmetric dominant blocks: F = S (W^T T) written as the four TF32
+// planes of F, with S = -1 on the swept rows (< k0) and the rows of K replaced by -T.
+sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
+                         cudaStream_t s);
 
 }  // namespace sca
 

@@ -207,6 +207,12 @@ struct TcArgs {
   int sym;                             // lower-triangle tiles only (tiles_m == tiles_n)
   int per_block;                       // tiles per block
   int* err;                            // device error word (bit 1: wait time-out)
+  // Split output (the prep product of the symmetric dominant blocks): no accumulation into
+  // the output, v = (A B) row-signed (-1 for rows < k0 when split_neg), rows in K replaced by
+  // -T (Gauss-Jordan), stored as the four TF32 planes re_hi, im_hi, re_lo, im_lo.
+  int split_out, split_neg;
+  const float2* T;                     // pivot-block inverses, (mat0+mat) * t_mat + r * nb + j
+  long long t_mat;
 };
 
 // Tile t -> (block, tile row, tile column).  With `sym` only tiles on or below the diagonal
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(&rempty[rslot]);
       if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
       if (t < 0) break;
-      if (leader && prefetched != t) issue_load(t, 0, ebuf);
+      if (leader && !a.split_out && prefetched != t) issue_load(t, 0, ebuf);
       const int buf = iter & 1;
       const uint32_t use = (uint32_t)(iter >> 1);
       int mat, tm, tn;
@@ -422,6 +428,61 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tbase = tmem_base + (uint32_t)(buf * 256) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
       for (int c = 0; c < nchunk; ++c) {
+        if (a.split_out) {
+          uint32_t cr[32], ci[32];
+          tmem_ld32(tbase + (uint32_t)(c * kEpiCols), cr);
+          tmem_ld32(tbase + (uint32_t)(kBNc + c * kEpiCols), ci);
+          tmem_ld_wait();
+          if (leader) bulk_wait_read0();  // the previous chunk's stores have read the staging
+          epi_bar();
+          const int jc = j0 + c * kEpiCols;
+          const bool neg = a.split_neg && i < a.k0;
+          const float2* trow =
+              rowk ? a.T + (size_t)(a.mat0 + mat) * a.t_mat + (size_t)(i - a.k0) * a.nb : nullptr;
+          unsigned char* s0 = epi;
+          unsigned char* s1 = epi + kEpiBufBytes;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int off = row * 128 + ((k ^ (row & 7)) << 4);
+            float vr[4], vi[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int j = jc + 4 * k + e;
+              if (rowk) {
+                const float2 tv = (j < a.kb) ? trow[j] : make_float2(0.f, 0.f);
+                vr[e] = -tv.x;
+                vi[e] = -tv.y;
+              } else {
+                vr[e] = -__uint_as_float(cr[4 * k + e]);
+                vi[e] = -__uint_as_float(ci[4 * k + e]);
+                if (neg) { vr[e] = -vr[e]; vi[e] = -vi[e]; }
+              }
+            }
+            float4 rh, ih, rl, il;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float hr = __uint_as_float(__float_as_uint(vr[e]) & 0xffffe000u);
+              const float hi = __uint_as_float(__float_as_uint(vi[e]) & 0xffffe000u);
+              (&rh.x)[e] = hr; (&ih.x)[e] = hi; (&rl.x)[e] = vr[e] - hr; (&il.x)[e] = vi[e] - hi;
+            }
+            *reinterpret_cast<float4*>(s0 + off) = rh;
+            *reinterpret_cast<float4*>(s0 + kEpiPlaneBytes + off) = ih;
+            *reinterpret_cast<float4*>(s1 + off) = rl;
+            *reinterpret_cast<float4*>(s1 + kEpiPlaneBytes + off) = il;
+          }
+          fence_proxy_async();
+          epi_bar();
+          if (leader) {
+            const int y = a.r0 + tm * kBM;
+            const int zb = (a.mat0 + mat) * a.m_zmul + a.m_zoff;
+            tma_store_3d(&tmM, s0, jc, y, zb);
+            tma_store_3d(&tmM, s0 + kEpiPlaneBytes, jc, y, zb + 1);
+            tma_store_3d(&tmM, s1, jc, y, zb + 2);
+            tma_store_3d(&tmM, s1 + kEpiPlaneBytes, jc, y, zb + 3);
+            bulk_commit();
+          }
+          continue;
+        }
         const int eb = ebuf;
         // prefetch the next chunk (of this tile, or the first of the next tile)
         if (leader) {
@@ -528,6 +589,7 @@ struct TcMaps {
   CUtensorMap M;       // the blocks, for the epilogue
   CUtensorMap TT;      // -T^T split planes (nb x nb per block): B of F = M[:, K] T
   CUtensorMap FP;      // planar F = M[:, K] T (W scratch planes 4, 5): output of that product
+  CUtensorMap FO;      // the F planes themselves: split output of the symmetric prep product
   int sms = 0;
 };
 
@@ -614,7 +676,8 @@ sca_status tc_prepare(Engine& e) {
     // map as W), B = -T^T planes, output planar into W scratch planes 4, 5.
     const long long ztt = (long long)e.chunk * 6;
     bool ok = !e.tt || (make_fw_map(&t->TT, e.tt, e.nb, e.nb, ztt) &&
-                        make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf));
+                        make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf) &&
+                        make_m_map_rows(&t->FO, e.F, e.nb, e.N, e.nb, (long long)e.fw_plane, zf));
     if (!ok) {
       delete t;
       set_error("cuTensorMapEncodeTiled failed for the tensor-core prep product");
@@ -683,6 +746,9 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.m_zmul = 2;
   a.m_zoff = 0;
   a.err = e.flags;
+  a.split_out = a.split_neg = 0;
+  a.T = nullptr;
+  a.t_mat = 0;
   if (a.tiles <= 0) return SCA_OK;
   if (e.tc_next >= kCounters) {
     set_error("too many tensor-core launches in one pass");
@@ -727,6 +793,9 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: W scratch planes 4, 5
   a.m_zoff = 4;
   a.err = e.flags;
+  a.split_out = a.split_neg = 0;
+  a.T = nullptr;
+  a.t_mat = 0;
   if (a.tiles <= 0) return SCA_OK;
   if (e.tc_next >= kCounters) {
     set_error("too many tensor-core launches in one pass");
@@ -735,6 +804,54 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
   k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
+  return SCA_OK;
+}
+
+sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
+                         cudaStream_t s) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t || !e.tt) {
+    set_error("tensor-core prep used before tc_prepare");
+    return SCA_ENOSTATE;
+  }
+  TcArgs a;
+  a.M = nullptr;
+  a.N = e.N;
+  a.ldm = e.nb;
+  a.mat_stride = 0;
+  a.plane_stride = 0;
+  a.nb = e.nb;
+  a.r0 = r0;
+  a.c0 = 0;
+  a.k0 = k0;
+  a.kb = kb;
+  a.gj = gj ? 1 : 0;
+  a.tiles_m = (e.N - r0 + kBM - 1) / kBM;
+  a.tiles_n = (e.nb + kBNc - 1) / kBNc;
+  a.sym = 0;
+  a.per_block = a.tiles_m * a.tiles_n;
+  a.tiles = a.per_block * cnt;
+  a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W planes 0-3 (re_hi, im_hi, re_lo, im_lo)
+  a.wplanes = 6;                             // B: -T^T planes
+  a.mat0 = m0;
+  a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: F planes 0-3
+  a.m_zoff = 0;
+  a.err = e.flags;
+  a.split_out = 1;
+  a.split_neg = 1;
+  a.T = static_cast<const float2*>(e.Tinv);
+  a.t_mat = 2ll * e.nb * e.nb;
+  if (a.tiles <= 0) return SCA_OK;
+  if (e.tc_next >= kCounters) {
+    set_error("too many tensor-core launches in one pass");
+    return SCA_EINVAL;
+  }
+  a.counter = e.tc_counters + e.tc_next++;
+  const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
+  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
