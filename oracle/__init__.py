@@ -82,6 +82,11 @@ def lib():
             l.orc_blocks_sample.argtypes = [P, dp, dp, ctypes.c_int, ip, dp, dp]
             l.orc_blocks_sample.restype = ctypes.c_int
             l.orc_seed_phi.argtypes = [ctypes.c_uint64, ctypes.c_int, dp]
+            l.orc_metropolis.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_int64, dp, ip]
+            l.orc_metropolis.restype = ctypes.c_int
+            l.orc_metro_normal.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+            l.orc_metro_normal.restype = ctypes.c_double
             for fn in (l.orc_dos, l.orc_dos_eig):
                 fn.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp]
                 fn.restype = ctypes.c_int
@@ -209,6 +214,26 @@ def dos(p: Params, phi, sigma: int, w, eta: float, eps_extra=None, route: str = 
     if rc != 0:
         raise FloatingPointError("oracle: singular resolvent")
     return out
+
+
+def metropolis(p: Params, phi0, n_steps: int, delta: float, seed: int, step0: int = 0,
+               eps_extra=None):
+    """Metropolis chain on exp(-Omega/T) from phi0 (Sec. II): returns (phi, Omega trace,
+    accept flags) after n_steps steps numbered step0 .. step0 + n_steps - 1."""
+    phi = np.array(phi0, dtype=np.float64, copy=True)
+    ee = None if eps_extra is None else np.ascontiguousarray(eps_extra, dtype=np.float64)
+    om = np.zeros(max(n_steps, 1))
+    acc = np.zeros(max(n_steps, 1), dtype=np.int32)
+    rc = lib().orc_metropolis(ctypes.byref(p), _dp(ee), _dp(phi), int(n_steps), float(delta),
+                              ctypes.c_uint64(seed).value, int(step0), _dp(om),
+                              acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise FloatingPointError("oracle: singular block")
+    return phi, om[:n_steps], acc[:n_steps].astype(bool)
+
+
+def metro_normal(seed: int, step: int, N: int, j: int) -> float:
+    return float(lib().orc_metro_normal(ctypes.c_uint64(seed).value, int(step), int(N), int(j)))
 
 
 def seed_phi(seed: int, N: int) -> np.ndarray:

@@ -429,6 +429,52 @@ void orc_seed_phi(uint64_t seed, int N, double* phi) {
 
 /* -------------------------------------------------------------- Adam ----- */
 
+/* ------------------------------------------------- Metropolis sampling -- */
+
+/* Uniform in [0, 1): the top 53 bits of output k of the splitmix64 stream `seed`. */
+static double u01(uint64_t seed, uint64_t k) {
+  return (double)(orc_splitmix64(seed, k) >> 11) * 0x1.0p-53;
+}
+
+/* Standard normal number j of step s: the Box-Muller transform (Box & Muller 1958) of the
+ * uniforms U(seed, 2(sN + j)) and U(seed, 2(sN + j) + 1). */
+double orc_metro_normal(uint64_t seed, int64_t s, int N, int j) {
+  const uint64_t k = 2ull * ((uint64_t)s * (uint64_t)N + (uint64_t)j);
+  const double u1 = u01(seed, k), u2 = u01(seed, k + 1);
+  return sqrt(-2.0 * log(1.0 - u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* Metropolis sampling of the static-field weight exp(-V(phi)/T) of the SCA partition function
+ * (Sec. II, the integral over phi_1 .. phi_N with weight exp(-beta V)), V = Omega as defined
+ * above.  Step s (global index step0 + s of the chain):
+ *     phi'_i = phi_i + delta g_i,       g_i = orc_metro_normal(seed, s, N, i),
+ *     accepted iff U(seed + 1, s) < exp(-(Omega(phi') - Omega(phi)) / T).
+ * Omega by the LU route.  phi is updated in place; omega_trace[s] = Omega of the chain's state
+ * after step s and accepted[s] in {0, 1} (both optional). */
+int orc_metropolis(const orc_params* p, const double* eps_extra, double* phi, int n_steps,
+                   double delta, uint64_t seed, int64_t step0, double* omega_trace,
+                   int* accepted) {
+  const int N = p->L * p->L;
+  double* prop = (double*)malloc(sizeof(double) * N);
+  double om = 0.0;
+  if (orc_omega_grad(p, eps_extra, phi, &om, NULL, NULL, NULL) != 0) { free(prop); return -1; }
+  for (int s = 0; s < n_steps; ++s) {
+    const int64_t gs = step0 + s;
+    for (int i = 0; i < N; ++i) prop[i] = phi[i] + delta * orc_metro_normal(seed, gs, N, i);
+    double om2 = 0.0;
+    if (orc_omega_grad(p, eps_extra, prop, &om2, NULL, NULL, NULL) != 0) { free(prop); return -1; }
+    const int acc = u01(seed + 1, (uint64_t)gs) < exp(-(om2 - om) / p->T);
+    if (acc) {
+      memcpy(phi, prop, sizeof(double) * N);
+      om = om2;
+    }
+    if (omega_trace) omega_trace[s] = om;
+    if (accepted) accepted[s] = acc;
+  }
+  free(prop);
+  return 0;
+}
+
 /* Runs Adam on Omega from phi (in/out).  Each iteration evaluates the
  * gradient at the current phi; if max|g| < grad_tol it stops, else it takes
  * one Adam step.  Histories (max_steps entries, optional) hold Omega and

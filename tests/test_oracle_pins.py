@@ -363,3 +363,53 @@ def test_dos_unit_weight():
     exact = 0.5 * np.sum(np.arctan((W - ev) / eta) + np.arctan((W + ev) / eta)) / (np.pi * L * L)
     assert integral == pytest.approx(exact, rel=1e-8)
     assert 0.99 < integral < 1.0
+
+
+# ------------------------------------------------------ Metropolis sampling ---
+
+def test_metropolis_normals_are_standard():
+    """The proposal increments: Box-Muller normals from the SplitMix64 stream have the
+    moments of N(0, 1) (mean, variance, fourth moment, two-sided tail) within sampling error."""
+    n = 40000
+    g = np.array([oracle.metro_normal(7, s, 4, j) for s in range(n // 4) for j in range(4)])
+    assert abs(g.mean()) < 4.0 / math.sqrt(n)
+    assert abs(g.var() - 1.0) < 4.0 * math.sqrt(2.0 / n)
+    assert abs(np.mean(g ** 4) - 3.0) < 4.0 * math.sqrt(96.0 / n)
+    assert abs(np.mean(np.abs(g) > 1.959964) - 0.05) < 4.0 * math.sqrt(0.05 * 0.95 / n)
+
+
+def test_metropolis_zero_step_always_accepts():
+    p = oracle.make_params(4, 3, U=4.0, T=0.2, delta=0.5)
+    phi0 = inputs.random_phi(5, 16, 0.8)
+    phi, om, acc = oracle.metropolis(p, phi0, 6, 0.0, 11)
+    assert acc.all() and np.array_equal(phi, phi0)
+    assert np.allclose(om, oracle.omega_grad(p, phi0)[0], rtol=1e-14)
+
+
+def test_metropolis_samples_the_sca_weight():
+    """With t = 0 the weight exp(-Omega/T) factorises over sites, so the marginal of each phi_i
+    is a 1D density f(x) ~ exp(-(Omega(x, 0, 0, 0) - Omega(0)) / T) (Sec. II, the SCA partition
+    function).  The chain's <phi_i^2> and <|phi_i|> must match the 1D quadrature of that
+    density within four batch-means standard errors: a wrong acceptance rule (sign, missing
+    1/T, asymmetric proposal) shifts them by many errors."""
+    p = oracle.make_params(2, 4, U=2.0, T=0.5, delta=0.5, t=0.0)
+    x = np.linspace(-6.0, 6.0, 481)
+    om0 = oracle.omega_grad(p, np.zeros(4))[0]
+    f = np.array([math.exp(-(oracle.omega_grad(p, np.array([v, 0.0, 0.0, 0.0]))[0] - om0) / 0.5)
+                  for v in x])
+    z = np.trapezoid(f, x)
+    m2, m1 = np.trapezoid(f * x * x, x) / z, np.trapezoid(f * np.abs(x), x) / z
+    n_burn, n = 500, 24000
+    cur = oracle.metropolis(p, np.zeros(4), n_burn, 0.8, 2024)[0]
+    states = np.empty((n, 4))
+    accepted = 0
+    for s in range(n):  # one step per call: the chain continues through the global step number
+        cur, _, acc = oracle.metropolis(p, cur, 1, 0.8, 2024, step0=n_burn + s)
+        states[s] = cur
+        accepted += int(acc[0])
+    for vals, ref in ((states ** 2, m2), (np.abs(states), m1)):
+        per_step = vals.mean(axis=1)
+        batches = per_step.reshape(40, -1).mean(axis=1)
+        err = batches.std(ddof=1) / math.sqrt(len(batches))
+        assert abs(per_step.mean() - ref) < 4.0 * err + 1e-3, (per_step.mean(), ref, err)
+    assert 0.2 < accepted / n < 0.9
