@@ -43,6 +43,8 @@ def parse():
                     help="timed steps of the no-pivoting variant (0 = skip)")
     ap.add_argument("--dos-points", type=int, default=128,
                     help="real frequencies of the timed density of states (0 = skip)")
+    ap.add_argument("--metro-steps", type=int, default=10,
+                    help="timed Metropolis steps (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=0,
@@ -303,6 +305,23 @@ def run_ours(args):
                "resolvents_per_s": round(2 * args.dos_points / dos_s, 2),
                "rho_max": round(float(rho.max()), 6)}
 
+    # ---------------- Metropolis sampling of exp(-Omega/T) (Sec. II): LU-only elimination per
+    # step, decisions on the device
+    metro = None
+    if args.metro_steps > 0 and rank == 0:
+        cm = api.Context(params)
+        cm.set_stream(stream)
+        cm.metropolis_init(0.01, seed=wl.seed)
+        cm.metropolis_step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, acc, _, _ = cm.metropolis_step(args.metro_steps)
+        mt_s = time.perf_counter() - t0
+        cm.close()
+        metro = {"steps_per_s": round(args.metro_steps / mt_s, 3),
+                 "ms_per_step": round(mt_s * 1e3 / args.metro_steps, 3), "delta": 0.01,
+                 "acceptance": round(float(acc.mean()), 3), "timed_steps": args.metro_steps}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl)
@@ -329,6 +348,7 @@ def run_ours(args):
             "fp64_path": fp64,
             "no_pivoting_variant": nopiv,
             "dos": dos,
+            "metropolis": metro,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

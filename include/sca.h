@@ -272,6 +272,26 @@ sca_status sca_set_wait_limit(sca_ctx* ctx, int64_t cycles);
 sca_status sca_dos(sca_ctx* ctx, const double* phi_host, const double* w_host, int32_t n_w,
                    double eta, double* rho_out);
 
+/* Metropolis sampling of the static-field weight exp(-Omega(phi)/T) of the SCA partition
+ * function (Sec. II: Z is an integral over phi_1 .. phi_N with weight exp(-beta V), V = Omega).
+ * The chain's state is the context's resident field (the one sca_get_phi returns; Adam's
+ * moments are left alone).  Step t (t = 0, 1, ... counted from sca_metropolis_init):
+ *     phi'_i = phi_i + delta g_i,  g_i = sqrt(-2 ln(1 - U(seed, 2(tN+i)))) cos(2 pi U(seed, 2(tN+i)+1)),
+ *     accepted iff U(seed + 1, t) < exp(-(Omega(phi') - Omega(phi)) / T),
+ * with U(s, k) the top 53 bits of output k of the SplitMix64 stream started at s, times 2^-53.
+ * Omega(phi') comes from the LU-only elimination in the context's precision; steps run on the
+ * device without host round trips.
+ * sca_metropolis_init: phi0_host (N doubles, host) or NULL for the seeded start field;
+ *   delta >= 0 finite; evaluates Omega(phi0).  SCA_EINVAL for bad arguments.
+ * sca_metropolis_step: n_steps >= 0 further steps; optional host outputs omega_trace (n_steps
+ *   doubles: Omega of the state after each step) and accepted (n_steps bytes, 0/1); omega: Omega
+ *   of the final state; accepted_total: accepted steps since init.  SCA_ENOSTATE before init;
+ *   SCA_ENONFINITE if a proposal gave a non-finite Omega (it was rejected).
+ * The paper has no device-side sampler; it names the integral the field is drawn from. */
+sca_status sca_metropolis_init(sca_ctx* ctx, const double* phi0_host, double delta, uint64_t seed);
+sca_status sca_metropolis_step(sca_ctx* ctx, int32_t n_steps, double* omega_trace,
+                               uint8_t* accepted, double* omega, int64_t* accepted_total);
+
 /* Pivoting of the batched elimination of the A_{n,sigma} (Sec. II, Eq. 2).
  *   SCA_PIVOT_PARTIAL (default): partial pivoting for the blocks whose column diagonal
  *     dominance is not guaranteed (omega_n <= 4|t|); the remaining blocks provably keep their

@@ -72,6 +72,9 @@ SIGNATURES = [
     ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("sca_set_pivoting", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_dos", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int32, ctypes.c_double, _dp]),
+    ("sca_metropolis_init", ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_uint64]),
+    ("sca_metropolis_step", ctypes.c_int, [_vp, ctypes.c_int32, _dp, ctypes.POINTER(ctypes.c_uint8),
+                                           _dp, ctypes.POINTER(ctypes.c_int64)]),
     ("sca_profile_enable", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_profile_read", ctypes.c_int, [_vp, ctypes.c_int32, _dp, _u64p]),
     ("sca_flops_per_grad", ctypes.c_double, [_PP]),

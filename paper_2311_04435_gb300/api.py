@@ -157,6 +157,25 @@ class Context:
         check(_lib.lib().sca_dos(self._h, _ptr(phi), _ptr(w), len(w), float(eta), _ptr(out)))
         return out.reshape(2, len(w))
 
+    def metropolis_init(self, delta: float, seed: int = 0, phi0=None):
+        """Start a Metropolis chain on exp(-Omega/T) (Sec. II) at phi0 (or the seeded field)."""
+        self._bump()
+        p = None if phi0 is None else _f64(phi0)
+        check(_lib.lib().sca_metropolis_init(self._h, None if p is None else _ptr(p),
+                                             float(delta), ctypes.c_uint64(seed).value))
+
+    def metropolis_step(self, n_steps: int):
+        """n_steps further steps: (Omega trace, accept flags, final Omega, accepted since init)."""
+        self._bump()
+        om_tr = np.zeros(max(n_steps, 1))
+        acc = np.zeros(max(n_steps, 1), dtype=np.uint8)
+        om = ctypes.c_double()
+        tot = ctypes.c_int64()
+        check(_lib.lib().sca_metropolis_step(
+            self._h, int(n_steps), _ptr(om_tr), acc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+            ctypes.byref(om), ctypes.byref(tot)))
+        return om_tr[:n_steps], acc[:n_steps].astype(bool), om.value, int(tot.value)
+
     def blocks(self, phi, grad: bool = True):
         """Per block b = 2n+s: ln|det A_b| and (grad) sigma_b Re G_b,ii."""
         self._bump()

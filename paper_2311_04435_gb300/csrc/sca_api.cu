@@ -369,6 +369,9 @@ void sca_destroy(sca_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->own) cudaStreamDestroy(c->own);
   if (c->d_in) cudaFree(c->d_in);
+  if (c->d_prop) cudaFree(c->d_prop);
+  if (c->d_metro) cudaFree(c->d_metro);
+  if (c->d_mtrace) cudaFree(c->d_mtrace);
   release(c->e);
   delete c;
 }

@@ -166,6 +166,15 @@ struct sca_ctx {
   int32_t step = 0;
   bool kept = false;              // inverses of every block resident from sca_forward_dev
   const double* kept_phi = nullptr;
+  // Metropolis chain (sca_metropolis_*): the state is e.d_phi
+  double* d_prop = nullptr;       // N: proposal
+  double* d_metro = nullptr;      // 4: Omega of the state, accepted, last proposal, non-finite
+  double* d_mtrace = nullptr;     // 2 x capacity: per-step Omega and accept flag
+  int32_t mtrace_cap = 0;
+  double m_delta = 0.0;
+  uint64_t m_seed = 0;
+  int64_t m_step = 0;             // global step number of the next proposal
+  bool metro_ready = false;
 };
 
 namespace sca {
