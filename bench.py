@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ionic_40x40")
-    ap.add_argument("--prec", default=None, help="fp32 | 3xtf32 (default: the fastest built)")
+    ap.add_argument("--prec", default=None,
+                    help="fp32 | 3xtf32 | bf16x3 (default: bf16x3)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 steps (0 = skip)")
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="timed steps of the no-pivoting variant (0 = skip)")
@@ -125,28 +126,62 @@ def peaks():
 # Nominal dense ratios (tf32 1.1 PF vs bf16 2.25 PF per GPU) and the CUDA-core rates measured
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
+DEFAULT_PREC = "bf16x3"
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum averaged over 8 update launches of a 16-block
-# 40x40 gradient: 434.0 MB per launch; traffic grows with the blocks).  The algorithmic bytes
-# are ~30 MB per block (lower-triangle tiles of M read and written, F and W planes once).
-UPDATE_TC_BYTES_PER_BLOCK_N1600 = 434.0e6 / 16
+# 40x40 gradient, divided by 16; traffic grows with the blocks), per split precision, for the
+# kernel as captured (profiles/).  3xTF32: 434.0 MB per 16-block launch; BF16x3: 358.6 MB.
+UPDATE_BYTES_PER_BLOCK_N1600 = {"3xtf32": 434.0e6 / 16, "bf16x3": 358.6e6 / 16}
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
 
-def roofline_for(prec: str, achieved_tflops: float, traffic):
+def update_algorithmic(prec: str, N: int, nb: int, sym: bool):
+    """Algorithmic flops and bytes of one dominant-group update launch, per block: 8 kb flops
+    per updated complex entry (lower triangle on or below the diagonal when symmetric), the
+    updated tiles of M read and written once (complex64), the F (4) and W (6) split planes
+    read once (bf16 or float32 elements)."""
+    tiles = (N + 127) // 128
+    rows = [min(128, N - 128 * t) for t in range(tiles)]
+    area = sum(rows[a] * rows[b] for a in range(tiles) for b in range(tiles) if b <= a or not sym)
+    flops = 8.0 * nb * (N * (N + 1) / 2 if sym else float(N) * N)
+    es = 2 if prec == "bf16x3" else 4
+    bytes_ = 2.0 * 8.0 * area + 10.0 * N * nb * es
+    return flops, bytes_
+
+
+def roofline_for(prec: str, flops: float, bytes_: float, seconds: float, traffic):
+    """The dominant kernel against the roofline: its bound is the lower of the tensor peak for
+    its arithmetic and the HBM bandwidth times its algorithmic intensity."""
     pk, src = peaks()
+    hbm = pk["hbm_gbs"]
     if prec == "3xtf32":
         tf32 = pk["bf16_tflops_sustained"] * TF32_OVER_BF16
         peak = tf32 / 3.0  # three TF32 products per complex-split product
         bound, note = "tensor", f"tf32 = {src} sustained bf16 x 1.1/2.25, / 3 for the split"
+    elif prec == "bf16x3":
+        peak = pk["bf16_tflops_sustained"] / 3.0  # three bf16 products per split product
+        bound, note = "tensor", f"{src} sustained bf16, / 3 for the split"
     elif prec == "fp32":
         peak, bound, note = FP32_SIMT_TFLOPS, "alu", "FP32 CUDA-core FMA rate measured on GB300"
     else:
         peak, bound, note = FP64_SIMT_TFLOPS, "alu", "FP64 FMA rate measured on GB300"
-    return {"bound": bound, "achieved": round(achieved_tflops, 3), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved_tflops / peak, 4), "traffic": traffic,
-            "kernel": "update (rank-nb Gauss-Jordan contraction)", "peak_source": note}
+    tflops = flops / seconds / 1e12 if seconds > 0 else 0.0
+    gbs = bytes_ / seconds / 1e9 if seconds > 0 else 0.0
+    intensity = flops / bytes_
+    out = {"kernel": "update (rank-nb Gauss-Jordan contraction)",
+           "intensity_flop_per_byte": round(intensity, 2),
+           "tensor_tflops": round(tflops, 3), "tensor_peak": round(peak, 3)}
+    if bound == "tensor" and intensity * hbm / 1e3 < peak:
+        out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": round(hbm, 1),
+                    "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": traffic,
+                    "peak_source": f"{src} HBM copy bandwidth (intensity {intensity:.1f} flop/B "
+                                   f"is below the ridge {peak * 1e3 / hbm:.1f} of {note})"})
+    else:
+        out.update({"bound": bound, "achieved": round(tflops, 3), "peak": round(peak, 3),
+                    "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": traffic,
+                    "peak_source": note})
+    return out
 
 
 def aggregate_replicas(ms_local: float, steps: int, world: int):
@@ -175,7 +210,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     wl = inputs.WORKLOADS[args.workload]
-    prec = args.prec or "3xtf32"
+    prec = args.prec or DEFAULT_PREC
     params = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, t=wl.t, mu=wl.mu,
                         prec=prec)
     adam = api.AdamConfig(lr=wl.lr, seed=wl.seed)
@@ -218,13 +253,14 @@ def run_ours(args):
     # 4 N^2 (N + 1) per block; the full update (CUDA cores, or SCA_SYM=0) needs 8 N^3.
     upd_ms, upd_n = prof["update"]
     n_dom = 2 * wl.n_omega - api.pivoted_blocks(params)
-    N = float(params.N)
-    sym = prec == "3xtf32" and os.environ.get("SCA_SYM", "1") != "0"
-    flops_dom = (4.0 * N * N * (N + 1.0) if sym else 8.0 * N ** 3) * n_dom
-    achieved = flops_dom / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    sym = prec in ("3xtf32", "bf16x3") and os.environ.get("SCA_SYM", "1") != "0"
+    fl_blk, by_blk = update_algorithmic(prec, params.N, 128 if prec in ("3xtf32", "bf16x3") else 64,
+                                        sym)
+    launch_s = (upd_ms / 1e3) / max(upd_n, 1)  # average duration of one update launch
     traffic = None
-    if sym and params.N == 1600 and UPDATE_TC_BYTES_PER_BLOCK_N1600:
-        traffic = round(UPDATE_TC_BYTES_PER_BLOCK_N1600 * n_dom, 0)  # bytes per launch
+    per_block = UPDATE_BYTES_PER_BLOCK_N1600.get(prec)
+    if sym and params.N == 1600 and per_block:
+        traffic = round(per_block * n_dom, 0)  # bytes per launch
     per_kernel = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
     ctx.close()
 
@@ -287,6 +323,28 @@ def run_ours(args):
                  "timed_steps": args.variant_steps, "warmup": 1, "final_omega": omn,
                  "final_gmax": gmn}
 
+    # ---------------- the other split precision beside it (same workload, same path)
+    other = None
+    if args.variant_steps > 0 and rank == 0 and prec in ("3xtf32", "bf16x3"):
+        oprec = "3xtf32" if prec == "bf16x3" else "bf16x3"
+        po = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, t=wl.t, mu=wl.mu,
+                        prec=oprec)
+        co = api.Context(po)
+        co.set_stream(stream)
+        co.adam_init(adam)
+        co.adam_step(1)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        omo, gmo = co.adam_step(args.variant_steps)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        mso = a0.elapsed_time(a1) / args.variant_steps
+        co.close()
+        other = {"prec": oprec, "steps_per_s": round(1e3 / mso, 4), "ms_per_step": round(mso, 3),
+                 "timed_steps": args.variant_steps, "warmup": 1, "final_omega": omo,
+                 "final_gmax": gmo}
+
     # ---------------- density of states at the final field (Sec. II): one batch of n_omega
     # real frequencies per spin, every resolvent pivoted (eta < 4t)
     dos = None
@@ -331,8 +389,8 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 storage, 3xtf32 contractions, f64 log-det and diag(G) refinement"
-            if prec == "3xtf32" else "f32" if prec == "fp32" else "f64",
+            "dtype": f"f32 storage, {prec} contractions, f64 log-det and diag(G) refinement"
+            if prec in ("3xtf32", "bf16x3") else "f32" if prec == "fp32" else "f64",
             "data": "synthetic (seeded SplitMix64 start field, no dataset)",
             "config": {"workload": f"{args.workload}: L={wl.L} (N={params.N}), U={wl.U}, "
                                    f"Delta={wl.delta}, T={wl.T}, n_omega={wl.n_omega}, "
@@ -343,10 +401,11 @@ def run_ours(args):
                        "final_omega": om, "final_gmax": gm},
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": roofline_for(prec, achieved, traffic),
+            "roofline": roofline_for(prec, fl_blk * n_dom, by_blk * n_dom, launch_s, traffic),
             "kernels_ms_one_step": per_kernel,
             "fp64_path": fp64,
             "no_pivoting_variant": nopiv,
+            "other_precision": other,
             "dos": dos,
             "metropolis": metro,
             "clocks": clk,
@@ -423,7 +482,7 @@ def run_serve(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     trace = inputs.serving_trace(args.serve, rate_per_s=args.serve_rate)
-    prec = args.prec or "3xtf32"
+    prec = args.prec or DEFAULT_PREC
     reqs = [(api.Params(r.L, r.n_omega, U=r.U, T=r.T, delta=r.delta, prec=prec),
              api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=args.serve_steps, seed=r.seed))
             for r in trace]

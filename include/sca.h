@@ -66,15 +66,19 @@ typedef enum {
 /* Arithmetic of the dense contractions.  FP64: everything in float64.
  * FP32: blocks stored as complex64, CUDA-core float32 contractions.
  * 3XTF32: complex64 blocks, contractions on tcgen05 tensor cores in split
- * TF32 (hi*hi + hi*lo + lo*hi) with float32 accumulation.
+ * TF32 (hi*hi + hi*lo + lo*hi, hi = the value with 13 low mantissa bits cleared) with
+ * float32 accumulation.
+ * BF16X3: complex64 blocks, the same contractions with bf16 halves (hi = RN_bf16(v),
+ * lo = RN_bf16(v - hi): about 17 significant bits) on kind::f16 at twice the TF32 rate.
  * For the three reduced-precision modes ln|u_kk| is accumulated in float64
  * and every diagonal G_ii gets one float64 refinement step
- * (G_ii <- 2 X_ii - (X A X^T)_ii with the sparse A). */
+ * (G_ii <- 2 X_ii - (X A X^T)_ii with the sparse A).  Blocks below 128 x 128 take the FP32
+ * path in both split modes. */
 typedef enum {
   SCA_PREC_FP64 = 0,
   SCA_PREC_FP32 = 1,
   SCA_PREC_3XTF32 = 2,
-  SCA_PREC_BF16X3 = 3  /* reserved; sca_create returns SCA_EINVAL */
+  SCA_PREC_BF16X3 = 3
 } sca_prec;
 
 typedef enum {

@@ -20,7 +20,7 @@ SCA_OK, SCA_EINVAL, SCA_ENOMEM, SCA_EBUDGET, SCA_ECUDA, SCA_ETIMEOUT, SCA_EPENDI
     SCA_ENONFINITE, SCA_ENOTFOUND, SCA_ENOSTATE = range(10)
 STATUS_NAMES = ["SCA_OK", "SCA_EINVAL", "SCA_ENOMEM", "SCA_EBUDGET", "SCA_ECUDA", "SCA_ETIMEOUT",
                 "SCA_EPENDING", "SCA_ENONFINITE", "SCA_ENOTFOUND", "SCA_ENOSTATE"]
-PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2}
+PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2, "bf16x3": 3}
 IONIC = {"paper": 0, "half": 1}
 
 

@@ -36,7 +36,7 @@ class Params:
     delta: float = 0.0
     t: float = 1.0
     mu: float = 0.0
-    prec: str = "fp64"        # "fp64" | "fp32" | "3xtf32"
+    prec: str = "fp64"        # "fp64" | "fp32" | "3xtf32" | "bf16x3"
     ionic: str = "paper"      # "paper" (-/+Delta) | "half" (-/+Delta/2)
 
     @property

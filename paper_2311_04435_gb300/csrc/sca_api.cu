@@ -47,8 +47,8 @@ static sca_status validate(const sca_params* p) {
     set_error("t, delta and mu must be finite");
     return SCA_EINVAL;
   }
-  if (p->prec < SCA_PREC_FP64 || p->prec > SCA_PREC_3XTF32) {
-    set_error("prec must be SCA_PREC_FP64, SCA_PREC_FP32 or SCA_PREC_3XTF32");
+  if (p->prec < SCA_PREC_FP64 || p->prec > SCA_PREC_BF16X3) {
+    set_error("prec must be SCA_PREC_FP64, SCA_PREC_FP32, SCA_PREC_3XTF32 or SCA_PREC_BF16X3");
     return SCA_EINVAL;
   }
   if (p->ionic != SCA_IONIC_PAPER && p->ionic != SCA_IONIC_HALF) {
@@ -80,7 +80,9 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.refine = !e.fp64;
   e.delta_eff = (p.ionic == SCA_IONIC_HALF) ? 0.5 * p.delta : p.delta;
   // tcgen05 path for blocks of at least 128 rows; smaller blocks use CUDA cores.
-  e.tc = (p.prec == SCA_PREC_3XTF32) && e.N >= 128 && tc_supported();
+  e.tc = (p.prec == SCA_PREC_3XTF32 || p.prec == SCA_PREC_BF16X3) && e.N >= 128 &&
+         tc_supported();
+  e.bf16 = e.tc && p.prec == SCA_PREC_BF16X3;
   int nb = e.fp64 ? 32 : (e.tc ? 128 : 64);
   if (const char* v = std::getenv("SCA_NB")) {
     const int x = std::atoi(v);

@@ -22,6 +22,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "sca_internal.h"
 #include "sca_device.cuh"
 
@@ -379,7 +381,7 @@ template <typename S, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_stride,
                                                 size_t plane_stride, int k0, int kb, int nb,
                                                 int b0, double* ld, cpx<C>* Tinv, float* TT,
-                                                int* flags) {
+                                                int tt_bf16, int* flags) {
   // The block is padded to KB x KB with the identity (pivots 1: no effect on ln|det|; the
   // padded inverse is diag(T, I)), so the thread -> (row, column) map is compile-time:
   // column j = tid % KB, rows r = tid / KB + q * RS.  The owners of row / column c + 1
@@ -451,7 +453,19 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
     const bool in = r < kb && j < kb;
     const cpx<C> v = in ? a[q] : cpx<C>{(C)0, (C)0};
     T[(size_t)r * nb + j] = v;
-    if (tt) {  // W_T[j][r] = -T[r][j], split for TF32
+    if (tt && tt_bf16) {  // W_T[j][r] = -T[r][j], split into bf16 planes
+      const size_t o = (size_t)j * nb + r;
+      const float fr = -(float)v.re, fi = -(float)v.im;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi = __float2bfloat16_rn(fi);
+      const __nv_bfloat16 lr = __float2bfloat16_rn(fr - __bfloat162float(hr));
+      const __nv_bfloat16 li = __float2bfloat16_rn(fi - __bfloat162float(hi));
+      reinterpret_cast<__nv_bfloat16*>(tt)[o] = hr;
+      reinterpret_cast<__nv_bfloat16*>(tt + P)[o] = hi;
+      reinterpret_cast<__nv_bfloat16*>(tt + 2 * P)[o] = lr;
+      reinterpret_cast<__nv_bfloat16*>(tt + 3 * P)[o] = li;
+      reinterpret_cast<__nv_bfloat16*>(tt + 4 * P)[o] = __hneg(hi);
+      reinterpret_cast<__nv_bfloat16*>(tt + 5 * P)[o] = __hneg(li);
+    } else if (tt) {  // W_T[j][r] = -T[r][j], split for TF32
       float* o = tt + (size_t)j * nb + r;
       const float fr = -(float)v.re, fi = -(float)v.im;
       const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
@@ -558,10 +572,26 @@ __global__ void k_split_f(const float* Fp, size_t fp_plane, size_t fp_mat, const
 // bits cleared, exact in TF32; lo = value - hi) and W adds {-im_hi, -im_lo}.
 template <typename S>
 __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, double vre, double vim,
-                                         bool split, bool neg) {
+                                         int split, bool neg) {
   if (!split) {
     base[off] = (S)vre;
     base[plane + off] = (S)vim;
+  } else if (split == 2) {
+    // bf16 planes (BF16x3): hi = RN_bf16(v), lo = RN_bf16(v - hi); a plane starts where the
+    // float32 plane would, element `off` at 2 bytes
+    const float fr = (float)vre, fi = (float)vim;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi = __float2bfloat16_rn(fi);
+    const __nv_bfloat16 lr = __float2bfloat16_rn(fr - __bfloat162float(hr));
+    const __nv_bfloat16 li = __float2bfloat16_rn(fi - __bfloat162float(hi));
+    float* b = reinterpret_cast<float*>(base);
+    reinterpret_cast<__nv_bfloat16*>(b)[off] = hr;
+    reinterpret_cast<__nv_bfloat16*>(b + plane)[off] = hi;
+    reinterpret_cast<__nv_bfloat16*>(b + 2 * plane)[off] = lr;
+    reinterpret_cast<__nv_bfloat16*>(b + 3 * plane)[off] = li;
+    if (neg) {
+      reinterpret_cast<__nv_bfloat16*>(b + 4 * plane)[off] = __hneg(hi);
+      reinterpret_cast<__nv_bfloat16*>(b + 5 * plane)[off] = __hneg(li);
+    }
   } else {
     const float fr = (float)vre, fi = (float)vim;
     const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
@@ -665,7 +695,7 @@ __global__ void __launch_bounds__(256)
       } else {
         vr = (double)ar[a][q]; vi = (double)ai[a][q];
       }
-      store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split != 0, false);
+      store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split, false);
     }
   }
 }
@@ -715,7 +745,7 @@ __global__ void __launch_bounds__(256)
       vr = (double)tr[c * 65 + jj];
       vi = (double)ti[c * 65 + jj];
     }
-    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split != 0, true);
+    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split, true);
   }
 }
 
@@ -1090,7 +1120,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   int* piv = e.piv + (size_t)m0 * N;
   int* perm = e.perm + (size_t)m0 * N;
   const size_t fw_plane = (size_t)N * nb;
-  const int split = tcg ? 1 : 0;
+  const int split = tcg ? (e.bf16 ? 2 : 1) : 0;
   // dominant blocks on the tensor cores: symmetric updates (lower tiles only)
   bool sym = tcg && !pivoted && e.tt != nullptr;
   if (const char* v = std::getenv("SCA_SYM"))
@@ -1141,7 +1171,8 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
       k_diag_gj<S, C, 768><<<cnt, 768, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
-                                                kb, nb, b0, e.ld, Tinv, TT, e.flags);
+                                                kb, nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0,
+                                                e.flags);
       prof_end(e, kDiag, s);
       SCA_LAUNCH_CHECK("diag");
     }
@@ -1161,7 +1192,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kPrep, s);
     } else {
       prof_begin(e, kPrep, s);
-      if (tcg && !pivoted && nb == e.nb && e.tt) {
+      if (tcg && !pivoted && nb == e.nb && e.tt && !e.bf16) {
         // F = M[:, K] T on the tensor cores (scratch: the W planes, rewritten below)
         const int rs = r0;
         const size_t tot = (size_t)(N - rs) * nb;

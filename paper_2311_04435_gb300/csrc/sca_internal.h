@@ -34,7 +34,8 @@ struct Engine {
   int chunk = 0;         // blocks resident at once
   bool fp64 = false;     // storage and arithmetic of the blocks
   bool refine = false;   // FP64 refinement of diag(G)
-  bool tc = false;       // tcgen05 3xTF32 rank-nb update
+  bool tc = false;       // tcgen05 split-precision rank-nb update (3xTF32 or BF16x3)
+  bool bf16 = false;     // BF16x3: bf16 hi/lo planes on kind::f16 (else TF32 planes)
   double delta_eff = 0;  // Delta or Delta/2 (ionic convention)
   size_t plane_stride = 0, mat_stride = 0;  // elements
   size_t fw_plane = 0, fw_mat = 0;          // F / W panel strides (elements)

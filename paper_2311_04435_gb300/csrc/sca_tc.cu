@@ -27,6 +27,8 @@
 #include <cstring>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "sca_internal.h"
 
 namespace sca {
@@ -162,6 +164,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
 }
 
+// kind::f16 with A = B = bf16, D = f32, both K-major, M = 128, N = 256 (BF16x3 path).
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
+                                ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescBf16), "r"(acc));
+}
+
+template <bool BF>
+__device__ __forceinline__ void mma_split(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (BF) mma_bf16(d_tmem, a, b, acc);
+  else mma_tf32(d_tmem, a, b, acc);
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -241,9 +261,13 @@ __device__ __forceinline__ void decode_tile(const TcArgs& a, int t, int& mat, in
 __constant__ int kFPlaneOfSlot[4] = {0, 1, 2, 3};
 __constant__ int kWPlaneOfSlot[6] = {4, 0, 1, 5, 2, 3};
 
+// BF: the operand planes are bf16 (BF16x3 on kind::f16, 32 K-elements per 64-byte stage row)
+// instead of TF32-split float32 (16 per row); the stage layout in bytes is the same.
+template <bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmW,
                 const __grid_constant__ CUtensorMap tmM, TcArgs a) {
+  constexpr int kKE = BF ? 32 : kKS;  // K elements per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -282,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int ksteps = a.nb / kKS;
+  const int ksteps = a.nb / kKE;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -310,10 +334,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(&full[stage], kStageBytes);
           unsigned char* st = smem + stage * kStageBytes;
           for (int s = 0; s < 4; ++s)
-            tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKS, frow,
+            tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKE, frow,
                         (a.mat0 + mat) * a.fplanes + kFPlaneOfSlot[s]);
           for (int s = 0; s < 6; ++s)
-            tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKS, wrow,
+            tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKE, wrow,
                         (a.mat0 + mat) * a.wplanes + kWPlaneOfSlot[s]);
           last_parity[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -360,12 +384,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t b2_lo = sdesc_k64(st + 7 * kTileBytes + off);
             const uint64_t b1_lo = sdesc_k64(st + 8 * kTileBytes + off);
             const uint32_t acc0 = (ks > 0 || k8 > 0) ? 1u : 0u;
-            mma_tf32(d_tmem, fr_hi, b1_hi, acc0);
-            mma_tf32(d_tmem, fr_hi, b1_lo, 1u);
-            mma_tf32(d_tmem, fr_lo, b1_hi, 1u);
-            mma_tf32(d_tmem, fi_hi, b2_hi, 1u);
-            mma_tf32(d_tmem, fi_hi, b2_lo, 1u);
-            mma_tf32(d_tmem, fi_lo, b2_hi, 1u);
+            mma_split<BF>(d_tmem, fr_hi, b1_hi, acc0);
+            mma_split<BF>(d_tmem, fr_hi, b1_lo, 1u);
+            mma_split<BF>(d_tmem, fr_lo, b1_hi, 1u);
+            mma_split<BF>(d_tmem, fi_hi, b2_hi, 1u);
+            mma_split<BF>(d_tmem, fi_hi, b2_lo, 1u);
+            mma_split<BF>(d_tmem, fi_lo, b2_hi, 1u);
           }
           mma_commit(&empty[stage]);  // frees the stage once these MMAs have read it
           if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -441,6 +465,47 @@ __global__ void __launch_bounds__(kThreads, 1)
               rowk ? a.T + (size_t)(a.mat0 + mat) * a.t_mat + (size_t)(i - a.k0) * a.nb : nullptr;
           unsigned char* s0 = epi;
           unsigned char* s1 = epi + kEpiBufBytes;
+          if constexpr (BF) {
+            // four bf16 planes of 128 rows x 64 bytes (8 KB each) in buffer 0, 64-byte swizzle:
+            // 16-byte unit u of row r sits at unit u ^ ((r >> 1) & 3)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int off = row * 64 + ((u ^ ((row >> 1) & 3)) << 4);
+              __nv_bfloat16 h[4][8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int j = jc + 8 * u + e;
+                float vr, vi;
+                if (rowk) {
+                  const float2 tv = (j < a.kb) ? trow[j] : make_float2(0.f, 0.f);
+                  vr = -tv.x;
+                  vi = -tv.y;
+                } else {
+                  vr = -__uint_as_float(cr[8 * u + e]);
+                  vi = -__uint_as_float(ci[8 * u + e]);
+                  if (neg) { vr = -vr; vi = -vi; }
+                }
+                h[0][e] = __float2bfloat16_rn(vr);
+                h[1][e] = __float2bfloat16_rn(vi);
+                h[2][e] = __float2bfloat16_rn(vr - __bfloat162float(h[0][e]));
+                h[3][e] = __float2bfloat16_rn(vi - __bfloat162float(h[1][e]));
+              }
+#pragma unroll
+              for (int pl = 0; pl < 4; ++pl)
+                *reinterpret_cast<uint4*>(s0 + pl * (kBM * 64) + off) =
+                    *reinterpret_cast<const uint4*>(h[pl]);
+            }
+            fence_proxy_async();
+            epi_bar();
+            if (leader) {
+              const int y = a.r0 + tm * kBM;
+              const int zb = (a.mat0 + mat) * a.m_zmul + a.m_zoff;
+#pragma unroll
+              for (int pl = 0; pl < 4; ++pl) tma_store_3d(&tmM, s0 + pl * (kBM * 64), jc, y, zb + pl);
+              bulk_commit();
+            }
+            continue;
+          }
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int off = row * 128 + ((k ^ (row & 7)) << 4);
@@ -593,31 +658,38 @@ struct TcMaps {
   int sms = 0;
 };
 
-// 3-D map over [blocks*planes][N rows][nbk] floats, box 16 x 128 x 1, 64-byte swizzle.
-bool make_fw_map(CUtensorMap* m, void* base, int nbk, int N, long long zdim) {
+// 3-D map over [blocks*planes][N rows][nbk] elements, box (64 bytes of K) x 128 x 1, 64-byte
+// swizzle: float32 planes (16 K-elements per box row) or bf16 planes (32), a bf16 plane
+// starting where the float32 plane would (plane stride N nbk x 4 bytes either way).
+bool make_fw_map(CUtensorMap* m, void* base, int nbk, int N, long long zdim, bool bf16 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  const cuuint64_t es_bytes = bf16 ? 2 : 4;
   cuuint64_t dims[3] = {(cuuint64_t)nbk, (cuuint64_t)N, (cuuint64_t)zdim};
-  cuuint64_t strides[2] = {(cuuint64_t)nbk * 4, (cuuint64_t)N * nbk * 4};
-  cuuint32_t box[3] = {(cuuint32_t)kKS, (cuuint32_t)kBM, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)nbk * es_bytes, (cuuint64_t)N * nbk * 4};
+  cuuint32_t box[3] = {(cuuint32_t)(bf16 ? 32 : kKS), (cuuint32_t)kBM, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
+  return fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+            dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // 3-D map over [z][rows][cols] floats (row stride ld), box 32 x 128 x 1, 128-byte swizzle: the
 // epilogue's staging tile.
+// bf16: the same rows of bf16 elements (64-byte staging rows, 64-byte swizzle); zstride counts
+// float32 elements either way.
 bool make_m_map_rows(CUtensorMap* m, void* base, int cols, int rows, int ld, long long zstride,
-                     long long z) {
+                     long long z, bool bf16 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)z};
-  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)zstride * 4};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * (bf16 ? 2 : 4), (cuuint64_t)zstride * 4};
   cuuint32_t box[3] = {(cuuint32_t)kEpiCols, (cuuint32_t)kBM, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  return fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+            dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -665,7 +737,8 @@ sca_status tc_prepare(Engine& e) {
   std::memset(&t->W, 0, sizeof(t->W));
   std::memset(&t->M, 0, sizeof(t->M));
   const long long zf = (long long)e.chunk * (long long)(e.fw_mat / e.fw_plane);
-  if (!make_fw_map(&t->F, e.F, e.nb, e.N, zf) || !make_fw_map(&t->W, e.W, e.nb, e.N, zf) ||
+  if (!make_fw_map(&t->F, e.F, e.nb, e.N, zf, e.bf16) ||
+      !make_fw_map(&t->W, e.W, e.nb, e.N, zf, e.bf16) ||
       !make_m_map(&t->M, e.M, e.N, e.ldm, (long long)e.plane_stride, 2ll * e.chunk)) {
     delete t;
     set_error("cuTensorMapEncodeTiled failed for the tensor-core update");
@@ -675,9 +748,10 @@ sca_status tc_prepare(Engine& e) {
     // F = M[:, K] T on the tensor cores: A = split pivot columns (W scratch planes 0-3, same
     // map as W), B = -T^T planes, output planar into W scratch planes 4, 5.
     const long long ztt = (long long)e.chunk * 6;
-    bool ok = !e.tt || (make_fw_map(&t->TT, e.tt, e.nb, e.nb, ztt) &&
-                        make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf) &&
-                        make_m_map_rows(&t->FO, e.F, e.nb, e.N, e.nb, (long long)e.fw_plane, zf));
+    bool ok = !e.tt ||
+              (make_fw_map(&t->TT, e.tt, e.nb, e.nb, ztt, e.bf16) &&
+               make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf) &&
+               make_m_map_rows(&t->FO, e.F, e.nb, e.N, e.nb, (long long)e.fw_plane, zf, e.bf16));
     if (!ok) {
       delete t;
       set_error("cuTensorMapEncodeTiled failed for the tensor-core prep product");
@@ -688,7 +762,11 @@ sca_status tc_prepare(Engine& e) {
   cudaError_t err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    err = cudaFuncSetAttribute(k_update_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemBytes);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_update_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemBytes);
   if (err != cudaSuccess) {
     delete t;
     return cuda_fail(err, "tcgen05 update set-up");
@@ -756,7 +834,8 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
+  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
+  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 update launch");
@@ -803,7 +882,7 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
+  k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
@@ -851,7 +930,8 @@ sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, boo
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  k_update_tc<<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
+  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
+  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");

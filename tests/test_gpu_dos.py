@@ -24,7 +24,7 @@ def tol(prec):
     return 1e-10 if prec == "fp64" else 2e-5
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3"])
 @pytest.mark.parametrize("L,nw,n_w,eta", [(4, 3, 7, 0.1), (10, 4, 9, 0.2), (20, 6, 13, 0.15)])
 def test_dos_matches_oracle(prec, L, nw, n_w, eta):
     """Several batches of n_omega frequencies with a short last one; random field plus

@@ -14,7 +14,7 @@ from paper_2311_04435_gb300 import _lib, api, inputs
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp64", "fp32", "3xtf32"]
+PRECS = ["fp64", "fp32", "3xtf32", "bf16x3"]
 
 
 def oparams(p: api.Params):
@@ -321,3 +321,22 @@ def test_no_pivoting_matches_oracle(prec):
     assert om_p == pytest.approx(o_om, rel=t["om"])
     for gg in (g, g_p):
         assert np.max(np.abs(gg - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+def test_full_size_40x40_sampled_blocks(prec):
+    """The benchmark's workload at full size (L = 40: 256 blocks of 1600 x 1600, 12 pivoted,
+    244 dominant, symmetric tensor-core update, SM reserve and side stream as timed): per-block
+    ln|det| and sigma Re G_ii of a sample of pivoted and dominant blocks against the oracle,
+    which computes those blocks one by one."""
+    wl = inputs.WORKLOADS["ionic_40x40"]
+    p = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, t=wl.t, mu=wl.mu, prec=prec)
+    assert api.pivoted_blocks(p) == 12
+    phi = inputs.seed_phi(wl.seed, p.N)
+    with api.Context(p) as c:
+        ld, gd = c.blocks(phi, grad=True)
+    sample = [0, 1, 11, 12, 13, 128, 255]
+    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, sample)
+    t = tol(prec)
+    assert np.allclose(ld[sample], o_ld, rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(gd[sample] - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
