@@ -316,7 +316,9 @@ sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
  * 2 row interchanges, 3 pivot-block inverse of the pivoted group, 4 rank-nb factors,
  * 5 rank-nb update of the dominant blocks (the dominant contraction), 6 refine (adjoint
  * diag(G)), 7 reduce (+Adam), 8 pivot-block inverse of the dominant blocks, 9 rank-nb update
- * of the pivoted group, 10 fused small-block Adam launch.  Enabling resets the counters.  Timing adds a small host overhead per
+ * of the pivoted group, 10 fused small-block Adam launch, 11 wall span of the pivoted group on
+ * its stream, 12 wall span of the dominant group on the main stream (spans contain the
+ * kernels above, so they are not part of any sum).  Enabling resets the counters.  Timing adds a small host overhead per
  * launch; keep it off when measuring throughput. */
 sca_status sca_profile_enable(sca_ctx* ctx, int32_t enable);
 sca_status sca_profile_read(sca_ctx* ctx, int32_t kind, double* total_ms, uint64_t* launches);

@@ -238,7 +238,7 @@ class Context:
 
     # ---- streams and per-kernel timing
     KINDS = ["assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
-             "update_piv", "fused"]
+             "update_piv", "fused", "span_pivoted", "span_dominant"]
 
     def set_stream(self, stream=None):
         """Enqueue on a torch.cuda.Stream (or raw handle); None restores the own stream."""

@@ -23,7 +23,7 @@ thread_local std::string t_err;
 
 // SMs the dominant group's persistent tensor-core launches leave free while the pivoted
 // group runs beside them on its own (high-priority) stream.
-constexpr int kDefaultSmReserve = 8;
+constexpr int kDefaultSmReserve = 16;
 }
 
 void set_error(const std::string& msg) { t_err = msg; }
@@ -221,6 +221,19 @@ void prof_begin(Engine& e, int kind, cudaStream_t s) {
   r.a = p->pool[p->used++];
   r.b = p->pool[p->used++];
   cudaEventRecord(r.a, s);
+}
+
+int prof_span_begin(Engine& e, int kind, cudaStream_t s) {
+  Profiler* p = e.prof;
+  if (!p || !p->on) return -1;
+  prof_begin(e, kind, s);
+  return p->nrec - 1;
+}
+
+void prof_span_end(Engine& e, int rec, cudaStream_t s) {
+  Profiler* p = e.prof;
+  if (!p || !p->on || rec < 0 || rec >= p->nrec) return;
+  cudaEventRecord(p->recs[rec].b, s);
 }
 
 void prof_end(Engine& e, int kind, cudaStream_t s) {

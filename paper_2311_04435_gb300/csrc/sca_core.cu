@@ -174,8 +174,9 @@ __global__ void k_swap(S* M, int N, int ldm, size_t mat_stride, size_t plane_str
 // ------------------------------------------------------------ panel (SMEM)
 // Pivoted LU of the column panel rows [k0, N) x cols [k0, k0+kb) of each block, one CTA per
 // block, the m x kb panel (m = N - k0) held in shared memory for the whole column loop.
-// Pivot: row of largest |z|^2 (first index on ties), found with warp shuffles then across
-// warps.  ld[b] += sum ln|u_kk| in float64; piv / perm record the interchanges.
+// Pivot: row of largest |z|^2 in the compute type (first index on ties), found with warp
+// shuffles then across warps.  ld[b] += sum ln|u_kk| in float64; piv / perm record the
+// interchanges.
 template <typename S, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t mat_stride,
                                                    size_t plane_stride, int k0, int kb, int b0,
@@ -183,12 +184,17 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   extern __shared__ unsigned char smem_raw[];
   cpx<C>* P = reinterpret_cast<cpx<C>*>(smem_raw);  // m x (kb+1), row-major, padded
   const int ps = kb + 1;  // odd row stride: conflict-free column access
-  __shared__ double red_v[NT / 32];
+  __shared__ C red_v[NT / 32];
   __shared__ int red_i[NT / 32];
   __shared__ int s_p;
   __shared__ double piv2[256];
   const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = N - k0;
+  // after the panel: the pivot row (panel-relative) of each column, then the perm entries
+  // the interchanges touch (positions and values, 2 kb each)
+  int* s_sw = reinterpret_cast<int*>(P + (size_t)m * ps);
+  int* s_pos = s_sw + kb;
+  int* s_val = s_pos + 2 * kb;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
   for (int e = tid; e < m * kb; e += NT) {
@@ -198,27 +204,28 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   }
   __syncthreads();
   for (int c = 0; c < kb; ++c) {
-    double best = -1.0;
+    // |z|^2 in the compute type: the pivot is the stored entry of largest modulus
+    C best = (C)-1;
     int bi = m;
     for (int r = c + tid; r < m; r += NT) {
       const cpx<C> z = P[r * ps + c];
-      const double v = (double)z.re * z.re + (double)z.im * z.im;
+      const C v = z.re * z.re + z.im * z.im;
       if (v > best) { best = v; bi = r; }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, off);
+      const C ov = __shfl_down_sync(0xffffffffu, best, off);
       const int oi = __shfl_down_sync(0xffffffffu, bi, off);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
     if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
     __syncthreads();
     if (warp == 0) {
-      best = (lane < NT / 32) ? red_v[lane] : -1.0;
+      best = (lane < NT / 32) ? red_v[lane] : (C)-1;
       bi = (lane < NT / 32) ? red_i[lane] : m;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, off);
+        const C ov = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
@@ -234,12 +241,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
       }
     if (tid == 0) {
       piv[(size_t)mat * N + k0 + c] = k0 + p;
-      if (p != c) {
-        int* pm = perm + (size_t)mat * N;
-        const int tmp = pm[k0 + c];
-        pm[k0 + c] = pm[k0 + p];
-        pm[k0 + p] = tmp;
-      }
+      s_sw[c] = p;
     }
     __syncthreads();
     const cpx<C> d = P[c * ps + c];
@@ -263,115 +265,44 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     re[o] = (S)P[r * ps + c].re;
     im[o] = (S)P[r * ps + c].im;
   }
+  // The row permutation: the kb interchanges (c, s_sw[c]) applied in order to the perm
+  // entries they touch, gathered once, swapped in shared memory and written back.
+  {
+    int* pm = perm + (size_t)mat * N + k0;
+    if (tid < 2 * kb) {
+      const int q = (tid < kb) ? tid : s_sw[tid - kb];
+      s_pos[tid] = q;
+      s_val[tid] = pm[q];
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int c = 0; c < kb; ++c) {
+        const int p = s_sw[c];
+        if (p == c) continue;
+        int a = -1, b = -1;  // first slots holding positions c and p (duplicates share values)
+        for (int t = 0; t < 2 * kb && (a < 0 || b < 0); ++t) {
+          if (a < 0 && s_pos[t] == c) a = t;
+          if (b < 0 && s_pos[t] == p) b = t;
+        }
+        const int tmp = s_val[a];
+        s_val[a] = s_val[b];
+        s_val[b] = tmp;
+        for (int t = a + 1; t < 2 * kb; ++t) if (s_pos[t] == c) s_val[t] = s_val[a];
+        for (int t = b + 1; t < 2 * kb; ++t) if (s_pos[t] == p) s_val[t] = s_val[b];
+      }
+    __syncthreads();
+    if (tid < 2 * kb) pm[s_pos[tid]] = s_val[tid];  // duplicates write the same value
+  }
   {
     const double s = logdet_sum<NT>(piv2, kb, flags);
     if (tid == 0) ld[b0 + mat] += s;
   }
 }
 
-// ---------------------------------------------------------------- diag block
-// The kb x kb pivot block M[K, K] in shared memory.  factor = 1: the block is strictly
-// diagonally dominant by columns (i w_n dominates the hopping), so partial pivoting would
-// keep the diagonal at every step: LU without interchanges, ln|u_kk| into ld[b].  factor = 0:
-// the block already holds L11\U11 from the pivoted panel.  Then, in place, inv(U11) and
-// inv(L11) (column-oriented triangular inversion), and out to Tinv:
-//   slot 0: T = inv(M_KK) = inv(U11) inv(L11)      slot 1: inv(L11)      (nb x nb, padded)
-template <typename S, typename C, int NT>
-__global__ void __launch_bounds__(NT) k_diag_inv(const S* M, int ldm, size_t mat_stride,
-                                                 size_t plane_stride, int k0, int kb, int nb,
-                                                 int b0, double* ld, cpx<C>* Tinv, int factor,
-                                                 int* flags) {
-  extern __shared__ unsigned char smem_raw[];
-  const int as = kb + 1;                            // odd row stride (bank-conflict free)
-  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x (kb+1)
-  cpx<C>* x = A + kb * as;                           // kb scratch column
-  const int mat = blockIdx.x, tid = threadIdx.x;
-  const S* re = M + mat * mat_stride;
-  const S* im = re + plane_stride;
-  for (int e = tid; e < kb * kb; e += NT) {
-    const int r = e / kb, c = e - r * kb;
-    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    A[r * as + c] = {(C)re[o], (C)im[o]};
-  }
-  __syncthreads();
-  if (factor) {
-    __shared__ double piv2[128];
-    for (int c = 0; c < kb; ++c) {
-      const cpx<C> d = A[c * as + c];
-      const C m2 = d.re * d.re + d.im * d.im;
-      const cpx<C> inv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
-      if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
-      for (int r = c + 1 + tid; r < kb; r += NT) A[r * as + c] = cmul(A[r * as + c], inv);
-      __syncthreads();
-      const int w = kb - c - 1;
-      for (int e = tid; e < w * w; e += NT) {
-        const int r = c + 1 + e / w, j = c + 1 + e % w;
-        const cpx<C> l = A[r * as + c], u = A[c * as + j];
-        A[r * as + j].re -= l.re * u.re - l.im * u.im;
-        A[r * as + j].im -= l.re * u.im + l.im * u.re;
-      }
-      __syncthreads();
-    }
-    const double s = logdet_sum<NT>(piv2, kb, flags);
-    if (tid == 0) ld[b0 + mat] += s;
-  }
-  // inv(U11) in place: column j gets inv(U[0:j,0:j]) * U[0:j, j] * (-1/u_jj).
-  for (int j = 0; j < kb; ++j) {
-    for (int i = tid; i < j; i += NT) x[i] = A[i * as + j];
-    __syncthreads();
-    const cpx<C> d = A[j * as + j];
-    const C m2 = d.re * d.re + d.im * d.im;
-    const cpx<C> dinv = {d.re / m2, -d.im / m2};
-    for (int i = tid; i < j; i += NT) {
-      cpx<C> s = {(C)0, (C)0};
-      for (int k = i; k < j; ++k) {
-        const cpx<C> t = cmul(A[i * as + k], x[k]);
-        s.re += t.re; s.im += t.im;
-      }
-      const cpx<C> q = cmul(s, dinv);
-      A[i * as + j] = {-q.re, -q.im};
-    }
-    __syncthreads();
-    if (tid == 0) A[j * as + j] = dinv;
-    __syncthreads();
-  }
-  // inv(L11) (unit lower) in place: column j gets -inv(L[j+1:, j+1:]) * L[j+1:, j].
-  for (int j = kb - 2; j >= 0; --j) {
-    for (int i = j + 1 + tid; i < kb; i += NT) x[i] = A[i * as + j];
-    __syncthreads();
-    for (int i = j + 1 + tid; i < kb; i += NT) {
-      cpx<C> s = x[i];
-      for (int k = j + 1; k < i; ++k) {
-        const cpx<C> t = cmul(A[i * as + k], x[k]);
-        s.re += t.re; s.im += t.im;
-      }
-      A[i * as + j] = {-s.re, -s.im};
-    }
-    __syncthreads();
-  }
-  // T = inv(U11) inv(L11): T_ij = sum_{k >= max(i,j)} Uinv_ik Linv_kj, Linv_jj = 1.
-  cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
-  cpx<C>* Li = T + (size_t)nb * nb;
-  for (int e = tid; e < nb * nb; e += NT) {
-    const int i = e / nb, j = e - i * nb;
-    cpx<C> t = {(C)0, (C)0}, l = {(C)0, (C)0};
-    if (i < kb && j < kb) {
-      if (i <= j) t = A[i * as + j];  // k = j term (unit diagonal of Linv)
-      for (int k = (i > j + 1 ? i : j + 1); k < kb; ++k) {
-        const cpx<C> p = cmul(A[i * as + k], A[k * as + j]);
-        t.re += p.re; t.im += p.im;
-      }
-      if (i > j) l = A[i * as + j];
-      else if (i == j) l = {(C)1, (C)0};
-    }
-    T[e] = t;
-    Li[e] = l;
-  }
-}
-
 // ------------------------------------------------------- dominant pivot block
-// T = inv(M_KK) for a strictly diagonally dominant pivot block (no interchanges needed, see
-// k_diag_inv) by in-place Gauss-Jordan, the block held in registers: thread (r0, j) owns
+// T = inv(M_KK) for a pivot block that needs no interchanges (a strictly column-diagonally
+// dominant block keeps its diagonal under partial pivoting, and the complex-symmetric
+// elimination takes none) by in-place Gauss-Jordan, the block held in registers: thread (r0, j) owns
 // column j, rows r0, r0 + RS, ... (RS = NT / kb row groups); each of the kb sweeps exchanges
 // only the pivot row and column through shared memory.  ld[b] += sum ln|pivot| (the pivots of
 // the LU).  Writes T to Tinv slot 0 (nb x nb, zero padded) and, if TT != null, the split planes
@@ -619,7 +550,7 @@ __global__ void __launch_bounds__(256)
   constexpr int NBMAX = sizeof(C) == 8 ? 64 : 128;
   constexpr int MAXC = NBMAX / 16;
   __shared__ C As[2][KC][BR + 1];
-  __shared__ cpx<C> Xs[2][KC][NBMAX];  // [0]: T chunk, [1]: inv(L11) chunk
+  __shared__ cpx<C> Xs[2][KC][NBMAX];  // [0]: T chunk, [1]: inv(L11) chunk (pivoted)
   const int mat = blockIdx.y;
   const int i0 = r_begin + blockIdx.x * BR;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -634,7 +565,7 @@ __global__ void __launch_bounds__(256)
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) { ar[a][q] = 0; ai[a][q] = 0; }
-  bool useL[4];
+  bool useL[4];  // pivoted rows below K: F_i = L_iK inv(L11)
 #pragma unroll
   for (int a = 0; a < 4; ++a) useL[a] = pivoted && (i0 + ty + 16 * a) >= kend;
   for (int kc = 0; kc < kb; kc += KC) {
@@ -698,6 +629,83 @@ __global__ void __launch_bounds__(256)
       store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split, false);
     }
   }
+}
+
+// Inverses of the pivoted group's pivot block from the packed LU of the outer panel (the
+// interchanges already moved the pivot rows into K, so M_KK = L_KK U_KK):
+//   Tinv slot 0: T = inv(M_KK) = inv(U_KK) inv(L_KK)        slot 1: inv(L_KK)
+// row by row, as solves from the right of unit rows e_r.  The packed kb x kb LU and the
+// reciprocals 1/u_jj are staged in shared memory once; 32 right-hand sides per CTA are then
+// solved column by column with one barrier per column (forward with U, the 1/u_jj applied
+// after the sweep, then backward with the unit-lower L).  Grid x: 2 ceil(kb/32) row groups
+// (rows of T, then rows of inv(L)).  Warp w owns the columns k = w (mod 8), so the L and U
+// entries of one step are the same for the whole warp (broadcast reads).
+template <typename S, typename C>
+__global__ void __launch_bounds__(256)
+    k_tinv_rows(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+                int nb, cpx<C>* Tinv) {
+  constexpr int R = 32;
+  extern __shared__ unsigned char smem_raw[];
+  const int xs = kb + 1;
+  cpx<C>* LU = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x (kb + 1)
+  cpx<C>* X = LU + (size_t)kb * xs;                  // R x (kb + 1)
+  cpx<C>* dinv = X + (size_t)R * xs;                 // kb
+  const int mat = blockIdx.y, tid = threadIdx.x;
+  const int groups = (kb + R - 1) / R;
+  const bool tpart = (int)blockIdx.x < groups;     // rows of T (else rows of inv(L))
+  const int row0 = (tpart ? blockIdx.x : blockIdx.x - groups) * R;
+  const S* re = M + mat * mat_stride + (size_t)k0 * ldm + k0;  // the packed pivot block
+  const S* im = re + plane_stride;
+  for (int e = tid; e < kb * kb; e += 256) {
+    const int a = e / kb, b = e - a * kb;
+    const size_t o = (size_t)a * ldm + b;
+    LU[a * xs + b] = {(C)re[o], (C)im[o]};
+  }
+  for (int e = tid; e < R * kb; e += 256) {
+    const int r = e / kb, cc = e - r * kb;
+    X[r * xs + cc] = {(C)((row0 + r == cc) ? 1 : 0), (C)0};
+  }
+  __syncthreads();
+  for (int k = tid; k < kb; k += 256) {
+    const cpx<C> d = LU[k * xs + k];
+    const C m2 = d.re * d.re + d.im * d.im;
+    dinv[k] = {d.re / m2, -d.im / m2};
+  }
+  __syncthreads();
+  const int r = tid & (R - 1), g = tid >> 5;
+  const bool live = row0 + r < kb;
+  cpx<C>* x = X + r * xs;
+  if (tpart) {
+    for (int j = 0; j < kb; ++j) {
+      if (live) {
+        const cpx<C> y = cmul(x[j], dinv[j]);
+        const cpx<C>* u = LU + j * xs;
+        for (int k = j + 1 + ((g - j - 1) & 7); k < kb; k += 8) {
+          x[k].re -= y.re * u[k].re - y.im * u[k].im;
+          x[k].im -= y.re * u[k].im + y.im * u[k].re;
+        }
+      }
+      __syncthreads();
+    }
+    if (live)
+      for (int k = g; k < kb; k += 8) x[k] = cmul(x[k], dinv[k]);
+    __syncthreads();
+  }
+  for (int j = kb - 1; j > 0; --j) {
+    if (live) {
+      const cpx<C> y = x[j];
+      const cpx<C>* l = LU + j * xs;
+      for (int k = g; k < j; k += 8) {
+        x[k].re -= y.re * l[k].re - y.im * l[k].im;
+        x[k].im -= y.re * l[k].im + y.im * l[k].re;
+      }
+    }
+    __syncthreads();
+  }
+  cpx<C>* out = Tinv + (size_t)mat * 2 * nb * nb + (tpart ? 0 : (size_t)nb * nb);
+  if (row0 + r < nb)
+    for (int cc = g; cc < nb; cc += 8)
+      out[(size_t)(row0 + r) * nb + cc] = (live && cc < kb) ? x[cc] : cpx<C>{(C)0, (C)0};
 }
 
 // W^T: 64 columns j x nb per CTA, transposed through shared memory.
@@ -1133,7 +1141,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       const int nbi = std::min(e.nb_piv, kb);
       for (int s0 = k0; s0 < kend; s0 += nbi) {
         const int kbi = std::min(nbi, kend - s0);
-        const size_t sm = sizeof(cpx<C>) * (size_t)(N - s0) * (kbi + 1);
+        const size_t sm = sizeof(cpx<C>) * (size_t)(N - s0) * (kbi + 1) + 5 * sizeof(int) * kbi;
         prof_begin(e, kPanel, s);
         k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
                                                       s0, kbi, b0, e.ld, piv, perm, e.flags);
@@ -1161,12 +1169,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       if (!want_grad && kend == N) break;
     }
     if (pivoted) {
-      const size_t sm = sizeof(cpx<C>) * ((size_t)kb * (kb + 1) + kb);
+      // T and inv(L_KK) of the factored pivot block, for F = M[:, K] T (inv(L_KK) below K)
+      const int groups = (kb + 31) / 32;
       prof_begin(e, kTrinv, s);
-      k_diag_inv<S, C, 512><<<cnt, 512, sm, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
-                                                  nb, b0, e.ld, Tinv, 0, e.flags);
+      const size_t smt = sizeof(cpx<C>) * ((size_t)(kb + 32) * (kb + 1) + kb);
+      k_tinv_rows<S, C><<<dim3(2 * groups, cnt), 256, smt, s>>>(M, e.ldm, e.mat_stride,
+                                                                e.plane_stride, k0, kb, nb, Tinv);
       prof_end(e, kTrinv, s);
-      SCA_LAUNCH_CHECK("diag");
+      SCA_LAUNCH_CHECK("pivot-block inverse");
     } else {
       prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
@@ -1277,12 +1287,16 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
     // While both groups run, the dominant group's persistent tensor-core launches leave
     // sm_reserve SMs to the pivoted group's kernels.
     e.tc_cap = 0;
+    const int span_p = np > 0 ? prof_span_begin(e, kSpanPiv, sp) : -1;
     if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
       return st;
+    prof_span_end(e, span_p, sp);
     if (fork && e.sm_reserve > 0 && e.tmap) e.tc_cap = tc_sms(e) - e.sm_reserve;
+    const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, s) : -1;
     st = nd > 0 ? run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s) : SCA_OK;
     e.tc_cap = 0;
     if (st != SCA_OK) return st;
+    prof_span_end(e, span_d, s);
     if (fork) {
       if (want_grad && refine_stage && !e.dos_mode) {  // each group refines its own blocks
         if ((st = launch_refine<S>(e, la, b0, 0, np, sp)) != SCA_OK) return st;
@@ -1326,8 +1340,8 @@ sca_status set_smem_limits() {
   if (done) return SCA_OK;
   cudaError_t err;
   if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
-  if ((err = allow_max_smem(k_diag_inv<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem diag");
   if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
+  if ((err = allow_max_smem(k_tinv_rows<S, C>)) != cudaSuccess) return cuda_fail(err, "smem tinv");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
   done = true;
   return SCA_OK;

@@ -84,6 +84,8 @@ enum KernelKind {
   kDiag,       // inverse of a dominant pivot block (Gauss-Jordan in registers)
   kUpdatePiv,  // rank-nb update of the pivoted group
   kFused,      // fused small-block Adam launch
+  kSpanPiv,    // wall span of the pivoted group on its stream (fork to its last kernel)
+  kSpanDom,    // wall span of the dominant group on the main stream (fork to its last kernel)
   kKinds
 };
 
@@ -100,6 +102,9 @@ struct Profiler {
 };
 void prof_begin(Engine& e, int kind, cudaStream_t s);
 void prof_end(Engine& e, int kind, cudaStream_t s);
+// A span that other records may nest in: begin returns its record (-1 when off).
+int prof_span_begin(Engine& e, int kind, cudaStream_t s);
+void prof_span_end(Engine& e, int rec, cudaStream_t s);
 void prof_collect(Engine& e);  // after a synchronisation: accumulate elapsed times
 void prof_free(Engine& e);
 
