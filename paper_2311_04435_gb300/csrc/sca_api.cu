@@ -23,7 +23,7 @@ thread_local std::string t_err;
 
 // SMs the dominant group's persistent tensor-core launches leave free while the pivoted
 // group runs beside them on its own (high-priority) stream.
-constexpr int kDefaultSmReserve = 16;
+constexpr int kDefaultSmReserve = 8;
 }
 
 void set_error(const std::string& msg) { t_err = msg; }
@@ -194,6 +194,9 @@ sca_status allocate(Engine& e) {
   }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming);
+  if (err == cudaSuccess && e.tc) err = cudaStreamCreateWithFlags(&e.aux, cudaStreamNonBlocking);
+  if (err == cudaSuccess && e.tc) err = cudaEventCreateWithFlags(&e.ev_aux0, cudaEventDisableTiming);
+  if (err == cudaSuccess && e.tc) err = cudaEventCreateWithFlags(&e.ev_aux1, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }
   return SCA_OK;
 }
@@ -275,8 +278,11 @@ void release(Engine& e) {
   if (e.side) { cudaStreamSynchronize(e.side); cudaStreamDestroy(e.side); }
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
-  e.side = nullptr;
-  e.ev_fork = e.ev_join = nullptr;
+  if (e.aux) { cudaStreamSynchronize(e.aux); cudaStreamDestroy(e.aux); }
+  if (e.ev_aux0) cudaEventDestroy(e.ev_aux0);
+  if (e.ev_aux1) cudaEventDestroy(e.ev_aux1);
+  e.side = e.aux = nullptr;
+  e.ev_fork = e.ev_join = e.ev_aux0 = e.ev_aux1 = nullptr;
   void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.piv, e.perm, e.flags, e.ld, e.d_z, e.tr, e.gd,
                   e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
   for (void* q : ptrs)

@@ -1168,6 +1168,25 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       }
       if (!want_grad && kend == N) break;
     }
+    const bool last_lu = !want_grad && kend == N;  // LU: nothing trails the last pivot block
+    bool w_aux = false;
+    if (sym && !last_lu && e.aux) {
+      // the W^T planes do not depend on the pivot-block inverse: build them on the auxiliary
+      // stream while the inverse runs (its second wave leaves SMs idle)
+      cudaError_t err = cudaEventRecord(e.ev_aux0, s);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(e.aux, e.ev_aux0, 0);
+      if (err != cudaSuccess) return cuda_fail(err, "aux fork");
+      const int cw = want_grad ? 0 : kend;
+      const size_t smw = 2 * sizeof(S) * (size_t)nb * 65;
+      prof_begin(e, kPrep, e.aux);
+      k_prep_w<S><<<dim3((N - cw + 63) / 64, cnt), 256, smw, e.aux>>>(
+          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, cw,
+          want_grad ? 1 : 0, split, 1);
+      prof_end(e, kPrep, e.aux);
+      SCA_LAUNCH_CHECK("prep w");
+      if ((err = cudaEventRecord(e.ev_aux1, e.aux)) != cudaSuccess) return cuda_fail(err, "aux join");
+      w_aux = true;
+    }
     if (pivoted) {
       // T and inv(L_KK) of the factored pivot block, for F = M[:, K] T (inv(L_KK) below K)
       const int groups = (kb + 31) / 32;
@@ -1186,17 +1205,24 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, kDiag, s);
       SCA_LAUNCH_CHECK("diag");
     }
-    if (!want_grad && kend == N) break;  // LU: nothing trails the last pivot block
+    if (last_lu) break;
     const int r0 = want_grad ? 0 : kend, c0 = want_grad ? 0 : kend;
     if (sym) {
       // W^T planes first: they are also the A operand of the prep product, since the swept
       // rows of M[:, K] are -W^T and the unswept ones +W^T (the sign rule above)
+      if (w_aux) {
+        cudaError_t err = cudaStreamWaitEvent(s, e.ev_aux1, 0);
+        if (err != cudaSuccess) return cuda_fail(err, "aux join");
+      } else {
+        const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
+        prof_begin(e, kPrep, s);
+        k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
+            want_grad ? 1 : 0, split, 1);
+        prof_end(e, kPrep, s);
+        SCA_LAUNCH_CHECK("prep w");
+      }
       prof_begin(e, kPrep, s);
-      const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
-      k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
-          M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
-          want_grad ? 1 : 0, split, 1);
-      SCA_LAUNCH_CHECK("prep w");
       sca_status st = tc_prep_split(e, m0, cnt, r0, k0, kb, want_grad, s);
       if (st != SCA_OK) return st;
       prof_end(e, kPrep, s);

@@ -67,6 +67,8 @@ struct Engine {
   struct Profiler* prof = nullptr;  // per-kernel event timing (sca_profile_enable)
   cudaStream_t side = nullptr;      // stream of the pivoted group (runs beside the rest)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t aux = nullptr;       // the dominant group's W planes beside its pivot-block inverse
+  cudaEvent_t ev_aux0 = nullptr, ev_aux1 = nullptr;
   int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
   int tc_next = 0;
   int tc_cap = 0;                   // CTA cap of the next tensor-core launches (0: one per SM)
