@@ -407,6 +407,211 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
   }
 }
 
+// Blocked form of k_diag_gj for float32 (same outputs).  The tableau stays in registers
+// (thread (rg, j) owns column j, rows rg + RS q) and is swept in 8 panels of 16 pivots.  Per
+// panel P: M[:, P] and W = M[P, :] (identity in the columns of P) go to shared memory; one
+// warp inverts the 16 x 16 pivot block M_PP by Gauss-Jordan (its pivots are those of the LU,
+// so ln|det| is the same); all threads form F = M[:, P] inv(M_PP) (rows of P: -inv(M_PP));
+// then each thread applies the rank-16 update M <- mask(M) - F W to the entries it owns
+// (mask: zero in the rows and the columns of P).  Four barriers per panel instead of one per
+// pivot, and the update is 32 FMAs per 8 broadcast loads.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t mat_stride,
+                                                 size_t plane_stride, int k0, int kb, int nb,
+                                                 int b0, double* ld, cpx<float>* Tinv,
+                                                 float* TT, int tt_bf16, int* flags) {
+  constexpr int KB = 128, PW = 16;
+  constexpr int RS = NT / KB;
+  constexpr int MAXR = (KB + RS - 1) / RS;
+  __shared__ cpx<float> Ms[KB][PW + 1];  // M[:, P], then F in place
+  __shared__ cpx<float> Ws[PW][KB];      // W = M[P, :]
+  __shared__ cpx<float> Tp[PW][PW + 1];  // inv(M_PP), in place
+  __shared__ double piv2[KB];
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const int j = tid % KB, rg = tid / KB;
+  const float* re = M + mat * mat_stride;
+  const float* im = re + plane_stride;
+  cpx<float> a[MAXR];
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) {
+    const int r = rg + q * RS;
+    if (r < kb && j < kb) {
+      const size_t o = (size_t)(k0 + r) * ldm + k0 + j;
+      a[q] = {re[o], im[o]};
+    } else {
+      a[q] = {(r == j) ? 1.f : 0.f, 0.f};
+    }
+  }
+  for (int p0 = 0; p0 < KB; p0 += PW) {
+    const bool jP = (unsigned)(j - p0) < (unsigned)PW;
+    // (a) the panel's columns and rows
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int r = rg + q * RS;
+      if (q == MAXR - 1 && r >= KB) break;
+      if (jP) Ms[r][j - p0] = a[q];
+      if ((unsigned)(r - p0) < (unsigned)PW)
+        Ws[r - p0][j] = jP ? cpx<float>{(j == r) ? 1.f : 0.f, 0.f} : a[q];
+    }
+    __syncthreads();
+    // (b) one warp: inv(M_PP) by Gauss-Jordan; lane owns column lane % 16, rows lane / 16 + 2m
+    if (tid < 32) {
+      const int cl = tid & 15, r0 = tid >> 4;
+      for (int m = 0; m < 8; ++m) Tp[r0 + 2 * m][cl] = Ms[p0 + r0 + 2 * m][cl];
+      __syncwarp();
+      for (int cc = 0; cc < PW; ++cc) {
+        const cpx<float> d = Tp[cc][cc];
+        const float m2 = d.re * d.re + d.im * d.im;
+        const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
+        const cpx<float> dinv = {d.re * rm, -d.im * rm};
+        if (tid == 0) piv2[p0 + cc] = (double)d.re * d.re + (double)d.im * d.im;
+        const cpx<float> pr = Tp[cc][cl];  // pivot row, this lane's column
+        cpx<float> nv[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int r = r0 + 2 * m;
+          const cpx<float> pc = Tp[r][cc];  // pivot column, this row
+          const cpx<float> t = Tp[r][cl];
+          if (r == cc) {
+            nv[m] = (cl == cc) ? dinv : cmul(t, dinv);
+          } else if (cl == cc) {
+            const cpx<float> q2 = cmul(pc, dinv);
+            nv[m] = {-q2.re, -q2.im};
+          } else {
+            const cpx<float> u = cmul(pr, dinv);
+            nv[m] = {t.re - (pc.re * u.re - pc.im * u.im), t.im - (pc.re * u.im + pc.im * u.re)};
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) Tp[r0 + 2 * m][cl] = nv[m];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (c) F = M[:, P] inv(M_PP) (rows of P: -inv(M_PP)), in place of M[:, P]: four threads
+    // per row, 4 columns each, all reads before the barrier
+    {
+      constexpr int FC = 4;
+      const bool act = tid < (PW / FC) * KB;
+      const int r = tid / (PW / FC), kh = (tid % (PW / FC)) * FC;
+      cpx<float> f[FC];
+      if (act) {
+        if ((unsigned)(r - p0) < (unsigned)PW) {
+#pragma unroll
+          for (int k = 0; k < FC; ++k) {
+            const cpx<float> t = Tp[r - p0][kh + k];
+            f[k] = {-t.re, -t.im};
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < FC; ++k) f[k] = {0.f, 0.f};
+#pragma unroll
+          for (int m = 0; m < PW; ++m) {
+            const cpx<float> x = Ms[r][m];
+#pragma unroll
+            for (int k = 0; k < FC; ++k) {
+              const cpx<float> t = Tp[m][kh + k];
+              f[k].re += x.re * t.re - x.im * t.im;
+              f[k].im += x.re * t.im + x.im * t.re;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int k = 0; k < FC; ++k) Ms[r][kh + k] = f[k];
+      }
+    }
+    __syncthreads();
+    // (d) M <- mask(M) - F W on the owned entries
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int r = rg + q * RS;
+      if (jP || (unsigned)(r - p0) < (unsigned)PW) a[q] = {0.f, 0.f};
+    }
+#pragma unroll 2
+    for (int k = 0; k < PW; ++k) {
+      const cpx<float> w = Ws[k][j];
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) {  // independent chains: the loads run ahead
+        const int r = rg + q * RS;
+        if (q == MAXR - 1 && r >= KB) break;
+        const cpx<float> f = Ms[r][k];
+        a[q].re -= f.re * w.re - f.im * w.im;
+        a[q].im -= f.re * w.im + f.im * w.re;
+      }
+    }
+    __syncthreads();
+  }
+  {
+    const double s = logdet_sum<NT>(piv2, kb, flags);  // padded pivots are 1
+    if (tid == 0) ld[b0 + mat] += s;
+  }
+  cpx<float>* T = Tinv + (size_t)mat * 2 * nb * nb;
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) {
+    const int r = rg + q * RS;
+    if (r >= nb || j >= nb) continue;
+    T[(size_t)r * nb + j] = (r < kb && j < kb) ? a[q] : cpx<float>{0.f, 0.f};
+  }
+  if (!TT) return;
+  // W_T[j][r] = -T[r][j] in split planes, 16 rows j at a time through shared memory (the
+  // owners of columns j deposit them, then every thread writes 4 consecutive r of one row)
+  const size_t P = (size_t)nb * nb;
+  float* tt = TT + (size_t)mat * 6 * P;
+  cpx<float>(*S)[KB] = Ws;  // [16][KB]
+  for (int jc0 = 0; jc0 < nb; jc0 += PW) {
+    if ((unsigned)(j - jc0) < (unsigned)PW) {
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) {
+        const int r = rg + q * RS;
+        if (q == MAXR - 1 && r >= KB) break;
+        S[j - jc0][r] = (r < kb && j < kb) ? a[q] : cpx<float>{0.f, 0.f};
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < PW * (KB / 4); e += NT) {
+      const int jj = e / (KB / 4), r4 = (e - jj * (KB / 4)) * 4;
+      const int jr = jc0 + jj;
+      if (jr >= nb || r4 >= nb) continue;
+      float fr[4], fi[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { fr[t] = -S[jj][r4 + t].re; fi[t] = -S[jj][r4 + t].im; }
+      const size_t o = (size_t)jr * nb + r4;
+      if (tt_bf16) {
+        __nv_bfloat16 h[6][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          h[0][t] = __float2bfloat16_rn(fr[t]);
+          h[1][t] = __float2bfloat16_rn(fi[t]);
+          h[2][t] = __float2bfloat16_rn(fr[t] - __bfloat162float(h[0][t]));
+          h[3][t] = __float2bfloat16_rn(fi[t] - __bfloat162float(h[1][t]));
+          h[4][t] = __hneg(h[1][t]);
+          h[5][t] = __hneg(h[3][t]);
+        }
+#pragma unroll
+        for (int pl = 0; pl < 6; ++pl)
+          *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(tt + pl * P) + o) =
+              *reinterpret_cast<const uint2*>(h[pl]);
+      } else {
+        float4 v[6];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float hr = __uint_as_float(__float_as_uint(fr[t]) & 0xffffe000u);
+          const float hi = __uint_as_float(__float_as_uint(fi[t]) & 0xffffe000u);
+          (&v[0].x)[t] = hr; (&v[1].x)[t] = hi; (&v[2].x)[t] = fr[t] - hr;
+          (&v[3].x)[t] = fi[t] - hi; (&v[4].x)[t] = -hi; (&v[5].x)[t] = -(fi[t] - hi);
+        }
+#pragma unroll
+        for (int pl = 0; pl < 6; ++pl) *reinterpret_cast<float4*>(tt + pl * P + o) = v[pl];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Split copy of the pivot columns for the tensor-core product F = M[:, K] T:
 // Fs[i][k] = split(M[i][k0 + k]) (planes re_hi, im_hi, re_lo, im_lo; N x nb, zero for k >= kb).
 template <typename S>
@@ -1199,9 +1404,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     } else {
       prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
-      k_diag_gj<S, C, 768><<<cnt, 768, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
-                                                kb, nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0,
-                                                e.flags);
+      if constexpr (sizeof(C) == 4) {
+        k_diag_gjb<512><<<cnt, 512, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb,
+                                            b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags);
+      } else {
+        k_diag_gj<S, C, 768><<<cnt, 768, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
+                                                  kb, nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0,
+                                                  e.flags);
+      }
       prof_end(e, kDiag, s);
       SCA_LAUNCH_CHECK("diag");
     }
