@@ -69,41 +69,7 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
 // Two-level blocking of the pivoted group: an outer panel of width kbo is factorised by
 // shared-memory sub-panels of width kbi; after each sub-panel [s0, s0+kbi) the rest of the outer
 // panel (columns [s0+kbi, c_end)) is brought up to date as in a right-looking LU:
-//   U12 = inv(L11) A12  (rows [s0, s0+kbi))       then    A22 -= L21 U12  (rows >= s0+kbi).
-// k_trsm_u12: one CTA per block, one thread per column of A12 (forward substitution with the
-// unit-lower L11 held in shared memory), U12 written in place.
-template <typename S, typename C>
-__global__ void k_trsm_u12(S* M, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
-                           int c_end) {
-  __shared__ cpx<C> Ls[16][17];
-  const int mat = blockIdx.x;
-  S* re = M + mat * mat_stride;
-  S* im = re + plane_stride;
-  for (int e = threadIdx.x; e < kbi * kbi; e += blockDim.x) {
-    const int r = e / kbi, c = e - r * kbi;
-    const size_t o = (size_t)(s0 + r) * ldm + s0 + c;
-    Ls[r][c] = {(C)re[o], (C)im[o]};
-  }
-  __syncthreads();
-  const int nc = c_end - (s0 + kbi);
-  for (int cc = threadIdx.x; cc < nc; cc += blockDim.x) {
-    const int col = s0 + kbi + cc;
-    cpx<C> u[16];
-    for (int r = 0; r < kbi; ++r) {
-      const size_t o = (size_t)(s0 + r) * ldm + col;
-      cpx<C> s = {(C)re[o], (C)im[o]};
-      for (int k = 0; k < r; ++k) {
-        const cpx<C> t = cmul(Ls[r][k], u[k]);
-        s.re -= t.re;
-        s.im -= t.im;
-      }
-      u[r] = s;
-      re[o] = (S)s.re;
-      im[o] = (S)s.im;
-    }
-  }
-}
-
+//   U12 = inv(L11) A12  (rows [s0, s0+kbi), k_swap_trsm)   then   A22 -= L21 U12  (rows >= s0+kbi).
 // k_gemm_panel: A22[r][c] -= sum_k L21[r][k] U12[k][c] for rows r >= s0+kbi (64 per CTA),
 // columns [s0+kbi, c_end), K = kbi <= 16; U12 staged in shared memory.
 template <typename S, typename C>
@@ -146,28 +112,61 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// ---------------------------------------------------------------------- swap
-// Applies the panel's interchanges, in order, to the columns outside the panel
-// (columns >= jstart only).
-template <typename S>
-__global__ void k_swap(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0,
-                       int kb, int jstart, const int* piv) {
+// ------------------------------------------------------------ swap + trsm
+// After a pivoted sub-panel [s0, s0+kbi): each thread takes one column j >= jstart outside the
+// sub-panel, applies the sub-panel's interchanges to it in order and, for the columns of the
+// outer panel still to be factored ([s0+kbi, c_end)), the forward substitution with the
+// unit-lower L11 of the sub-panel (U12 = inv(L11) A12), in place.  A sub-panel as wide as its
+// outer panel (up to 128 columns) leaves no such columns; narrower ones are at most 16 wide.
+template <typename S, typename C>
+__global__ void __launch_bounds__(128)
+    k_swap_trsm(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
+                int jstart, int c_end, const int* piv) {
+  constexpr int KMAX = 128;  // widest sub-panel
+  constexpr int TMAX = 16;   // widest sub-panel that leaves outer-panel columns behind
+  __shared__ cpx<C> Ls[TMAX][TMAX + 1];
+  __shared__ int sp[KMAX];
   const int mat = blockIdx.y;
-  __shared__ int sp[256];
-  for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[c] = piv[(size_t)mat * N + k0 + c];
-  __syncthreads();
-  const int j = jstart + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N || (j >= k0 && j < k0 + kb)) return;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
-  for (int c = 0; c < kb; ++c) {
-    const int p = sp[c];
-    if (p != k0 + c) {
-      const size_t a = (size_t)(k0 + c) * ldm + j, q = (size_t)p * ldm + j;
-      const S tr = re[a], ti = im[a];
-      re[a] = re[q]; im[a] = im[q];
-      re[q] = tr; im[q] = ti;
+  const bool tr = c_end > s0 + kbi && kbi <= TMAX;  // the host never asks otherwise
+  if (tr)
+    for (int e = threadIdx.x; e < kbi * kbi; e += blockDim.x) {
+      const int r = e / kbi, cc = e - r * kbi;
+      const size_t o = (size_t)(s0 + r) * ldm + s0 + cc;
+      Ls[r][cc] = {(C)re[o], (C)im[o]};
     }
+  for (int t = threadIdx.x; t < kbi && t < KMAX; t += blockDim.x)
+    sp[t] = piv[(size_t)mat * N + s0 + t];
+  __syncthreads();
+  const int j = jstart + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N || (j >= s0 && j < s0 + kbi)) return;
+  for (int cc = 0; cc < kbi && cc < KMAX; ++cc) {
+    const int p = sp[cc];
+    if (p != s0 + cc) {
+      const size_t a = (size_t)(s0 + cc) * ldm + j, q = (size_t)p * ldm + j;
+      const S xr = re[a], xi = im[a];
+      re[a] = re[q]; im[a] = im[q];
+      re[q] = xr; im[q] = xi;
+    }
+  }
+  if (!tr || j < s0 + kbi || j >= c_end) return;
+  cpx<C> u[TMAX];
+#pragma unroll
+  for (int r = 0; r < TMAX; ++r) {
+    if (r >= kbi) break;
+    const size_t o = (size_t)(s0 + r) * ldm + j;
+    cpx<C> acc = {(C)re[o], (C)im[o]};
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) {
+      if (k >= r) break;
+      const cpx<C> t = cmul(Ls[r][k], u[k]);
+      acc.re -= t.re;
+      acc.im -= t.im;
+    }
+    u[r] = acc;
+    re[o] = (S)acc.re;
+    im[o] = (S)acc.im;
   }
 }
 
@@ -1355,16 +1354,18 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
         if (!want_grad && s0 + kbi == N) break;
         const int jstart = want_grad ? 0 : k0;
         const int ncols = N - jstart;
+        // interchanges on the other columns, then U12 for the rest of the outer panel
+        if (s0 + kbi < kend && kbi > 16) {
+          set_error("pivoted sub-panel wider than 16 inside an outer panel");
+          return SCA_EINVAL;
+        }
         prof_begin(e, kSwap, s);
-        k_swap<S><<<dim3((ncols + 255) / 256, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
-                                                                   e.plane_stride, s0, kbi, jstart,
-                                                                   piv);
+        k_swap_trsm<S, C><<<dim3((ncols + 127) / 128, cnt), 128, 0, s>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, jstart, kend, piv);
         prof_end(e, kSwap, s);
         SCA_LAUNCH_CHECK("swap");
         if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
           prof_begin(e, kTrinv, s);
-          k_trsm_u12<S, C><<<cnt, 128, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, s0, kbi,
-                                                kend);
           k_gemm_panel<S, C><<<dim3((N - s0 - kbi + 63) / 64, cnt), 256, 0, s>>>(
               M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, kend);
           prof_end(e, kTrinv, s);
