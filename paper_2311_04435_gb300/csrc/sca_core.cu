@@ -40,8 +40,10 @@ constexpr size_t kRefineSmem = 208 * 1024;
 // row, one thread per row.
 template <typename S>
 __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
-                           Lattice la, double* ld, int* perm) {
-  const int mat = blockIdx.y, b = b0 + mat, n = b >> 1, sg = (b & 1) ? -1 : 1;
+                           Lattice la0, double* ld, int* perm) {
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
   const int N = la.N, L = la.L;
   const double w = la.zshift ? la.zshift[2 * n + 1] : (2.0 * n + 1.0) * kPi * la.T;
   const double zr = la.zshift ? la.zshift[2 * n] : la.mu;
@@ -1046,10 +1048,12 @@ __global__ void __launch_bounds__(256)
 // memory, a_j cached per CTA as a double-float pair.
 template <typename S>
 __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
-                         Lattice la, const int* perm, double* gd, int refine) {
+                         Lattice la0, const int* perm, double* gd, int refine) {
   extern __shared__ unsigned char smem_raw[];
-  const int N = la.N, L = la.L;
-  const int mat = blockIdx.y, b = b0 + mat, n = b >> 1, sg = (b & 1) ? -1 : 1;
+  const int N = la0.N, L = la0.L;
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int* sperm = reinterpret_cast<int*>(smem_raw);
   const S* re = M + mat * mat_stride;
@@ -1111,11 +1115,13 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
 constexpr int kRefineRowsPerCta = 32;
 __global__ void __launch_bounds__(256)
     k_refine_direct(const float* __restrict__ M, int ldm, size_t mat_stride, size_t plane_stride,
-                    int b0, Lattice la, double* __restrict__ gd) {
+                    int b0, Lattice la0, double* __restrict__ gd) {
   extern __shared__ unsigned char smem_raw[];
   dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
-  const int N = la.N, L = la.L;
-  const int mat = blockIdx.y, b = b0 + mat, n = b >> 1, sg = (b & 1) ? -1 : 1;
+  const int N = la0.N, L = la0.L;
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = ds_of(la.mu - site_energy(la, r, sg));
   __syncthreads();
@@ -1183,12 +1189,13 @@ __global__ void __launch_bounds__(256)
 // tree reductions, so the result does not depend on what else runs on the device.
 // status: [0] Omega [1] max|g| [2] |mean s_i phi_i| [3] mean |phi_i| [4] nonfinite flag
 // (all at the phi the gradient was taken at) [5] number of updates applied (accumulates).
+// slots (optional): the workspace slot of each of the B blocks, in block order.
 constexpr int RT = 1024;
-__global__ void __launch_bounds__(RT)
-    k_reduce(int N, int L, int B, const double* ld, const double* gd, const double* phi,
-             double* phi_out, double* m, double* v, double* g_out, double* omega_out,
-             double* status, const int* flags, double U, double T, int want_grad, int do_adam,
-             double step, double sbc2, double beta1, double beta2, double eps, double grad_tol) {
+__device__ __forceinline__ void reduce_body(
+    int N, int L, int B, const int* slots, const double* ld, const double* gd,
+    const double* phi, double* phi_out, double* m, double* v, double* g_out, double* omega_out,
+    double* status, const int* flags, double U, double T, int want_grad, int do_adam,
+    double step, double sbc2, double beta1, double beta2, double eps, double grad_tol) {
   __shared__ double s_q[RT], s_gm[RT], s_st[RT], s_ab[RT];
   __shared__ int s_bad;
   const int tid = threadIdx.x;
@@ -1203,7 +1210,7 @@ __global__ void __launch_bounds__(RT)
     ab += fabs(ph);
     if (want_grad) {
       double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += gd[(size_t)b * N + i];
+      for (int b = 0; b < B; ++b) acc += gd[(size_t)(slots ? slots[b] : b) * N + i];
       const double g = 2.0 * ph / U - 2.0 * T * acc;
       if (!isfinite(g)) bad = true;
       gm = fmax(gm, fabs(g));
@@ -1225,7 +1232,7 @@ __global__ void __launch_bounds__(RT)
   __shared__ double s_om;
   if (tid == 0) {
     double sld = 0.0;
-    for (int b = 0; b < B; ++b) sld += ld[b];
+    for (int b = 0; b < B; ++b) sld += ld[slots ? slots[b] : b];
     s_om = s_q[0] / U - 2.0 * T * sld;
   }
   __syncthreads();
@@ -1254,6 +1261,26 @@ __global__ void __launch_bounds__(RT)
   }
 }
 
+__global__ void __launch_bounds__(RT)
+    k_reduce(int N, int L, int B, const double* ld, const double* gd, const double* phi,
+             double* phi_out, double* m, double* v, double* g_out, double* omega_out,
+             double* status, const int* flags, double U, double T, int want_grad, int do_adam,
+             double step, double sbc2, double beta1, double beta2, double eps, double grad_tol) {
+  reduce_body(N, L, B, nullptr, ld, gd, phi, phi_out, m, v, g_out, omega_out, status, flags, U,
+              T, want_grad, do_adam, step, sbc2, beta1, beta2, eps, grad_tol);
+}
+
+// One CTA per request of a shared pass: its Omega, gradient and gated Adam update from its
+// own blocks (slots in block order), exactly as a pass of its own would compute them.
+__global__ void __launch_bounds__(RT) k_reduce_batch(int N, int L, const ReqDesc* rq,
+                                                     const double* ld, const double* gd,
+                                                     const int* flags) {
+  const ReqDesc r = rq[blockIdx.x];
+  reduce_body(N, L, r.nblocks, r.slots, ld, gd, r.phi, r.phi, r.m, r.v, r.g, nullptr, r.status,
+              flags, r.U, r.T, 1, r.do_adam, r.adam.lr_over_bc1, r.adam.sqrt_bc2, r.adam.beta1,
+              r.adam.beta2, r.adam.eps, r.adam.grad_tol);
+}
+
 __global__ void k_seed_phi(double* phi, int N, unsigned long long seed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -1269,6 +1296,7 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
   la.L = e.L; la.N = e.N; la.t = e.p.t; la.delta_eff = e.delta_eff; la.mu = e.p.mu; la.T = e.p.T;
   la.phi = d_phi; la.eps_extra = e.eps_extra;
   la.zshift = e.dos_mode ? e.d_z : nullptr;
+  la.bd = e.bd;
   return la;
 }
 
@@ -1635,6 +1663,14 @@ sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d
                             adam ? adam->grad_tol : 0.0);
   prof_end(e, kReduce, s);
   SCA_LAUNCH_CHECK("reduce");
+  return SCA_OK;
+}
+
+sca_status run_reduce_batch(Engine& e, const ReqDesc* rq, int nreq, cudaStream_t s) {
+  prof_begin(e, kReduce, s);
+  k_reduce_batch<<<nreq, RT, 0, s>>>(e.N, e.L, rq, e.ld, e.gd, e.flags);
+  prof_end(e, kReduce, s);
+  SCA_LAUNCH_CHECK("reduce batch");
   return SCA_OK;
 }
 

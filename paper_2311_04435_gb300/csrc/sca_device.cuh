@@ -17,13 +17,39 @@ __device__ __forceinline__ cpx<C> cmul(cpx<C> a, cpx<C> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 
+// Physics of one block slot when several requests share a pass (size-bucket batching):
+// block (n, sg) of a request with its own field, site energies, t, Delta_eff, mu and T.
+struct BlockDesc {
+  const double* phi;
+  const double* eps_extra;
+  double t, delta_eff, mu, T;
+  int n, sg;
+};
+
 struct Lattice {
   int L, N;
   double t, delta_eff, mu, T;
   const double* phi;
   const double* eps_extra;
   const double* zshift;  // null: z_n = mu + i omega_n; else z_n = zshift[2n] + i zshift[2n+1]
+  const BlockDesc* bd;   // null: slot b is block (b >> 1, sigma = b & 1 ? -1 : +1) of one set
 };
+
+// The lattice of slot b and its frequency index n and spin sg.
+__device__ __forceinline__ Lattice block_lattice(const Lattice& la, int b, int& n, int& sg) {
+  if (!la.bd) {
+    n = b >> 1;
+    sg = (b & 1) ? -1 : 1;
+    return la;
+  }
+  const BlockDesc d = la.bd[b];
+  Lattice l = la;
+  l.t = d.t; l.delta_eff = d.delta_eff; l.mu = d.mu; l.T = d.T;
+  l.phi = d.phi; l.eps_extra = d.eps_extra;
+  n = d.n;
+  sg = d.sg;
+  return l;
+}
 
 __device__ __forceinline__ double site_energy(const Lattice& la, int i, int sg) {
   const int x = i / la.L, y = i - x * la.L;

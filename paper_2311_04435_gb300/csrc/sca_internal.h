@@ -20,6 +20,23 @@ extern std::atomic<uint64_t> g_launches;
 void set_error(const std::string& msg);
 sca_status cuda_fail(cudaError_t e, const char* where);
 
+// Arguments of one Adam update (PyTorch's order and bias corrections).
+struct AdamStep {
+  double lr_over_bc1, sqrt_bc2, beta1, beta2, eps, grad_tol;
+};
+
+struct BlockDesc;  // per-slot physics (sca_device.cuh)
+
+// One request of a shared pass (size-bucket batching): its device state and blocks.
+struct ReqDesc {
+  double *phi, *m, *v, *g, *status;  // N, N, N, N, 8
+  const int* slots;                  // nblocks workspace slots, in block order
+  int nblocks;
+  int do_adam;                       // 0: Omega and gradient only
+  double U, T;
+  AdamStep adam;
+};
+
 // Device buffers and sizes of one parameter set.  Blocks are stored planar:
 // for block m of a chunk, the real plane is M + m*mat_stride and the
 // imaginary plane follows at + plane_stride; rows have `ldm` elements.
@@ -53,6 +70,7 @@ struct Engine {
   double* tr = nullptr;     // B: Im Tr G per block (DOS)
   bool nopiv = false;       // SCA_PIVOT_NONE: no block is pivoted
   bool dos_mode = false;    // blocks use the shifts d_z and end in a trace, not a refine
+  const BlockDesc* bd = nullptr;  // per-slot physics of a shared pass (or null)
   double* gd = nullptr;     // B x N
   double* eps_extra = nullptr;  // N or null
   double* d_phi = nullptr;  // N (Adam state)
@@ -128,9 +146,7 @@ sca_status run_refine_resident(Engine& e, const double* d_phi, cudaStream_t s);
 // Enqueue the reduction of ld / gd into Omega (d_omega) and the gradient
 // (d_grad, may be null).  With adam != null also the Adam update of e.d_phi
 // (step index `step` >= 1).  Writes status[0..7].
-struct AdamStep {
-  double lr_over_bc1, sqrt_bc2, beta1, beta2, eps, grad_tol;
-};
+
 sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d_grad,
                       const AdamStep* adam, cudaStream_t s);
 
@@ -146,6 +162,9 @@ sca_status run_fused_adam(Engine& e, int nsteps, const AdamStep* steps, bool do_
 
 // Seeded start field on the device.
 sca_status run_seed_phi(double* d_phi, int N, uint64_t seed, cudaStream_t s);
+// One reduction CTA per request of a shared pass (device table rq of nreq entries).
+sca_status run_reduce_batch(Engine& e, const ReqDesc* rq, int nreq, cudaStream_t s);
+AdamStep adam_step_args(const sca_adam& a, int32_t step);
 
 // tcgen05 3xTF32 rank-nb update (sca_tc.cu).
 bool tc_supported();
@@ -162,6 +181,30 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
 sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
                          cudaStream_t s);
 
+
+// ----------------------------------------------------------- size buckets
+// One request served through a size bucket: its parameters, Adam settings and device state
+// (phi | m | v | g, N doubles each, then 8 status doubles as in the single-request path).
+struct BucketReq {
+  sca_params p{};
+  sca_adam a{};
+  int32_t step = 0;
+  int nb = 0, npiv = 0;
+  double delta_eff = 0.0;
+  double* d = nullptr;
+};
+struct Bucket;
+bool bucketed(const sca_params& p);               // served through a size bucket
+sca_params bucket_shape(int32_t L, int32_t prec, int cap);
+sca_status bucket_create(int32_t L, int32_t prec, int cap, Bucket** out);
+void bucket_destroy(Bucket* b);
+cudaStream_t bucket_stream(Bucket* b);
+sca_status bucket_req_init(Bucket* b, BucketReq* r, const sca_params& p, const sca_adam& a);
+void bucket_req_release(BucketReq* r);
+// nsteps gated Adam steps (adam) or one evaluation without update (!adam) for n requests.
+sca_status bucket_run(Bucket* b, BucketReq* const* reqs, int n, int nsteps, bool adam);
+sca_status bucket_status(Bucket* b, BucketReq* const* reqs, int n, double* out);
+sca_status bucket_get_phi(Bucket* b, const BucketReq* r, double* out);
 }  // namespace sca
 
 struct sca_ctx {

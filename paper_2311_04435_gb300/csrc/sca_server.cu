@@ -2,22 +2,27 @@
 // n_omega) under an HBM admission budget.
 //
 // One worker thread owns every device object.  Each round it
-//   1. admits queued requests in arrival order while a slot is free and the request's
-//      workspace fits the remaining budget (each admitted request gets its own context,
-//      stream and SplitMix64 start field; phi, m and v stay resident on the device),
-//   2. enqueues a batch of gated Adam iterations for every request in flight, each on its
-//      own stream, so the requests' kernels overlap on the device,
-//   3. synchronises each request's stream in turn and retires the ones that converged
-//      (max|g| < grad_tol: the device stops applying updates) or reached max_steps,
-//      releasing their slot and budget for the next admission.
-// A request's arithmetic depends only on its own context, so its result is the same alone
-// and in any mix.  submit / poll / times only touch the bookkeeping under a mutex.
+//   1. admits queued requests in arrival order while a slot is free and the request's memory
+//      fits the remaining budget.  Small requests (blocks that the fused kernel holds) get a
+//      context and stream of their own; larger ones join the size bucket of their lattice
+//      size and precision (one shared workspace of kBucketSlots block slots, created with the
+//      bucket's first request and counted against the budget until its last one leaves), and
+//      only their field, Adam moments and status are their own;
+//   2. enqueues a batch of gated Adam iterations for every request in flight: one launch
+//      sequence per small request, on its own stream, and per bucket one launch sequence for
+//      all its requests (in passes of at most kBucketSlots blocks);
+//   3. synchronises and retires the requests that converged (max|g| < grad_tol: the device
+//      stops applying updates) or reached max_steps, releasing their slot and budget.
+// A request's arithmetic does not depend on what it shares a bucket or the device with, so its
+// result is the same alone and in any mix.  submit / poll / times only touch the bookkeeping
+// under a mutex.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -29,7 +34,22 @@
 
 namespace {
 
-constexpr int32_t kRoundSteps = 8;  // Adam iterations enqueued per request per round
+constexpr int32_t kRoundSteps = 8;     // Adam iterations enqueued per request per round
+constexpr int kBucketSlots = 256;      // block slots of a size bucket's workspace
+
+uint64_t bucket_bytes(int32_t L, int32_t prec, int cap) {
+  const sca_params s = sca::bucket_shape(L, prec, cap);
+  uint64_t b = 0;
+  return sca_workspace_bytes(&s, &b) == SCA_OK ? b : ~0ull;
+}
+
+// Slots of a new bucket: kBucketSlots, or fewer (a power of two no smaller than the request's
+// blocks) where the remaining budget is short; 0 if even that does not fit.
+int bucket_cap(int32_t L, int32_t prec, int need, uint64_t room) {
+  for (int cap = kBucketSlots; cap >= need; cap /= 2)
+    if (bucket_bytes(L, prec, cap) <= room) return cap;
+  return (bucket_bytes(L, prec, need) <= room) ? need : 0;
+}
 
 struct Request {
   uint64_t id = 0;
@@ -40,6 +60,8 @@ struct Request {
   sca_status status = SCA_EPENDING;
   double t_submit = -1, t_admit = -1, t_start = -1, t_finish = -1;
   sca_ctx* ctx = nullptr;
+  bool in_bucket = false;   // served through the size bucket of (L, prec)
+  sca::BucketReq br;
   int32_t launched = 0;
   std::vector<double> phi;
   double omega = 0, gmax = 0;
@@ -48,6 +70,13 @@ struct Request {
 };
 
 }  // namespace
+
+struct BucketSlot {
+  sca::Bucket* b = nullptr;  // null until created by the worker
+  int cap = 0;
+  uint64_t bytes = 0;        // its workspace, counted in `used`
+  int members = 0;           // admitted requests not yet finished
+};
 
 struct sca_server {
   uint64_t budget = 0;
@@ -59,6 +88,7 @@ struct sca_server {
   std::deque<Request*> queue;
   std::vector<Request*> active;  // worker-owned
   std::unordered_map<uint64_t, Request*> all;
+  std::map<std::pair<int32_t, int32_t>, BucketSlot> buckets;  // (L, prec); under the mutex
   uint64_t next_id = 1;
   bool stop = false;
   std::thread worker;
@@ -69,6 +99,7 @@ struct sca_server {
   }
   void run();
   void finish(Request* r, sca_status st);
+  void run_buckets(std::vector<Request*>& active, std::vector<Request*>& still);
 };
 
 void sca_server::finish(Request* r, sca_status st) {
@@ -77,11 +108,114 @@ void sca_server::finish(Request* r, sca_status st) {
     sca_destroy(r->ctx);
     r->ctx = nullptr;
   }
-  std::lock_guard<std::mutex> lock(mu);
-  r->status = st;
-  r->state = 2;
-  r->t_finish = now();
-  used -= r->bytes;
+  sca::Bucket* gone = nullptr;
+  if (r->in_bucket) sca::bucket_req_release(&r->br);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    r->status = st;
+    r->state = 2;
+    r->t_finish = now();
+    used -= r->bytes;
+    if (r->in_bucket) {
+      auto it = buckets.find({r->p.L, r->p.prec});
+      if (it != buckets.end() && --it->second.members == 0) {  // the last one leaves
+        gone = it->second.b;
+        used -= it->second.bytes;
+        buckets.erase(it);
+      }
+    }
+  }
+  if (gone) sca::bucket_destroy(gone);
+}
+
+// One round of every size bucket: a batch of gated steps for its requests (as many as the
+// closest to its max_steps may still take), then retirement as in the single-request path:
+// converged requests report the status of their last step, the others one more evaluation.
+void sca_server::run_buckets(std::vector<Request*>& active, std::vector<Request*>& still) {
+  std::map<std::pair<int32_t, int32_t>, std::vector<Request*>> groups;
+  for (Request* r : active)
+    if (r->in_bucket) groups[{r->p.L, r->p.prec}].push_back(r);
+  for (auto& kv : groups) {
+    sca::Bucket* b;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      b = buckets[kv.first].b;
+    }
+    std::vector<Request*>& rs = kv.second;
+    int32_t n = kRoundSteps;
+    for (Request* r : rs) n = std::min(n, r->a.max_steps - r->launched);
+    std::vector<sca::BucketReq*> br;
+    for (Request* r : rs) br.push_back(&r->br);
+    sca_status st = SCA_OK;
+    if (n > 0) {
+      st = sca::bucket_run(b, br.data(), (int)br.size(), n, true);
+      if (st == SCA_OK)
+        for (Request* r : rs) {
+          if (r->t_start < 0) {
+            std::lock_guard<std::mutex> lock(mu);
+            r->t_start = now();
+          }
+          r->launched += n;
+        }
+    }
+    std::vector<double> stat(8 * rs.size());
+    if (st == SCA_OK) st = sca::bucket_status(b, br.data(), (int)br.size(), stat.data());
+    if (st != SCA_OK) {
+      for (Request* r : rs) finish(r, st);
+      continue;
+    }
+    std::vector<Request*> done, evals;
+    for (size_t k = 0; k < rs.size(); ++k) {
+      Request* r = rs[k];
+      const double* s = &stat[8 * k];
+      if (((int)s[6]) & 2) {
+        sca::set_error("a bounded device-side wait ran out");
+        finish(r, SCA_ETIMEOUT);
+        continue;
+      }
+      if (s[4] != 0.0) {
+        sca::set_error("non-finite Omega or gradient, or a singular block");
+        finish(r, SCA_ENONFINITE);
+        continue;
+      }
+      const bool converged = s[5] < (double)r->launched;
+      if (!converged && r->launched < r->a.max_steps) {
+        still.push_back(r);
+        continue;
+      }
+      r->steps = (int32_t)s[5];
+      done.push_back(r);
+      if (!converged) evals.push_back(r);
+    }
+    if (!evals.empty()) {  // Omega and max|g| at the final phi
+      std::vector<sca::BucketReq*> be;
+      for (Request* r : evals) be.push_back(&r->br);
+      st = sca::bucket_run(b, be.data(), (int)be.size(), 1, false);
+      std::vector<double> s2(8 * evals.size());
+      if (st == SCA_OK) st = sca::bucket_status(b, be.data(), (int)be.size(), s2.data());
+      for (size_t k = 0; k < evals.size() && st == SCA_OK; ++k)
+        for (size_t i = 0; i < rs.size(); ++i)
+          if (rs[i] == evals[k]) std::copy(&s2[8 * k], &s2[8 * k] + 8, &stat[8 * i]);
+      if (st != SCA_OK) {
+        for (Request* r : done) finish(r, st);
+        continue;
+      }
+    }
+    for (Request* r : done) {
+      size_t i = 0;
+      while (rs[i] != r) ++i;
+      if (stat[8 * i + 4] != 0.0) {
+        sca::set_error("non-finite Omega or gradient, or a singular block");
+        finish(r, SCA_ENONFINITE);
+        continue;
+      }
+      r->phi.resize((size_t)r->p.L * r->p.L);
+      st = sca::bucket_get_phi(b, &r->br, r->phi.data());
+      r->omega = stat[8 * i];
+      r->gmax = stat[8 * i + 1];
+      finish(r, st);
+    }
+  }
 }
 
 void sca_server::run() {
@@ -90,11 +224,27 @@ void sca_server::run() {
     std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lock(mu);
-      while (!queue.empty() && (int32_t)(active.size() + admitted.size()) < slots &&
-             used + queue.front()->bytes <= budget) {
+      while (!queue.empty() && (int32_t)(active.size() + admitted.size()) < slots) {
         Request* r = queue.front();
+        uint64_t need = r->bytes;
+        int cap = 0;
+        const bool bk = sca::bucketed(r->p);
+        const auto key = std::make_pair(r->p.L, r->p.prec);
+        if (bk && !buckets.count(key)) {  // this request creates the bucket
+          if (used + need > budget) break;
+          cap = bucket_cap(r->p.L, r->p.prec, 2 * r->p.n_omega, budget - used - need);
+          if (cap == 0) break;
+          need += bucket_bytes(r->p.L, r->p.prec, cap);
+        }
+        if (used + need > budget) break;
         queue.pop_front();
-        used += r->bytes;
+        used += need;
+        if (bk) {
+          BucketSlot& bs = buckets[key];
+          if (cap) { bs.cap = cap; bs.bytes = need - r->bytes; }
+          ++bs.members;
+          r->in_bucket = true;
+        }
         r->state = 1;
         r->t_admit = now();
         admitted.push_back(r);
@@ -110,8 +260,19 @@ void sca_server::run() {
       }
     }
     for (Request* r : admitted) {
-      sca_status st = sca_create(&r->p, &r->ctx);
-      if (st == SCA_OK) st = sca_adam_init(r->ctx, &r->a, nullptr);
+      sca_status st = SCA_OK;
+      if (r->in_bucket) {
+        BucketSlot* bs;
+        {
+          std::lock_guard<std::mutex> lock(mu);
+          bs = &buckets[{r->p.L, r->p.prec}];
+        }
+        if (!bs->b) st = sca::bucket_create(r->p.L, r->p.prec, bs->cap, &bs->b);
+        if (st == SCA_OK) st = sca::bucket_req_init(bs->b, &r->br, r->p, r->a);
+      } else {
+        st = sca_create(&r->p, &r->ctx);
+        if (st == SCA_OK) st = sca_adam_init(r->ctx, &r->a, nullptr);
+      }
       if (st != SCA_OK) {
         finish(r, st);
         continue;
@@ -120,6 +281,7 @@ void sca_server::run() {
     }
     // one round: enqueue a batch for every request, then collect
     for (Request* r : active) {
+      if (r->in_bucket) continue;
       const int32_t n = std::min(kRoundSteps, r->a.max_steps - r->launched);
       if (n <= 0) continue;
       if (r->t_start < 0) {
@@ -130,7 +292,9 @@ void sca_server::run() {
       else r->launched += n;
     }
     std::vector<Request*> still;
+    run_buckets(active, still);
     for (Request* r : active) {
+      if (r->in_bucket) continue;
       sca_status st = SCA_OK;
       if (r->launched < 0) st = SCA_ECUDA;
       if (st == SCA_OK) st = sca::sync_status(r->ctx, r->ctx->stream);
@@ -202,8 +366,14 @@ sca_status sca_submit(sca_server* s, const sca_params* params, const sca_adam* a
     sca::set_error("sca_submit: invalid Adam settings");
     return SCA_EINVAL;
   }
-  if (bytes > s->budget) {
-    sca::set_error("sca_submit: the request's workspace (" + std::to_string(bytes) +
+  uint64_t least = bytes;  // memory the request needs on an otherwise idle server
+  if (sca::bucketed(*params)) {
+    // its own state (phi, m, v, g and status); the bucket's workspace is shared
+    bytes = sizeof(double) * (4 * (uint64_t)params->L * params->L + 8);
+    least = bytes + bucket_bytes(params->L, params->prec, 2 * params->n_omega);
+  }
+  if (least > s->budget) {
+    sca::set_error("sca_submit: the request's workspace (" + std::to_string(least) +
                    " bytes) exceeds the server's HBM budget");
     return SCA_EBUDGET;
   }
@@ -282,8 +452,10 @@ void sca_server_destroy(sca_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto& kv : s->all) {
     if (kv.second->ctx) sca_destroy(kv.second->ctx);
+    if (kv.second->in_bucket) sca::bucket_req_release(&kv.second->br);
     delete kv.second;
   }
+  for (auto& kv : s->buckets) sca::bucket_destroy(kv.second.b);
   for (Request* r : s->queue) (void)r;  // owned through `all`
   delete s;
 }

@@ -85,3 +85,49 @@ def test_over_budget_and_unknown_ids():
             srv.poll(12345)
         with pytest.raises(_lib.SCAError, match="SCA_EINVAL"):
             srv.submit(api.Params(3, 4, U=4.0, T=0.1), api.AdamConfig())
+
+
+# Sizes above the fused kernel's share a size bucket per (L, prec): one workspace, one launch
+# sequence for all their blocks, one reduction CTA per request.
+BUCKETED = [
+    (api.Params(16, 8, U=4.0, T=0.1, delta=1.0, prec="bf16x3"), api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=40, seed=11)),
+    (api.Params(16, 6, U=5.0, T=0.3, delta=0.5, prec="bf16x3"), api.AdamConfig(lr=0.02, grad_tol=1e-4, max_steps=60, seed=12)),
+    (api.Params(16, 4, U=3.0, T=0.5, delta=0.0, prec="bf16x3", ionic="half"), api.AdamConfig(lr=0.02, grad_tol=1e-6, max_steps=25, seed=13)),
+    (api.Params(10, 5, U=4.0, T=0.2, delta=0.7, prec="fp64"), api.AdamConfig(lr=0.02, grad_tol=1e-6, max_steps=30, seed=14)),
+    (api.Params(10, 3, U=6.0, T=0.4, delta=0.2, prec="fp64"), api.AdamConfig(lr=0.02, grad_tol=1e-6, max_steps=35, seed=15)),
+    (api.Params(16, 5, U=4.0, T=0.15, delta=0.8, prec="fp32"), api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=20, seed=16)),
+]
+
+
+def _check_same(reqs, mixed, alone):
+    for (p, a), x, y in zip(reqs, alone, mixed):
+        assert x.steps == y.steps
+        assert np.array_equal(x.phi, y.phi)
+        assert x.omega == y.omega and x.gmax == y.gmax
+
+
+def test_bucketed_requests_identical_alone_and_shared():
+    """Requests sharing a size bucket's passes (pivoted and dominant blocks of several
+    requests stacked, different T, n_omega, U, Delta, ionic convention and step counts) give
+    bit for bit what each gives alone."""
+    alone = [api.solve(p, a) for p, a in BUCKETED]
+    with api.Server(hbm_budget_bytes=16 << 30, max_slots=8) as srv:
+        ids = [srv.submit(p, a) for p, a in BUCKETED]
+        mixed = [_wait(srv, rid, p.N) for rid, (p, _) in zip(ids, BUCKETED)]
+    _check_same(BUCKETED, mixed, alone)
+
+
+def test_bucket_spread_over_passes():
+    """A budget that leaves the bucket 16 block slots: three requests of 8 to 12 blocks are
+    spread over several passes and still match their solo results."""
+    reqs = [(api.Params(16, n, U=4.0, T=0.12, delta=0.6, prec="3xtf32"),
+             api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=12, seed=20 + n)) for n in (4, 6, 5)]
+    alone = [api.solve(p, a) for p, a in reqs]
+    ws16 = api.workspace_bytes(api.Params(16, 8, U=1.0, T=1.0, prec="3xtf32"))
+    ws32 = api.workspace_bytes(api.Params(16, 16, U=1.0, T=1.0, prec="3xtf32"))
+    state = 8 * (4 * 256 + 8)
+    budget = ws16 + 3 * state + (ws32 - ws16) // 2  # room for a 16-slot bucket, not 32
+    with api.Server(hbm_budget_bytes=budget, max_slots=4) as srv:
+        ids = [srv.submit(p, a) for p, a in reqs]
+        mixed = [_wait(srv, rid, p.N) for rid, (p, _) in zip(ids, reqs)]
+    _check_same(reqs, mixed, alone)
