@@ -514,7 +514,8 @@ def run_serve(args):
         "value": round(len(ids) / wall, 4), "unit": "solves/s", "n_gpus": world,
         "steps": len(ids), "warmup": 0, "ms_per_step": round(1e3 * wall / len(ids), 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 storage, 3xtf32 / f32 contractions, f64 refinement" if prec != "fp64" else "f64",
+        "dtype": f"f32 storage, {prec} contractions (f32 below 128 x 128), f64 refinement"
+        if prec != "fp64" else "f64",
         "data": "synthetic (seeded Poisson trace, SplitMix64 start fields)",
         "config": {"workload": f"{len(ids)} requests, L in {{8..32}}, Poisson {args.serve_rate}/s, "
                                f"max|g| < 1e-6 or {args.serve_steps} steps, 120 GB budget, "

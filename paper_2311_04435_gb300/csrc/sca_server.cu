@@ -135,22 +135,28 @@ void sca_server::run_buckets(std::vector<Request*>& active, std::vector<Request*
   std::map<std::pair<int32_t, int32_t>, std::vector<Request*>> groups;
   for (Request* r : active)
     if (r->in_bucket) groups[{r->p.L, r->p.prec}].push_back(r);
-  for (auto& kv : groups) {
+  struct Round {
     sca::Bucket* b;
+    std::vector<Request*> rs;
+    std::vector<sca::BucketReq*> br;
+    sca_status st = SCA_OK;
+  };
+  std::vector<Round> rounds;
+  // enqueue every bucket's batch first (each on its own stream), then collect
+  for (auto& kv : groups) {
+    Round rd;
     {
       std::lock_guard<std::mutex> lock(mu);
-      b = buckets[kv.first].b;
+      rd.b = buckets[kv.first].b;
     }
-    std::vector<Request*>& rs = kv.second;
+    rd.rs = kv.second;
     int32_t n = kRoundSteps;
-    for (Request* r : rs) n = std::min(n, r->a.max_steps - r->launched);
-    std::vector<sca::BucketReq*> br;
-    for (Request* r : rs) br.push_back(&r->br);
-    sca_status st = SCA_OK;
+    for (Request* r : rd.rs) n = std::min(n, r->a.max_steps - r->launched);
+    for (Request* r : rd.rs) rd.br.push_back(&r->br);
     if (n > 0) {
-      st = sca::bucket_run(b, br.data(), (int)br.size(), n, true);
-      if (st == SCA_OK)
-        for (Request* r : rs) {
+      rd.st = sca::bucket_run(rd.b, rd.br.data(), (int)rd.br.size(), n, true);
+      if (rd.st == SCA_OK)
+        for (Request* r : rd.rs) {
           if (r->t_start < 0) {
             std::lock_guard<std::mutex> lock(mu);
             r->t_start = now();
@@ -158,8 +164,14 @@ void sca_server::run_buckets(std::vector<Request*>& active, std::vector<Request*
           r->launched += n;
         }
     }
+    rounds.push_back(std::move(rd));
+  }
+  for (Round& rd : rounds) {
+    sca::Bucket* b = rd.b;
+    std::vector<Request*>& rs = rd.rs;
+    sca_status st = rd.st;
     std::vector<double> stat(8 * rs.size());
-    if (st == SCA_OK) st = sca::bucket_status(b, br.data(), (int)br.size(), stat.data());
+    if (st == SCA_OK) st = sca::bucket_status(b, rd.br.data(), (int)rd.br.size(), stat.data());
     if (st != SCA_OK) {
       for (Request* r : rs) finish(r, st);
       continue;
