@@ -198,17 +198,22 @@ sca_status sca_solve(const sca_params* params, const sca_adam* adam, const doubl
 /* ------------------------------------------------------------ serving ---- */
 
 /* Creates a serving loop on the current device with an HBM admission budget
- * (bytes of workspace that admitted requests may hold at once) and at most
- * max_slots requests in flight.  A host thread admits queued requests as
- * slots and budget free up and advances all admitted requests together:
- * each round runs one Adam update for every in-flight request (their blocks
- * overlap on the device), so new requests join while others run
- * (continuous batching).  Errors: SCA_EINVAL, SCA_ENOMEM, SCA_ECUDA. */
+ * (bytes of device memory that admitted requests may hold at once) and at most
+ * max_slots requests in flight.  A host thread admits queued requests in
+ * arrival order as slots and budget free up and advances all admitted
+ * requests together, a few gated Adam updates per round, so new requests join
+ * while others run (continuous batching).  Requests whose blocks exceed the
+ * fused kernel's size (N > 144; FP64: N > 64) are batched by size bucket: those
+ * with the same L and precision share one workspace of up to 256 block slots
+ * (counted against the budget while the bucket has requests) and one launch
+ * sequence per step.  A request's result is the same bit for bit as with
+ * sca_solve.  Errors: SCA_EINVAL, SCA_ENOMEM, SCA_ECUDA. */
 sca_status sca_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, sca_server** out);
 
 /* Queues a solve request (parameters and Adam settings are copied; phi0 is
  * the seeded field of adam->seed).  *req_id receives its id.  Errors:
- * SCA_EINVAL, SCA_EBUDGET (the request alone exceeds the budget). */
+ * SCA_EINVAL, SCA_EBUDGET (the request alone, with a bucket just large enough
+ * for its blocks where it is bucketed, exceeds the budget). */
 sca_status sca_submit(sca_server* srv, const sca_params* params, const sca_adam* adam,
                       uint64_t* req_id);
 
