@@ -413,3 +413,46 @@ def test_metropolis_samples_the_sca_weight():
         err = batches.std(ddof=1) / math.sqrt(len(batches))
         assert abs(per_step.mean() - ref) < 4.0 * err + 1e-3, (per_step.mean(), ref, err)
     assert 0.2 < accepted / n < 0.9
+
+
+# ------------------------------------------------------------- paper trends ---
+
+def _stag_minimum(L, U, T, n_omega, hi=5.0):
+    """Minimiser of Omega over uniform staggered fields phi_i = a s_i (golden section)."""
+    p = oracle.make_params(L, n_omega, U=U, T=T)
+    s = sublattice(L)
+    f = lambda a: oracle.omega_grad(p, a * s)[0]
+    lo, g = 0.0, (math.sqrt(5.0) - 1.0) / 2.0
+    c, d = hi - g * (hi - lo), lo + g * (hi - lo)
+    fc, fd = f(c), f(d)
+    for _ in range(60):
+        if fc < fd:
+            hi, d, fd = d, c, fc
+            c = hi - g * (hi - lo)
+            fc = f(c)
+        else:
+            lo, c, fc = c, d, fd
+            d = lo + g * (hi - lo)
+            fd = f(d)
+    return 0.5 * (lo + hi)
+
+
+def test_paper_trend_order_parameter_grows_with_cutoff():
+    """Fig. 1 / Sec. III: |phi| grows with the Matsubara cut-off w_nmax and nearly converges by
+    w_nmax ~ 100 (U = 6, T = 0.1)."""
+    cut = [_stag_minimum(4, 6.0, 0.1, n) for n in (8, 16, 32, 80, 160, 320)]  # w_max 5 .. 200
+    steps = np.diff(cut)
+    assert np.all(steps > 0)
+    assert np.all(np.diff(steps / np.log([2.0, 2.0, 2.5, 2.0, 2.0])) < 0)  # saturating
+    assert abs(cut[4] - cut[5]) < 0.02 * cut[5]
+
+
+def test_paper_trend_neel_temperature_grows_with_U():
+    """Fig. 4 / Sec. III: the antiferromagnetic order survives to a higher T for larger U
+    (w_n <= 100): at T = 1.0 it has vanished for U = 4 but not for U = 6, which loses it by
+    T = 1.5; both are ordered at T = 0.6."""
+    def phi_star(U, T):
+        return _stag_minimum(4, U, T, int(100.0 / (2.0 * math.pi * T)) + 1)
+    assert phi_star(4.0, 0.6) > 0.5 and phi_star(6.0, 0.6) > 0.5
+    assert phi_star(4.0, 1.0) < 1e-3 < 1.0 < phi_star(6.0, 1.0)
+    assert phi_star(6.0, 1.5) < 1e-3
