@@ -458,6 +458,7 @@ sca_status sca_grad_dev(sca_ctx* c, const double* d_phi, double* d_omega, double
 }
 
 sca_status sca_potential(sca_ctx* c, const double* phi_host, double* omega) {
+  NvtxRange range("sca_potential");
   if (!c || !omega) { set_error("NULL argument"); return SCA_EINVAL; }
   sca_status st = upload_phi(c, phi_host);
   if (st != SCA_OK) return st;
@@ -468,6 +469,7 @@ sca_status sca_potential(sca_ctx* c, const double* phi_host, double* omega) {
 }
 
 sca_status sca_grad(sca_ctx* c, const double* phi_host, double* omega, double* grad) {
+  NvtxRange range("sca_grad");
   if (!c || !omega || !grad) { set_error("NULL argument"); return SCA_EINVAL; }
   sca_status st = upload_phi(c, phi_host);
   if (st != SCA_OK) return st;
@@ -502,6 +504,7 @@ sca_status sca_blocks(sca_ctx* c, const double* phi_host, double* ld, double* gd
 
 sca_status sca_dos(sca_ctx* c, const double* phi_host, const double* w_host, int32_t n_w,
                    double eta, double* rho_out) {
+  NvtxRange range("sca_dos");
   if (!c || !w_host || !rho_out || n_w < 1 || !(eta > 0.0) || !std::isfinite(eta)) {
     set_error("sca_dos: need ctx, w and rho_out, n_w >= 1 and a finite eta > 0");
     return SCA_EINVAL;
@@ -656,6 +659,7 @@ sca_status final_eval(sca_ctx* c) {
 extern "C" {
 
 sca_status sca_adam_step(sca_ctx* c, int32_t nsteps, double* omega, double* gmax) {
+  NvtxRange range("sca_adam_step");
   if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
   if (!c->adam_ready) { set_error("sca_adam_init has not been called"); return SCA_ENOSTATE; }
   if (nsteps < 1) { set_error("nsteps must be >= 1"); return SCA_EINVAL; }
@@ -714,6 +718,7 @@ sca_status sca_set_state(sca_ctx* c, const sca_adam* adam, const double* phi, co
 
 sca_status sca_solve(const sca_params* params, const sca_adam* adam, const double* phi0_host,
                      double* phi_out, double* omega, int32_t* steps, double* gmax) {
+  NvtxRange range("sca_solve");
   sca_status st = validate_adam(adam);
   if (st != SCA_OK) return st;
   sca_ctx* c = nullptr;

@@ -147,6 +147,7 @@ void bucket_req_release(BucketReq* r) {
 }
 
 sca_status bucket_run(Bucket* b, BucketReq* const* reqs, int n, int nsteps, bool adam) {
+  NvtxRange range("sca.bucket_run");
   Engine& e = b->ctx->e;
   cudaStream_t s = b->ctx->stream;
   const int N = e.N;

@@ -1553,12 +1553,18 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
     // sm_reserve SMs to the pivoted group's kernels.
     e.tc_cap = 0;
     const int span_p = np > 0 ? prof_span_begin(e, kSpanPiv, sp) : -1;
-    if (np > 0 && (st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
-      return st;
+    if (np > 0) {
+      NvtxRange range("sca.pivoted_group");
+      if ((st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
+        return st;
+    }
     prof_span_end(e, span_p, sp);
     if (fork && e.sm_reserve > 0 && e.tmap) e.tc_cap = tc_sms(e) - e.sm_reserve;
     const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, s) : -1;
-    st = nd > 0 ? run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s) : SCA_OK;
+    if (nd > 0) {
+      NvtxRange range("sca.dominant_group");
+      st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s);
+    }
     e.tc_cap = 0;
     if (st != SCA_OK) return st;
     prof_span_end(e, span_d, s);
@@ -1616,6 +1622,7 @@ sca_status set_smem_limits() {
 
 sca_status run_blocks(Engine& e, const double* d_phi, bool want_grad, cudaStream_t s,
                       bool refine_stage) {
+  NvtxRange range(want_grad ? "sca.blocks(inverse)" : "sca.blocks(log-det)");
   sca_status st;
   if (e.fp64) {
     if ((st = set_smem_limits<double, double>()) != SCA_OK) return st;

@@ -8,8 +8,18 @@
 #include <string>
 
 #include "../../include/sca.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sca {
+
+// NVTX range over a scope (host-side phases: what each API call and pass enqueues); costs a
+// call when no tool listens.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxFusedSteps = 16;  // Adam iterations per fused persistent launch
 

@@ -291,6 +291,7 @@ void sca_server::run() {
       }
       active.push_back(r);
     }
+    sca::NvtxRange round("sca.server_round");
     // one round: enqueue a batch for every request, then collect
     for (Request* r : active) {
       if (r->in_bucket) continue;

@@ -340,3 +340,29 @@ def test_full_size_40x40_sampled_blocks(prec):
     t = tol(prec)
     assert np.allclose(ld[sample], o_ld, rtol=t["ld"], atol=t["ld"])
     assert np.max(np.abs(gd[sample] - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+
+
+def test_profile_kinds_and_group_spans():
+    """Per-kind event timing (sca_profile_*): with both groups present (12 pivoted + 4
+    dominant blocks of 400 x 400) every step records both group spans once, the dominant
+    update and pivot-block inverses once per elimination step, and no counts while off."""
+    p = api.Params(20, 8, U=6.0, T=0.1, delta=0.5, prec="bf16x3")
+    assert api.pivoted_blocks(p) == 12
+    phi = inputs.seed_phi(0, p.N)
+    with api.Context(p) as c:
+        c.grad(phi)  # profiling off
+        c.profile(True)
+        c.grad(phi)
+        prof = c.profile_read()
+        c.profile(False)
+        c.grad(phi)
+        after = c.profile_read()
+    steps = -(-p.N // 128)  # elimination steps of width 128
+    assert prof["span_pivoted"][1] == 1 and prof["span_dominant"][1] == 1
+    assert prof["update"][1] == steps and prof["diag"][1] == steps
+    assert prof["panel"][1] > 0 and prof["refine"][1] >= 2 and prof["reduce"][1] == 1
+    for k in ("span_pivoted", "span_dominant", "update", "panel", "refine"):
+        assert prof[k][0] > 0.0
+    # spans contain the kernels of their group
+    assert prof["span_dominant"][0] >= prof["update"][0]
+    assert after == {k: (0.0, 0) for k in after}
