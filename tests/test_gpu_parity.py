@@ -366,3 +366,29 @@ def test_profile_kinds_and_group_spans():
     # spans contain the kernels of their group
     assert prof["span_dominant"][0] >= prof["update"][0]
     assert after == {k: (0.0, 0) for k in after}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_64x64_staggered_field_closed_form(prec):
+    """The 64x64 workload (128 blocks of 4096 x 4096: 6 pivoted with 2-wide shared-memory
+    sub-panels, 122 dominant) at a staggered field phi_i = a s_i, where Omega and the gradient
+    have the Fourier closed form (spin sigma sees the staggered potential Delta + sigma a)."""
+    from test_oracle_pins import G_staggered, ld_staggered, sublattice
+    wl = inputs.WORKLOADS["ionic_64x64"]
+    p = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, prec=prec)
+    assert api.pivoted_blocks(p) == 6
+    a, L, N = 0.8, wl.L, wl.L * wl.L
+    s = sublattice(L)
+    with api.Context(p) as c:
+        om, g = c.grad(a * s)
+    om_ref = N * a * a / wl.U
+    g_a = 2 * a / wl.U  # gradient on an A site (s = +1); B sites carry the opposite sign
+    for n in range(wl.n_omega):
+        w = (2 * n + 1) * math.pi * wl.T
+        for sg in (1, -1):
+            D = wl.delta + sg * a
+            om_ref -= 2 * wl.T * ld_staggered(L, D, w)
+            g_a -= 2 * wl.T * sg * G_staggered(L, D, w, -D).real
+    t = tol(prec)
+    assert om == pytest.approx(om_ref, rel=t["om"])
+    assert np.max(np.abs(g - g_a * s)) <= t["g"] * max(1.0, abs(g_a)) * 10
