@@ -44,6 +44,8 @@ def parse():
                     help="timed steps of the no-pivoting variant (0 = skip)")
     ap.add_argument("--dos-points", type=int, default=128,
                     help="real frequencies of the timed density of states (0 = skip)")
+    ap.add_argument("--sm-partition", type=int, default=DEFAULT_SM_PARTITION,
+                    help="SMs kept free of the dominant group's launches (0 = none)")
     ap.add_argument("--metro-steps", type=int, default=10,
                     help="timed Metropolis steps (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
@@ -127,6 +129,7 @@ def peaks():
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
 DEFAULT_PREC = "bf16x3"
+DEFAULT_SM_PARTITION = 0  # SMs kept free of the dominant group's launches (0: priorities only)
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum averaged over 8 update launches of a 16-block
 # 40x40 gradient, divided by 16; traffic grows with the blocks), per split precision, for the
@@ -224,6 +227,7 @@ def run_ours(args):
     # ---------------- device-resident timing (inputs resident in HBM)
     ctx = api.Context(params)
     ctx.set_stream(stream)
+    partition = list(ctx.set_sm_partition(args.sm_partition)) if args.sm_partition else [0, 0]
     ctx.adam_init(adam)
     ctx.adam_step(args.warmup)
     l0 = api.kernel_launches()
@@ -268,6 +272,8 @@ def run_ours(args):
     phi0 = np.ascontiguousarray(inputs.seed_phi(wl.seed, params.N))
     ctx2 = api.Context(params)
     ctx2.set_stream(stream)
+    if args.sm_partition:
+        ctx2.set_sm_partition(args.sm_partition)
     ctx2.adam_init(adam, phi0)
     ctx2.adam_step(max(1, args.warmup))
     torch.cuda.synchronize()
@@ -396,6 +402,7 @@ def run_ours(args):
                                    f"Delta={wl.delta}, T={wl.T}, n_omega={wl.n_omega}, "
                                    f"{2 * wl.n_omega} complex {params.N}x{params.N} blocks",
                        "prec": prec, "parallelism": f"replicas x{world}",
+                       "sm_partition": partition,
                        "l2": "inputs larger than L2 (blocks resident in HBM, "
                              f"{api.workspace_bytes(params) / 1e9:.1f} GB)",
                        "final_omega": om, "final_gmax": gm},

@@ -315,6 +315,22 @@ sca_status sca_metropolis_step(sca_ctx* ctx, int32_t n_steps, double* omega_trac
 typedef enum { SCA_PIVOT_PARTIAL = 0, SCA_PIVOT_NONE = 1 } sca_pivot;
 sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
 
+/* SM partitions for the two block groups (driver green contexts).  The pivoted group (the
+ * lowest frequencies, a chain of short dependent launches) and the dominant group (bandwidth-
+ * bound launches that fill every SM they reach) run side by side on one GPU; with a
+ * partition, every launch of the dominant group stays on the SMs outside a set of
+ * `pivoted_sms` SMs (rounded up by the driver to its granularity, 8 on this GPU), so the
+ * pivoted chain never waits for a dominant CTA to leave an SM.  Modes: 1 the pivoted group
+ * may still use any SM (highest stream priority), 2 it is confined to its own set as well.
+ * pivoted_sms = 0 removes the partition (the default: the dominant group's persistent
+ * tensor-core launches then leave 8 SMs free, and priorities do the rest).  Needs the
+ * tensor-core path; results do not depend on the partition (tile order and reductions are
+ * fixed).  SCA_ECUDA when the driver refuses the partition; the context then keeps its
+ * ordinary streams.  sca_sm_partition reports the SM counts in use (0, 0 without one). */
+typedef enum { SCA_PARTITION_DOMINANT = 1, SCA_PARTITION_BOTH = 2 } sca_partition_mode;
+sca_status sca_set_sm_partition(sca_ctx* ctx, int32_t pivoted_sms, int32_t mode);
+sca_status sca_sm_partition(sca_ctx* ctx, int32_t* pivoted_sms, int32_t* dominant_sms);
+
 /* Per-kernel timing.  While enabled, every launch of the context is bracketed by CUDA
  * events on the stream it is launched on, and the elapsed times are accumulated per kernel
  * kind when the calling API function synchronises.  Kinds: 0 assemble, 1 pivoted panel,
@@ -323,8 +339,12 @@ sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
  * diag(G)), 7 reduce (+Adam), 8 pivot-block inverse of the dominant blocks, 9 rank-nb update
  * of the pivoted group, 10 fused small-block Adam launch, 11 wall span of the pivoted group on
  * its stream, 12 wall span of the dominant group on the main stream (spans contain the
- * kernels above, so they are not part of any sum).  Enabling resets the counters.  Timing adds a small host overhead per
- * launch; keep it off when measuring throughput. */
+ * kernels above, so they are not part of any sum), 13 update of the rest of a pivoted outer
+ * panel after each sub-panel, 14 rank-nb factors of the pivoted group.  Enabling resets the
+ * counters.  Timing adds a small host overhead per launch; keep it off when measuring
+ * throughput.  With the environment variable SCA_PROFILE_TRACE set to a file name, each
+ * synchronisation also appends the launches it collected to that file, one line each:
+ * kind name, stream index (order of first use), start and duration in ms from the first. */
 sca_status sca_profile_enable(sca_ctx* ctx, int32_t enable);
 sca_status sca_profile_read(sca_ctx* ctx, int32_t kind, double* total_ms, uint64_t* launches);
 

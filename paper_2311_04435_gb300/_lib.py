@@ -71,6 +71,8 @@ SIGNATURES = [
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
     ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("sca_set_pivoting", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("sca_set_sm_partition", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("sca_sm_partition", ctypes.c_int, [_vp, _i32p, _i32p]),
     ("sca_dos", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int32, ctypes.c_double, _dp]),
     ("sca_metropolis_init", ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_uint64]),
     ("sca_metropolis_step", ctypes.c_int, [_vp, ctypes.c_int32, _dp, ctypes.POINTER(ctypes.c_uint8),

@@ -238,7 +238,7 @@ class Context:
 
     # ---- streams and per-kernel timing
     KINDS = ["assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
-             "update_piv", "fused", "span_pivoted", "span_dominant"]
+             "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv"]
 
     def set_stream(self, stream=None):
         """Enqueue on a torch.cuda.Stream (or raw handle); None restores the own stream."""
@@ -256,6 +256,21 @@ class Context:
         if mode not in modes:
             raise ValueError(f"pivoting mode must be one of {sorted(modes)}")
         check(_lib.lib().sca_set_pivoting(self._h, modes[mode]))
+
+    def set_sm_partition(self, pivoted_sms: int = 0, mode: str = "dominant"):
+        """Keep the dominant group's launches off `pivoted_sms` SMs (green contexts); mode
+        'dominant' leaves the pivoted group free to use any SM, 'both' confines it to its
+        set.  0 removes the partition.  Returns the SM counts in use (pivoted, dominant)."""
+        modes = {"dominant": 1, "both": 2}
+        if mode not in modes:
+            raise ValueError(f"partition mode must be one of {sorted(modes)}")
+        check(_lib.lib().sca_set_sm_partition(self._h, int(pivoted_sms), modes[mode]))
+        return self.sm_partition()
+
+    def sm_partition(self):
+        p, d = ctypes.c_int32(), ctypes.c_int32()
+        check(_lib.lib().sca_sm_partition(self._h, ctypes.byref(p), ctypes.byref(d)))
+        return p.value, d.value
 
     def profile(self, enable: bool = True):
         check(_lib.lib().sca_profile_enable(self._h, 1 if enable else 0))

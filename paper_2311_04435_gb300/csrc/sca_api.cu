@@ -124,6 +124,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   bytes += 2 * (size_t)e.chunk * e.fw_mat * S;            // F, W
   bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
   if (e.tc) bytes += (size_t)e.chunk * 6 * e.nb * e.nb * 4;  // -T^T split planes
+  bytes += (size_t)e.chunk * e.N * 2 * sizeof(float);     // Re A_jj as double-float
   bytes += 2 * (size_t)e.chunk * e.N * sizeof(int);       // piv, perm
   bytes += (size_t)e.B * sizeof(double) * (3 + e.N);      // ld, d_z, tr, gd
   bytes += (size_t)e.N * sizeof(double) * 7 + 256;        // eps, phi, m, v, g, in, misc
@@ -153,6 +154,7 @@ sca_status allocate(Engine& e) {
   SCA_ALLOC(e.F, (size_t)e.chunk * e.fw_mat * S, "F");
   SCA_ALLOC(e.W, (size_t)e.chunk * e.fw_mat * S, "W");
   SCA_ALLOC(e.Tinv, (size_t)e.chunk * 2 * e.nb * e.nb * 2 * S, "Tinv");
+  SCA_ALLOC(e.adiag, (size_t)e.chunk * e.N * 2 * sizeof(float), "diagonal table");
   SCA_ALLOC(e.piv, (size_t)e.chunk * e.N * sizeof(int), "piv");
   SCA_ALLOC(e.perm, (size_t)e.chunk * e.N * sizeof(int), "perm");
   SCA_ALLOC(e.flags, 16, "flags");
@@ -198,6 +200,8 @@ sca_status allocate(Engine& e) {
   if (err == cudaSuccess && e.tc) err = cudaEventCreateWithFlags(&e.ev_aux0, cudaEventDisableTiming);
   if (err == cudaSuccess && e.tc) err = cudaEventCreateWithFlags(&e.ev_aux1, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }
+  err = cudaEventCreateWithFlags(&e.ev_join2, cudaEventDisableTiming);
+  if (err != cudaSuccess) { release(e); return cuda_fail(err, "join event"); }
   return SCA_OK;
 }
 
@@ -223,6 +227,7 @@ void prof_begin(Engine& e, int kind, cudaStream_t s) {
   r.kind = kind;
   r.a = p->pool[p->used++];
   r.b = p->pool[p->used++];
+  r.s = s;
   cudaEventRecord(r.a, s);
 }
 
@@ -246,16 +251,36 @@ void prof_end(Engine& e, int kind, cudaStream_t s) {
   if (r.kind == kind) cudaEventRecord(r.b, s);
 }
 
+// Names of the kinds in the timeline file (SCA_PROFILE_TRACE), in KernelKind order.
+static const char* const kKindNames[kKinds] = {
+    "assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
+    "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv"};
+
 void prof_collect(Engine& e) {
   Profiler* p = e.prof;
   if (!p) return;
+  // optional timeline: one line per launch (kind, stream index, start and duration in ms
+  // from the first record of this collection), appended to the file SCA_PROFILE_TRACE names
+  FILE* tf = nullptr;
+  if (const char* path = std::getenv("SCA_PROFILE_TRACE"))
+    if (*path && p->nrec > 0) tf = std::fopen(path, "a");
+  std::vector<cudaStream_t> streams;
+  if (tf) std::fprintf(tf, "# collection of %d records: kind stream start_ms dur_ms\n", p->nrec);
   for (int k = 0; k < p->nrec; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->recs[k].a, p->recs[k].b) == cudaSuccess) {
       p->ms[p->recs[k].kind] += ms;
       p->n[p->recs[k].kind] += 1;
+      float t0 = 0.f;
+      if (tf && cudaEventElapsedTime(&t0, p->recs[0].a, p->recs[k].a) == cudaSuccess) {
+        size_t si = 0;
+        while (si < streams.size() && streams[si] != p->recs[k].s) ++si;
+        if (si == streams.size()) streams.push_back(p->recs[k].s);
+        std::fprintf(tf, "%s %zu %.4f %.4f\n", kKindNames[p->recs[k].kind], si, t0, ms);
+      }
     }
   }
+  if (tf) std::fclose(tf);
   (void)cudaGetLastError();
   p->nrec = 0;
   p->used = 0;
@@ -275,6 +300,9 @@ void release(Engine& e) {
   prof_free(e);
   tc_release(e);
   fused_release(e);
+  partition_release(e);
+  if (e.ev_join2) cudaEventDestroy(e.ev_join2);
+  e.ev_join2 = nullptr;
   if (e.side) { cudaStreamSynchronize(e.side); cudaStreamDestroy(e.side); }
   if (e.ev_fork) cudaEventDestroy(e.ev_fork);
   if (e.ev_join) cudaEventDestroy(e.ev_join);
@@ -283,7 +311,7 @@ void release(Engine& e) {
   if (e.ev_aux1) cudaEventDestroy(e.ev_aux1);
   e.side = e.aux = nullptr;
   e.ev_fork = e.ev_join = e.ev_aux0 = e.ev_aux1 = nullptr;
-  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.piv, e.perm, e.flags, e.ld, e.d_z, e.tr, e.gd,
+  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.adiag, e.piv, e.perm, e.flags, e.ld, e.d_z, e.tr, e.gd,
                   e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -292,6 +320,7 @@ void release(Engine& e) {
   e.h_flags = nullptr;
   e.M = e.F = e.W = e.Tinv = nullptr;
   e.tt = nullptr;
+  e.adiag = nullptr;
   e.piv = e.perm = e.flags = nullptr;
   e.d_z = e.tr = nullptr;
   e.ld = e.gd = e.eps_extra = e.d_phi = e.d_m = e.d_v = e.d_g = e.d_status = e.d_omega = nullptr;
@@ -776,6 +805,34 @@ sca_status sca_set_pivoting(sca_ctx* c, int32_t mode) {
   }
   c->e.piv_blocks = (mode == SCA_PIVOT_NONE) ? 0 : c->e.piv_planned;
   c->e.nopiv = (mode == SCA_PIVOT_NONE);
+  return SCA_OK;
+}
+
+sca_status sca_set_sm_partition(sca_ctx* c, int32_t pivoted_sms, int32_t mode) {
+  if (!c || pivoted_sms < 0 || (pivoted_sms > 0 && mode != SCA_PARTITION_DOMINANT &&
+                                mode != SCA_PARTITION_BOTH)) {
+    set_error("bad context, SM count or partition mode");
+    return SCA_EINVAL;
+  }
+  cudaError_t err = cudaStreamSynchronize(c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "partition change");
+  partition_release(c->e);
+  if (pivoted_sms == 0) return SCA_OK;
+  if (!c->e.tc) {
+    set_error("SM partitions need the tensor-core path (3xTF32 or BF16x3)");
+    return SCA_EINVAL;
+  }
+  if (!partition_setup(c->e, pivoted_sms, mode)) {
+    set_error("green-context SM partition unavailable or refused");
+    return SCA_ECUDA;
+  }
+  return SCA_OK;
+}
+
+sca_status sca_sm_partition(sca_ctx* c, int32_t* pivoted_sms, int32_t* dominant_sms) {
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  if (pivoted_sms) *pivoted_sms = c->e.dom ? c->e.part_sms[0] : 0;
+  if (dominant_sms) *dominant_sms = c->e.dom ? c->e.part_sms[1] : 0;
   return SCA_OK;
 }
 

@@ -840,78 +840,175 @@ __global__ void __launch_bounds__(256)
 // Inverses of the pivoted group's pivot block from the packed LU of the outer panel (the
 // interchanges already moved the pivot rows into K, so M_KK = L_KK U_KK):
 //   Tinv slot 0: T = inv(M_KK) = inv(U_KK) inv(L_KK)        slot 1: inv(L_KK)
-// row by row, as solves from the right of unit rows e_r.  The packed kb x kb LU and the
-// reciprocals 1/u_jj are staged in shared memory once; 32 right-hand sides per CTA are then
-// solved column by column with one barrier per column (forward with U, the 1/u_jj applied
-// after the sweep, then backward with the unit-lower L).  Grid x: 2 ceil(kb/32) row groups
-// (rows of T, then rows of inv(L)).  Warp w owns the columns k = w (mod 8), so the L and U
-// entries of one step are the same for the whole warp (broadcast reads).
-template <typename S, typename C>
-__global__ void __launch_bounds__(256)
-    k_tinv_rows(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
-                int nb, cpx<C>* Tinv) {
-  constexpr int R = 32;
+// row by row, as solves from the right of unit rows e_r: row r of T is e_r inv(U) inv(L)
+// (forward with U from column r on, then backward with the unit-lower L), row r of inv(L)
+// is e_r inv(L) (backward from column r down).  One CTA per block: the packed kb x kb LU and
+// the reciprocals 1/u_jj sit in shared memory, and each warp solves whole rows with the row
+// held in registers (lane l keeps columns l, l + 32, ...; the pivot entry of a step comes by
+// shuffle), so a step needs no barrier.  Warp w of W takes the pairs (row r of T, row r of
+// inv(L)) for r = w, w + W, ..., whose lengths add up to 2 kb steps.
+template <typename S, typename C, int NT>
+__global__ void __launch_bounds__(NT)
+    k_tinv_warp(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+                int nb, cpx<C>* Tinv, float* TT) {
+  constexpr int NBMAX = sizeof(C) == 8 ? 64 : 128;
+  constexpr int KQ = NBMAX / 32;  // columns per lane
   extern __shared__ unsigned char smem_raw[];
-  const int xs = kb + 1;
-  cpx<C>* LU = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x (kb + 1)
-  cpx<C>* X = LU + (size_t)kb * xs;                  // R x (kb + 1)
-  cpx<C>* dinv = X + (size_t)R * xs;                 // kb
-  const int mat = blockIdx.y, tid = threadIdx.x;
-  const int groups = (kb + R - 1) / R;
-  const bool tpart = (int)blockIdx.x < groups;     // rows of T (else rows of inv(L))
-  const int row0 = (tpart ? blockIdx.x : blockIdx.x - groups) * R;
+  cpx<C>* LU = reinterpret_cast<cpx<C>*>(smem_raw);  // kb x kb
+  cpx<C>* dinv = LU + (size_t)kb * kb;               // kb
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const S* re = M + mat * mat_stride + (size_t)k0 * ldm + k0;  // the packed pivot block
   const S* im = re + plane_stride;
-  for (int e = tid; e < kb * kb; e += 256) {
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int a = e / kb, b = e - a * kb;
     const size_t o = (size_t)a * ldm + b;
-    LU[a * xs + b] = {(C)re[o], (C)im[o]};
-  }
-  for (int e = tid; e < R * kb; e += 256) {
-    const int r = e / kb, cc = e - r * kb;
-    X[r * xs + cc] = {(C)((row0 + r == cc) ? 1 : 0), (C)0};
+    LU[e] = {(C)re[o], (C)im[o]};
   }
   __syncthreads();
-  for (int k = tid; k < kb; k += 256) {
-    const cpx<C> d = LU[k * xs + k];
+  for (int k = tid; k < kb; k += blockDim.x) {
+    const cpx<C> d = LU[k * kb + k];
     const C m2 = d.re * d.re + d.im * d.im;
     dinv[k] = {d.re / m2, -d.im / m2};
   }
   __syncthreads();
-  const int r = tid & (R - 1), g = tid >> 5;
-  const bool live = row0 + r < kb;
-  cpx<C>* x = X + r * xs;
-  if (tpart) {
-    for (int j = 0; j < kb; ++j) {
-      if (live) {
-        const cpx<C> y = cmul(x[j], dinv[j]);
-        const cpx<C>* u = LU + j * xs;
-        for (int k = j + 1 + ((g - j - 1) & 7); k < kb; k += 8) {
-          x[k].re -= y.re * u[k].re - y.im * u[k].im;
-          x[k].im -= y.re * u[k].im + y.im * u[k].re;
+  cpx<C>* outT = Tinv + (size_t)mat * 2 * nb * nb;
+  cpx<C>* outL = outT + (size_t)nb * nb;
+  for (int r = warp; r < nb; r += NT / 32) {
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {  // 0: row r of T, 1: row r of inv(L)
+      C xr[KQ], xi[KQ];
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        xr[q] = (C)((q * 32 + lane == r) ? 1 : 0);
+        xi[q] = (C)0;
+      }
+      if (r < kb) {
+        if (part == 0) {  // x <- x inv(U): x_j /= u_jj, then x_k -= x_j u_jk (k > j)
+#pragma unroll
+          for (int q = 0; q < KQ; ++q) {
+            for (int jj = 0; jj < 32; ++jj) {
+              const int j = q * 32 + jj;
+              if (j < r || j >= kb) continue;
+              const C yr0 = __shfl_sync(0xffffffffu, xr[q], jj);
+              const C yi0 = __shfl_sync(0xffffffffu, xi[q], jj);
+              const cpx<C> d = dinv[j];
+              const C yr = yr0 * d.re - yi0 * d.im, yi = yr0 * d.im + yi0 * d.re;
+              if (lane == jj) { xr[q] = yr; xi[q] = yi; }
+              const cpx<C>* u = LU + (size_t)j * kb;
+#pragma unroll
+              for (int q2 = q; q2 < KQ; ++q2) {
+                const int k = q2 * 32 + lane;
+                if (k > j && k < kb) {
+                  const cpx<C> uv = u[k];
+                  xr[q2] -= yr * uv.re - yi * uv.im;
+                  xi[q2] -= yr * uv.im + yi * uv.re;
+                }
+              }
+            }
+          }
+        }
+        // x <- x inv(L): for j descending, x_k -= x_j l_jk (k < j); a unit row e_r of
+        // inv(L) has x_j = 0 above r
+        const int jtop = part == 0 ? kb - 1 : r;
+#pragma unroll
+        for (int q = KQ - 1; q >= 0; --q) {
+          for (int jj = 31; jj >= 0; --jj) {
+            const int j = q * 32 + jj;
+            if (j > jtop || j < 1) continue;
+            const C yr = __shfl_sync(0xffffffffu, xr[q], jj);
+            const C yi = __shfl_sync(0xffffffffu, xi[q], jj);
+            const cpx<C>* l = LU + (size_t)j * kb;
+#pragma unroll
+            for (int q2 = 0; q2 <= q; ++q2) {
+              const int k = q2 * 32 + lane;
+              if (k < j) {
+                const cpx<C> lv = l[k];
+                xr[q2] -= yr * lv.re - yi * lv.im;
+                xi[q2] -= yr * lv.im + yi * lv.re;
+              }
+            }
+          }
         }
       }
-      __syncthreads();
-    }
-    if (live)
-      for (int k = g; k < kb; k += 8) x[k] = cmul(x[k], dinv[k]);
-    __syncthreads();
-  }
-  for (int j = kb - 1; j > 0; --j) {
-    if (live) {
-      const cpx<C> y = x[j];
-      const cpx<C>* l = LU + j * xs;
-      for (int k = g; k < j; k += 8) {
-        x[k].re -= y.re * l[k].re - y.im * l[k].im;
-        x[k].im -= y.re * l[k].im + y.im * l[k].re;
+      cpx<C>* out = (part == 0 ? outT : outL) + (size_t)r * nb;
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        const int k = q * 32 + lane;
+        if (k < nb) out[k] = (r < kb && k < kb) ? cpx<C>{xr[q], xi[q]} : cpx<C>{(C)0, (C)0};
       }
     }
+  }
+  if (!TT) return;
+  // B operands of the tensor-core prep product F = M[:, K] X as bf16 split planes of -X^T
+  // (re_hi, im_hi, re_lo, im_lo, -im_hi, -im_lo; element [j][r] = -X[r][j]): X = T in the
+  // first half of each of the block's six float-plane slots, X = inv(L) in the second half.
+  // The rows just written are read back through shared memory (the LU is no longer needed).
+  __syncthreads();
+  const size_t P = (size_t)nb * nb;
+  float* tt = TT + (size_t)mat * 6 * P;
+  cpx<C>* Sm = LU;  // [nb][nb + 1]
+  for (int part = 0; part < 2; ++part) {
+    const cpx<C>* src = part == 0 ? outT : outL;
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e / nb, j = e - r * nb;
+      Sm[(size_t)r * (nb + 1) + j] = src[e];
+    }
+    __syncthreads();
+    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(tt + (part == 0 ? 0 : P / 2));
+    for (int e = tid; e < nb * (nb / 4); e += NT) {
+      const int jr = e / (nb / 4), r4 = (e - jr * (nb / 4)) * 4;
+      __nv_bfloat16 h[6][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const cpx<C> v = Sm[(size_t)(r4 + t) * (nb + 1) + jr];
+        const float fr = -(float)v.re, fi = -(float)v.im;
+        h[0][t] = __float2bfloat16_rn(fr);
+        h[1][t] = __float2bfloat16_rn(fi);
+        h[2][t] = __float2bfloat16_rn(fr - __bfloat162float(h[0][t]));
+        h[3][t] = __float2bfloat16_rn(fi - __bfloat162float(h[1][t]));
+        h[4][t] = __hneg(h[1][t]);
+        h[5][t] = __hneg(h[3][t]);
+      }
+      const size_t o = (size_t)jr * nb + r4;
+#pragma unroll
+      for (int pl = 0; pl < 6; ++pl)
+        *reinterpret_cast<uint2*>(dst + 2 * pl * P + o) = *reinterpret_cast<const uint2*>(h[pl]);
+    }
     __syncthreads();
   }
-  cpx<C>* out = Tinv + (size_t)mat * 2 * nb * nb + (tpart ? 0 : (size_t)nb * nb);
-  if (row0 + r < nb)
-    for (int cc = g; cc < nb; cc += 8)
-      out[(size_t)(row0 + r) * nb + cc] = (live && cc < kb) ? x[cc] : cpx<C>{(C)0, (C)0};
+}
+
+// A operand of the pivoted group's tensor-core prep product: the columns K of rows
+// [r_begin, N) as bf16 split planes (re_hi, im_hi, re_lo, im_lo; columns past kb zero) in the
+// block's W planes, which k_prep_w rewrites afterwards.  4 columns per thread.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_split_a(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+              int nb, float* W, size_t fw_plane, size_t fw_mat, int r_begin) {
+  const int mat = blockIdx.y;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q4 = nb / 4;
+  const int i = r_begin + (int)(e / q4), c4 = (int)(e % q4) * 4;
+  if (i >= N) return;
+  const S* re = M + mat * mat_stride + (size_t)i * ldm + k0;
+  const S* im = re + plane_stride;
+  __nv_bfloat16 h[4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int c = c4 + t;
+    const float fr = c < kb ? (float)re[c] : 0.f, fi = c < kb ? (float)im[c] : 0.f;
+    h[0][t] = __float2bfloat16_rn(fr);
+    h[1][t] = __float2bfloat16_rn(fi);
+    h[2][t] = __float2bfloat16_rn(fr - __bfloat162float(h[0][t]));
+    h[3][t] = __float2bfloat16_rn(fi - __bfloat162float(h[1][t]));
+  }
+  float* w = W + mat * fw_mat;
+  const size_t o = (size_t)i * nb + c4;
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl)
+    *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(w + pl * fw_plane) + o) =
+        *reinterpret_cast<const uint2*>(h[pl]);
 }
 
 // W^T: 64 columns j x nb per CTA, transposed through shared memory.
@@ -1109,13 +1206,32 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
 
 // The same refinement for unpivoted blocks (X = R, no permutation): each warp reads its row
 // straight from the inverse, the bond partners x_{j+L} and x_{j+1} come through L1, and only
-// the double-float a_j sit in shared memory, so the kernel runs at full occupancy and is
-// bound by the single read of the inverses.  The arithmetic and its order per row are those
-// of k_refine.
-constexpr int kRefineRowsPerCta = 32;
+// the double-float a_j sit in shared memory.  The double-float arithmetic costs ~140 FP32
+// operations per site, so the kernel is ALU-bound; away from site i, where the inverse has
+// decayed, it is not needed: a warp whose 32 sites all have term magnitudes
+//   s_j = |a_j| |x_j|^2 + 2 w_n |Re x_j Im x_j| + 2|t| (|Re x_j| (|Re x_{j+x}| + |Re x_{j+y}|)
+//         + |Im x_j| (|Im x_{j+x}| + |Im x_{j+y}|))
+// below 2^-18 / N sums them in plain float32 into a second accumulator.  Each such term is
+// then off by less than ~2^-21 s_j, so all of them together by less than 2^-39 (absolute) in
+// G_ii; the sites near i keep the double-float arithmetic of k_refine.
+constexpr int kRefineRowsPerCta = 64;
+constexpr int kRefineUnroll = 4;
+
+// Re A_jj = mu - eps_j of each block as a double-float pair, once per block (FP64 is a slow
+// pipe here; the refinement's CTAs then stage the table instead of recomputing it).
 __global__ void __launch_bounds__(256)
+    k_adiag(Lattice la0, int b0, dsf* __restrict__ out) {
+  const int N = la0.N;
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) out[(size_t)mat * N + r] = ds_of(la.mu - site_energy(la, r, sg));
+}
+
+__global__ void __launch_bounds__(256, 4)
     k_refine_direct(const float* __restrict__ M, int ldm, size_t mat_stride, size_t plane_stride,
-                    int b0, Lattice la0, double* __restrict__ gd) {
+                    int b0, Lattice la0, const dsf* __restrict__ adiag_g, double* __restrict__ gd) {
   extern __shared__ unsigned char smem_raw[];
   dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
   const int N = la0.N, L = la0.L;
@@ -1123,39 +1239,76 @@ __global__ void __launch_bounds__(256)
   int n, sg;
   const Lattice la = block_lattice(la0, b, n, sg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = ds_of(la.mu - site_energy(la, r, sg));
+  for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = adiag_g[(size_t)mat * N + r];
   __syncthreads();
   const float* re0 = M + mat * mat_stride;
   const float* im0 = re0 + plane_stride;
   const double w = (2.0 * n + 1.0) * kPi * la.T;
   const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
+  const float small = 0x1.0p-18f / (float)N;
   const int dxs = 32 / L, dys = 32 % L;
   const int i_end = min(N, (int)(blockIdx.x + 1) * kRefineRowsPerCta);
   for (int i = blockIdx.x * kRefineRowsPerCta + warp; i < i_end; i += 8) {
     const float* re = re0 + (size_t)i * ldm;
     const float* im = im0 + (size_t)i * ldm;
     dsf acc = {0.f, 0.f};
+    float accf = 0.f;
     int xx = lane / L, yy = lane - (lane / L) * L;
-    for (int j = lane; j < N; j += 32) {
-      const int jx = (xx + 1 == L) ? yy : j + L;
-      const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
-      const float a = re[j], bq = im[j];
-      const float ax = re[jx], bx = im[jx];
-      const float ay = re[jy], by = im[jy];
-      const dsf q = ds_sub(two_prod(a, a), two_prod(bq, bq));
-      const dsf ab = two_prod(a, bq);
-      const dsf u = ds_add(ds_sub(two_prod(a, ax), two_prod(bq, bx)),
-                           ds_sub(two_prod(a, ay), two_prod(bq, by)));
-      const dsf e = ds_add(ds_sub(ds_mul(adiag[j], q), ds_mul(w2, ab)), ds_mul(t2, u));
-      acc = ds_add(acc, e);
-      yy += dys;
-      xx += dxs;
-      if (yy >= L) { yy -= L; xx += 1; }
-    }
-    double qsum = (double)acc.h + (double)acc.l;
+    // kRefineUnroll chunks of 32 sites per round: all their loads are issued before any of
+    // them is used, so a warp keeps several row segments in flight
+    for (int j0 = 0; j0 < N; j0 += 32 * kRefineUnroll) {  // warp-uniform trip count
+      float a[kRefineUnroll], bq[kRefineUnroll], ax[kRefineUnroll], bx[kRefineUnroll];
+      float ay[kRefineUnroll], by[kRefineUnroll];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, off);
-    if (lane == 0) gd[(size_t)b * N + i] = sg * (2.0 * (double)re[i] - qsum);
+      for (int u = 0; u < kRefineUnroll; ++u) {
+        const int j = j0 + 32 * u + lane;
+        const bool in = j < N;
+        const int jx = (xx + 1 == L) ? yy : j + L;
+        const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
+        a[u] = in ? re[j] : 0.f;
+        bq[u] = in ? im[j] : 0.f;
+        ax[u] = in ? re[jx] : 0.f;
+        bx[u] = in ? im[jx] : 0.f;
+        ay[u] = in ? re[jy] : 0.f;
+        by[u] = in ? im[jy] : 0.f;
+        yy += dys;
+        xx += dxs;
+        if (yy >= L) { yy -= L; xx += 1; }
+      }
+#pragma unroll
+      for (int u = 0; u < kRefineUnroll; ++u) {
+        const int j = j0 + 32 * u + lane;
+        const dsf ad = j < N ? adiag[j] : dsf{0.f, 0.f};
+        const float aa = fabsf(a[u]), ba = fabsf(bq[u]);
+        const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
+                         t2a * (aa * (fabsf(ax[u]) + fabsf(ay[u])) +
+                                ba * (fabsf(bx[u]) + fabsf(by[u])));
+        if (__any_sync(0xffffffffu, !(sj <= small))) {
+          const dsf q = ds_sub(two_prod(a[u], a[u]), two_prod(bq[u], bq[u]));
+          const dsf ab = two_prod(a[u], bq[u]);
+          const dsf uu = ds_add(ds_sub(two_prod(a[u], ax[u]), two_prod(bq[u], bx[u])),
+                                ds_sub(two_prod(a[u], ay[u]), two_prod(bq[u], by[u])));
+          const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, uu));
+          acc = ds_add(acc, e);
+        } else {
+          accf += ad.h * (a[u] * a[u] - bq[u] * bq[u]) - w2f * (a[u] * bq[u]) +
+                  t2f * (a[u] * (ax[u] + ay[u]) - bq[u] * (bx[u] + by[u]));
+        }
+      }
+    }
+    // the warp's sum in double-float too; float64 only for the one result of the row
+    acc = ds_add(acc, dsf{accf, 0.f});
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const dsf o = {__shfl_xor_sync(0xffffffffu, acc.h, off),
+                     __shfl_xor_sync(0xffffffffu, acc.l, off)};
+      acc = ds_add(acc, o);
+    }
+    if (lane == 0) {
+      const double qsum = (double)acc.h + (double)acc.l;
+      gd[(size_t)b * N + i] = sg * (2.0 * (double)re[i] - qsum);
+    }
   }
 }
 
@@ -1330,10 +1483,17 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, 
       SCA_LAUNCH_CHECK("refine");
     }
     if (cnt > np) {
+      if (!e.adiag) {
+        set_error("refinement without a diagonal table in the workspace");
+        return SCA_ENOSTATE;
+      }
       const int gx = (N + kRefineRowsPerCta - 1) / kRefineRowsPerCta;
+      dsf* tab = reinterpret_cast<dsf*>(e.adiag) + (size_t)(m0 + np) * N;
+      k_adiag<<<dim3((N + 255) / 256, cnt - np), 256, 0, s>>>(la, bg + np, tab);
+      SCA_LAUNCH_CHECK("diagonal table");
       k_refine_direct<<<dim3(gx, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
           reinterpret_cast<const float*>(M) + (size_t)np * e.mat_stride, e.ldm, e.mat_stride,
-          e.plane_stride, bg + np, la, e.gd);
+          e.plane_stride, bg + np, la, tab, e.gd);
       SCA_LAUNCH_CHECK("refine direct");
     }
   } else {
@@ -1361,6 +1521,9 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   int* perm = e.perm + (size_t)m0 * N;
   const size_t fw_plane = (size_t)N * nb;
   const int split = tcg ? (e.bf16 ? 2 : 1) : 0;
+  // the pivoted group's prep product on the tensor cores (BF16x3 with the -T^T planes)
+  const bool piv_tc_prep =
+      pivoted && tcg && e.bf16 && e.tt != nullptr && nb == e.nb && sizeof(C) == 4;
   // dominant blocks on the tensor cores: symmetric updates (lower tiles only)
   bool sym = tcg && !pivoted && e.tt != nullptr;
   if (const char* v = std::getenv("SCA_SYM"))
@@ -1393,10 +1556,10 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
         prof_end(e, kSwap, s);
         SCA_LAUNCH_CHECK("swap");
         if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
-          prof_begin(e, kTrinv, s);
+          prof_begin(e, kPanelUpd, s);
           k_gemm_panel<S, C><<<dim3((N - s0 - kbi + 63) / 64, cnt), 256, 0, s>>>(
               M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, kend);
-          prof_end(e, kTrinv, s);
+          prof_end(e, kPanelUpd, s);
           SCA_LAUNCH_CHECK("panel update");
         }
       }
@@ -1423,11 +1586,12 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     }
     if (pivoted) {
       // T and inv(L_KK) of the factored pivot block, for F = M[:, K] T (inv(L_KK) below K)
-      const int groups = (kb + 31) / 32;
       prof_begin(e, kTrinv, s);
-      const size_t smt = sizeof(cpx<C>) * ((size_t)(kb + 32) * (kb + 1) + kb);
-      k_tinv_rows<S, C><<<dim3(2 * groups, cnt), 256, smt, s>>>(M, e.ldm, e.mat_stride,
-                                                                e.plane_stride, k0, kb, nb, Tinv);
+      const size_t smt = sizeof(cpx<C>) * std::max((size_t)kb * kb + kb, (size_t)nb * (nb + 1));
+      constexpr int NT = sizeof(C) == 8 ? 512 : 1024;
+      float* TT = piv_tc_prep ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
+      k_tinv_warp<S, C, NT><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
+                                                  nb, Tinv, TT);
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("pivot-block inverse");
     } else {
@@ -1466,7 +1630,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       if (st != SCA_OK) return st;
       prof_end(e, kPrep, s);
     } else {
-      prof_begin(e, kPrep, s);
+      prof_begin(e, pivoted ? kPrepPiv : kPrep, s);
       if (tcg && !pivoted && nb == e.nb && e.tt && !e.bf16) {
         // F = M[:, K] T on the tensor cores (scratch: the W planes, rewritten below)
         const int rs = r0;
@@ -1482,6 +1646,16 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
             reinterpret_cast<const float*>(W) + 4 * fw_plane, fw_plane, e.fw_mat, Tinv, N, k0, kb,
             nb, r0, want_grad ? 1 : 0, reinterpret_cast<float*>(F), fw_plane, e.fw_mat);
         SCA_LAUNCH_CHECK("split f");
+      } else if (piv_tc_prep) {
+        // F = M[:, K] T (rows above K; rows of K: -T) and L21 inv(L11) (rows below K) on the
+        // tensor cores: A = split pivot columns in the W planes, B = the planes k_tinv_warp wrote
+        const size_t tot = (size_t)(N - r0) * (nb / 4);
+        k_split_a<S><<<dim3((unsigned)((tot + 255) / 256), cnt), 256, 0, s>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, reinterpret_cast<float*>(W),
+            fw_plane, e.fw_mat, r0);
+        SCA_LAUNCH_CHECK("split a");
+        sca_status st = tc_prep_piv(e, m0, cnt, r0, k0, kb, want_grad, s);
+        if (st != SCA_OK) return st;
       } else {
         k_prep_f<S, C><<<dim3((N - r0 + 63) / 64, cnt), 256, 0, s>>>(
             M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, fw_plane, e.fw_mat,
@@ -1491,7 +1665,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
           want_grad ? 1 : 0, split, 0);
-      prof_end(e, kPrep, s);
+      prof_end(e, pivoted ? kPrepPiv : kPrep, s);
       SCA_LAUNCH_CHECK("prep");
     }
     const int ukind = pivoted ? kUpdatePiv : kUpdate;
@@ -1542,16 +1716,25 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
     const int np = std::max(0, std::min(cnt, e.piv_blocks - b0));
     const int nd = cnt - np;
     const bool fork = np > 0 && nd > 0 && e.side != nullptr;
-    cudaStream_t sp = s;
+    // with SM partitions the dominant group runs on its partition's stream (and W-plane
+    // stream), the pivoted group on the SMs left over
+    const bool parted = fork && e.dom != nullptr;
+    cudaStream_t sp = s, sd = s;
+    cudaStream_t aux_saved = e.aux;
     if (fork) {
+      sp = e.part_side ? e.part_side : e.side;
       if ((err = cudaEventRecord(e.ev_fork, s)) != cudaSuccess) return cuda_fail(err, "fork");
-      if ((err = cudaStreamWaitEvent(e.side, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "fork");
-      sp = e.side;
+      if ((err = cudaStreamWaitEvent(sp, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "fork");
+      if (parted) {
+        sd = e.dom;
+        if ((err = cudaStreamWaitEvent(sd, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "fork");
+      }
     }
     sca_status st;
     // While both groups run, the dominant group's persistent tensor-core launches leave
-    // sm_reserve SMs to the pivoted group's kernels.
-    e.tc_cap = 0;
+    // sm_reserve SMs to the pivoted group's kernels (with partitions: each group's
+    // tensor-core launches take one CTA per SM of its partition).
+    e.tc_cap = parted && e.part_side ? e.part_sms[0] : 0;
     const int span_p = np > 0 ? prof_span_begin(e, kSpanPiv, sp) : -1;
     if (np > 0) {
       NvtxRange range("sca.pivoted_group");
@@ -1559,22 +1742,32 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
         return st;
     }
     prof_span_end(e, span_p, sp);
-    if (fork && e.sm_reserve > 0 && e.tmap) e.tc_cap = tc_sms(e) - e.sm_reserve;
-    const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, s) : -1;
+    if (parted) {
+      e.tc_cap = e.part_sms[1];
+      if (e.aux) e.aux = e.part_aux;
+    } else if (fork && e.sm_reserve > 0 && e.tmap) {
+      e.tc_cap = tc_sms(e) - e.sm_reserve;
+    }
+    const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, sd) : -1;
     if (nd > 0) {
       NvtxRange range("sca.dominant_group");
-      st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, s);
+      st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, sd);
     }
     e.tc_cap = 0;
+    e.aux = aux_saved;
     if (st != SCA_OK) return st;
-    prof_span_end(e, span_d, s);
+    prof_span_end(e, span_d, sd);
     if (fork) {
       if (want_grad && refine_stage && !e.dos_mode) {  // each group refines its own blocks
         if ((st = launch_refine<S>(e, la, b0, 0, np, sp)) != SCA_OK) return st;
-        if ((st = launch_refine<S>(e, la, b0, np, nd, s)) != SCA_OK) return st;
+        if ((st = launch_refine<S>(e, la, b0, np, nd, sd)) != SCA_OK) return st;
       }
-      if ((err = cudaEventRecord(e.ev_join, e.side)) != cudaSuccess) return cuda_fail(err, "join");
+      if ((err = cudaEventRecord(e.ev_join, sp)) != cudaSuccess) return cuda_fail(err, "join");
       if ((err = cudaStreamWaitEvent(s, e.ev_join, 0)) != cudaSuccess) return cuda_fail(err, "join");
+      if (parted) {
+        if ((err = cudaEventRecord(e.ev_join2, sd)) != cudaSuccess) return cuda_fail(err, "join");
+        if ((err = cudaStreamWaitEvent(s, e.ev_join2, 0)) != cudaSuccess) return cuda_fail(err, "join");
+      }
     }
     if (want_grad && e.dos_mode) {
       prof_begin(e, kRefine, s);
@@ -1612,7 +1805,7 @@ sca_status set_smem_limits() {
   cudaError_t err;
   if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
   if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
-  if ((err = allow_max_smem(k_tinv_rows<S, C>)) != cudaSuccess) return cuda_fail(err, "smem tinv");
+  if ((err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024>)) != cudaSuccess) return cuda_fail(err, "smem tinv");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
   done = true;
   return SCA_OK;

@@ -72,6 +72,7 @@ struct Engine {
   void* W = nullptr;        // same, W^T
   void* Tinv = nullptr;     // chunk x 2 x nb x nb complex (compute type)
   float* tt = nullptr;      // chunk x 6 x nb x nb: -T^T split planes (tensor-core prep)
+  float* adiag = nullptr;   // chunk x N x 2: Re A_jj = mu - eps_j as a double-float pair
   int* piv = nullptr;       // chunk x N
   int* perm = nullptr;      // chunk x N
   int* flags = nullptr;     // 1 int: nonfinite / singular
@@ -97,6 +98,13 @@ struct Engine {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t aux = nullptr;       // the dominant group's W planes beside its pivot-block inverse
   cudaEvent_t ev_aux0 = nullptr, ev_aux1 = nullptr;
+  // SM partitions (green contexts, sca_partition.cu): the dominant group's streams run on
+  // part_sms[1] SMs; the pivoted group keeps part_sms[0] SMs to itself (part_side: a stream
+  // confined to them, else the ordinary side stream).
+  void* green[2] = {nullptr, nullptr};
+  cudaStream_t dom = nullptr, part_aux = nullptr, part_side = nullptr;
+  cudaEvent_t ev_join2 = nullptr;
+  int part_sms[2] = {0, 0};
   int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
   int tc_next = 0;
   int tc_cap = 0;                   // CTA cap of the next tensor-core launches (0: one per SM)
@@ -116,6 +124,8 @@ enum KernelKind {
   kFused,      // fused small-block Adam launch
   kSpanPiv,    // wall span of the pivoted group on its stream (fork to its last kernel)
   kSpanDom,    // wall span of the dominant group on the main stream (fork to its last kernel)
+  kPanelUpd,   // pivoted group: update of the rest of the outer panel after a sub-panel
+  kPrepPiv,    // pivoted group: rank-nb factors
   kKinds
 };
 
@@ -124,7 +134,7 @@ struct Profiler {
   bool on = false;
   double ms[kKinds] = {};
   uint64_t n[kKinds] = {};
-  struct Rec { int kind; cudaEvent_t a, b; };
+  struct Rec { int kind; cudaEvent_t a, b; cudaStream_t s; };
   Rec* recs = nullptr;
   int nrec = 0, cap = 0;
   cudaEvent_t* pool = nullptr;
@@ -146,6 +156,8 @@ void release(Engine& e);
 // Enqueue: evaluate every block for field d_phi; on return (asynchronous),
 // e.ld[b] holds ln|det A_b| and, if want_grad, e.gd[b*N+i] holds
 // sigma_b Re G_{b,ii}.
+bool partition_setup(Engine& e, int piv_sms, int mode);  // false: ordinary streams stay
+void partition_release(Engine& e);
 sca_status run_blocks(Engine& e, const double* d_phi, bool want_grad, cudaStream_t s,
                       bool refine_stage = true);
 
@@ -186,6 +198,9 @@ int tc_sms(const Engine& e);  // CTAs of an uncapped tensor-core launch (one per
 sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's launches  // tensor-core maps exist for the pivoted group's width
 // F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
+// the pivoted group's prep product (BF16x3): rows [r0, k0+kb) times T, rows below times inv(L)
+sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
+                       cudaStream_t s);
 // Prep product of the symmetric dominant blocks: F = S (W^T T) written as the four TF32
 // planes of F, with S = -1 on the swept rows (< k0) and the rows of K replaced by -T.
 sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,

@@ -75,12 +75,12 @@ extern "C" sca_status sca_grad_noalloc_dev(const sca_params* params, const doubl
   // Fixed part: status, Omega scratch, flags, ld (B), gd (B x N).
   const size_t fixed = al256(8 * sizeof(double)) * 2 + al256(16) + al256((size_t)e.B * 8) +
                        al256((size_t)e.B * e.N * 8);
-  // Per resident block: block planes, F, W, Tinv, piv, perm.
+  // Per resident block: block planes, F, W, Tinv, piv, perm, diagonal table.
   const size_t per_block = e.mat_stride * S + 2 * e.fw_mat * S + 2 * (size_t)e.nb * e.nb * 2 * S +
-                           2 * (size_t)e.N * sizeof(int);
+                           2 * (size_t)e.N * sizeof(int) + (size_t)e.N * 2 * sizeof(float);
   const size_t room = kScratchBytes > fixed ? kScratchBytes - fixed : 0;
-  // every array below is rounded up to 256 bytes: leave 6 x 256 bytes of slack per chunk
-  const long long fit = room > 6 * 256 ? (long long)((room - 6 * 256) / per_block) : 0;
+  // every array below is rounded up to 256 bytes: leave 7 x 256 bytes of slack per chunk
+  const long long fit = room > 7 * 256 ? (long long)((room - 7 * 256) / per_block) : 0;
   if (fit < 1) {
     set_error("sca_grad_noalloc_dev: problem too large for the " +
               std::to_string(kScratchBytes >> 20) + " MiB static workspace (needs " +
@@ -104,6 +104,7 @@ extern "C" sca_status sca_grad_noalloc_dev(const sca_params* params, const doubl
   e.piv = static_cast<int*>(take((size_t)e.chunk * e.N * sizeof(int)));
   e.perm = static_cast<int*>(take((size_t)e.chunk * e.N * sizeof(int)));
   e.Tinv = take((size_t)e.chunk * 2 * e.nb * e.nb * 2 * S);
+  e.adiag = static_cast<float*>(take((size_t)e.chunk * e.N * 2 * sizeof(float)));
   e.F = take((size_t)e.chunk * e.fw_mat * S);
   e.W = take((size_t)e.chunk * e.fw_mat * S);
   e.M = take((size_t)e.chunk * e.mat_stride * S);

@@ -653,6 +653,7 @@ struct TcMaps {
   CUtensorMap F, W;    // rank-nb factors, K extent nb
   CUtensorMap M;       // the blocks, for the epilogue
   CUtensorMap TT;      // -T^T split planes (nb x nb per block): B of F = M[:, K] T
+  CUtensorMap TL;      // -inv(L)^T bf16 planes of the pivoted group (second halves of TT's)
   CUtensorMap FP;      // planar F = M[:, K] T (W scratch planes 4, 5): output of that product
   CUtensorMap FO;      // the F planes themselves: split output of the symmetric prep product
   int sms = 0;
@@ -748,8 +749,12 @@ sca_status tc_prepare(Engine& e) {
     // F = M[:, K] T on the tensor cores: A = split pivot columns (W scratch planes 0-3, same
     // map as W), B = -T^T planes, output planar into W scratch planes 4, 5.
     const long long ztt = (long long)e.chunk * 6;
+    // bf16 planes fill half of a float plane slot: the pivoted group's -inv(L)^T planes sit
+    // in the second halves
+    float* tl = e.tt ? e.tt + (size_t)e.nb * e.nb / 2 : nullptr;
     bool ok = !e.tt ||
               (make_fw_map(&t->TT, e.tt, e.nb, e.nb, ztt, e.bf16) &&
+               (!e.bf16 || make_fw_map(&t->TL, tl, e.nb, e.nb, ztt, true)) &&
                make_m_map_rows(&t->FP, e.W, e.nb, e.N, e.nb, (long long)e.fw_plane, zf) &&
                make_m_map_rows(&t->FO, e.F, e.nb, e.N, e.nb, (long long)e.fw_plane, zf, e.bf16));
     if (!ok) {
@@ -935,6 +940,61 @@ sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, boo
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
+  return SCA_OK;
+}
+
+sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
+                       cudaStream_t s) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t || !e.tt || !e.bf16) {
+    set_error("pivoted tensor-core prep needs the BF16x3 planes");
+    return SCA_ENOSTATE;
+  }
+  const int kend = k0 + kb;
+  // rows [r0, kend) times T (rows of K: -T), then rows [max(r0, kend), N) times inv(L)
+  for (int part = 0; part < 2; ++part) {
+    const int ra = part == 0 ? r0 : std::max(r0, kend);
+    const int rb = part == 0 ? std::min(kend, e.N) : e.N;
+    if (rb <= ra) continue;
+    TcArgs a;
+    a.M = nullptr;
+    a.N = e.N;
+    a.ldm = e.nb;
+    a.mat_stride = 0;
+    a.plane_stride = 0;
+    a.nb = e.nb;
+    a.r0 = ra;
+    a.c0 = 0;
+    a.k0 = k0;
+    a.kb = kb;
+    a.gj = (gj && part == 0) ? 1 : 0;
+    a.tiles_m = (rb - ra + kBM - 1) / kBM;
+    a.tiles_n = (e.nb + kBNc - 1) / kBNc;
+    a.sym = 0;
+    a.per_block = a.tiles_m * a.tiles_n;
+    a.tiles = a.per_block * cnt;
+    a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W planes 0-3
+    a.wplanes = 6;                             // B: -T^T or -inv(L)^T planes
+    a.mat0 = m0;
+    a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: F planes 0-3
+    a.m_zoff = 0;
+    a.err = e.flags;
+    a.split_out = 1;
+    a.split_neg = 0;
+    a.T = static_cast<const float2*>(e.Tinv);
+    a.t_mat = 2ll * e.nb * e.nb;
+    if (e.tc_next >= kCounters) {
+      set_error("too many tensor-core launches in one pass");
+      return SCA_EINVAL;
+    }
+    a.counter = e.tc_counters + e.tc_next++;
+    const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
+    k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->W, part == 0 ? t->TT : t->TL, t->FO,
+                                                          a);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "tcgen05 pivoted prep launch");
+  }
   return SCA_OK;
 }
 

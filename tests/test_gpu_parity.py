@@ -361,11 +361,35 @@ def test_profile_kinds_and_group_spans():
     assert prof["span_pivoted"][1] == 1 and prof["span_dominant"][1] == 1
     assert prof["update"][1] == steps and prof["diag"][1] == steps
     assert prof["panel"][1] > 0 and prof["refine"][1] >= 2 and prof["reduce"][1] == 1
+    # 16-wide sub-panels: the rest of each outer panel is updated after every sub-panel
+    assert prof["panel_update"][1] > 0 and prof["prep_piv"][1] == steps
+    assert prof["trinv"][1] == steps
     for k in ("span_pivoted", "span_dominant", "update", "panel", "refine"):
         assert prof[k][0] > 0.0
     # spans contain the kernels of their group
     assert prof["span_dominant"][0] >= prof["update"][0]
     assert after == {k: (0.0, 0) for k in after}
+
+
+@pytest.mark.parametrize("mode", ["dominant", "both"])
+def test_sm_partition_leaves_results_unchanged(mode):
+    """SM partitions (green contexts) only move launches between SMs: Omega and the
+    gradient are bit-identical with and without them, and removing one restores the plain
+    streams."""
+    import torch
+    p = api.Params(20, 8, U=6.0, T=0.1, delta=0.5, prec="bf16x3")
+    phi = inputs.seed_phi(3, p.N)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with api.Context(p) as c:
+        assert c.sm_partition() == (0, 0)
+        om0, g0 = c.grad(phi)
+        ps, ds = c.set_sm_partition(16, mode)
+        assert ps >= 16 and ds > 0 and ps + ds <= sms
+        om1, g1 = c.grad(phi)
+        assert c.set_sm_partition(0) == (0, 0)
+        om2, g2 = c.grad(phi)
+    assert om1 == om0 and om2 == om0
+    assert np.array_equal(g1, g0) and np.array_equal(g2, g0)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
