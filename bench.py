@@ -131,10 +131,11 @@ TF32_OVER_BF16 = 1.1 / 2.25
 DEFAULT_PREC = "bf16x3"
 DEFAULT_SM_PARTITION = 0  # SMs kept free of the dominant group's launches (0: priorities only)
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over 8 update launches of a 16-block
-# 40x40 gradient, divided by 16; traffic grows with the blocks), per split precision, for the
-# kernel as captured (profiles/).  3xTF32: 434.0 MB per 16-block launch; BF16x3: 358.6 MB.
-UPDATE_BYTES_PER_BLOCK_N1600 = {"3xtf32": 434.0e6 / 16, "bf16x3": 358.6e6 / 16}
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 update launches of one
+# step of the 16-block workload ionic_40x40_w8, divided by 16; traffic grows with the blocks),
+# for the kernel as captured (profiles/): BF16x3 344.5 MB per 16-block launch.  3xTF32 has no
+# capture of the current kernel, so its traffic is reported as null.
+UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 344.5e6 / 16}
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 

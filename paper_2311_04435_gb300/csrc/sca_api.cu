@@ -123,7 +123,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   bytes += (size_t)e.chunk * e.mat_stride * S;           // blocks
   bytes += 2 * (size_t)e.chunk * e.fw_mat * S;            // F, W
   bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
-  if (e.tc) bytes += (size_t)e.chunk * 6 * e.nb * e.nb * 4;  // -T^T split planes
+  if (e.tc) bytes += (size_t)e.chunk * kTtPlanes * e.nb * e.nb * 4;  // -T^T split planes
   bytes += (size_t)e.chunk * e.N * 2 * sizeof(float);     // Re A_jj as double-float
   bytes += 2 * (size_t)e.chunk * e.N * sizeof(int);       // piv, perm
   bytes += (size_t)e.B * sizeof(double) * (3 + e.N);      // ld, d_z, tr, gd
@@ -179,7 +179,7 @@ sca_status allocate(Engine& e) {
   if (err == cudaSuccess) err = cudaMemset(e.F, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err == cudaSuccess) err = cudaMemset(e.W, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
-  if (e.tc) SCA_ALLOC(e.tt, (size_t)e.chunk * 6 * e.nb * e.nb * sizeof(float), "T planes");
+  if (e.tc) SCA_ALLOC(e.tt, (size_t)e.chunk * kTtPlanes * e.nb * e.nb * sizeof(float), "T planes");
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
 #undef SCA_ALLOC
   if ((st = fused_prepare(e)) != SCA_OK) { release(e); return st; }

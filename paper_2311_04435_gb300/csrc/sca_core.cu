@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
 // only the pivot row and column through shared memory.  ld[b] += sum ln|pivot| (the pivots of
 // the LU).  Writes T to Tinv slot 0 (nb x nb, zero padded) and, if TT != null, the split planes
 // of W_T[j][k] = -T[k][j] for the tensor-core product F = M[:, K] T
-// (planes re_hi, im_hi, re_lo, im_lo, -im_hi, -im_lo; kb x kb per block, K-contiguous).
+// (planes re_hi, im_hi, re_lo, im_lo; kb x kb per block, K-contiguous).
 template <typename S, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_stride,
                                                 size_t plane_stride, int k0, int kb, int nb,
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
   }
   cpx<C>* T = Tinv + (size_t)mat * 2 * nb * nb;
   const size_t P = (size_t)nb * nb;  // one plane of W_T (nb x nb, K-contiguous)
-  float* tt = TT ? TT + (size_t)mat * 6 * P : nullptr;
+  float* tt = TT ? TT + (size_t)mat * kTtPlanes * P : nullptr;
 #pragma unroll
   for (int q = 0; q < MAXR; ++q) {
     const int r = rg + q * RS;
@@ -395,15 +395,12 @@ __global__ void __launch_bounds__(NT) k_diag_gj(const S* M, int ldm, size_t mat_
       reinterpret_cast<__nv_bfloat16*>(tt + P)[o] = hi;
       reinterpret_cast<__nv_bfloat16*>(tt + 2 * P)[o] = lr;
       reinterpret_cast<__nv_bfloat16*>(tt + 3 * P)[o] = li;
-      reinterpret_cast<__nv_bfloat16*>(tt + 4 * P)[o] = __hneg(hi);
-      reinterpret_cast<__nv_bfloat16*>(tt + 5 * P)[o] = __hneg(li);
     } else if (tt) {  // W_T[j][r] = -T[r][j], split for TF32
       float* o = tt + (size_t)j * nb + r;
       const float fr = -(float)v.re, fi = -(float)v.im;
       const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
       const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
       o[0] = hr; o[P] = hi; o[2 * P] = fr - hr; o[3 * P] = fi - hi;
-      o[4 * P] = -hi; o[5 * P] = -(fi - hi);
     }
   }
 }
@@ -561,7 +558,7 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
   // W_T[j][r] = -T[r][j] in split planes, 16 rows j at a time through shared memory (the
   // owners of columns j deposit them, then every thread writes 4 consecutive r of one row)
   const size_t P = (size_t)nb * nb;
-  float* tt = TT + (size_t)mat * 6 * P;
+  float* tt = TT + (size_t)mat * kTtPlanes * P;
   cpx<float>(*S)[KB] = Ws;  // [16][KB]
   for (int jc0 = 0; jc0 < nb; jc0 += PW) {
     if ((unsigned)(j - jc0) < (unsigned)PW) {
@@ -582,31 +579,29 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
       for (int t = 0; t < 4; ++t) { fr[t] = -S[jj][r4 + t].re; fi[t] = -S[jj][r4 + t].im; }
       const size_t o = (size_t)jr * nb + r4;
       if (tt_bf16) {
-        __nv_bfloat16 h[6][4];
+        __nv_bfloat16 h[4][4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           h[0][t] = __float2bfloat16_rn(fr[t]);
           h[1][t] = __float2bfloat16_rn(fi[t]);
           h[2][t] = __float2bfloat16_rn(fr[t] - __bfloat162float(h[0][t]));
           h[3][t] = __float2bfloat16_rn(fi[t] - __bfloat162float(h[1][t]));
-          h[4][t] = __hneg(h[1][t]);
-          h[5][t] = __hneg(h[3][t]);
         }
 #pragma unroll
-        for (int pl = 0; pl < 6; ++pl)
+        for (int pl = 0; pl < 4; ++pl)
           *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(tt + pl * P) + o) =
               *reinterpret_cast<const uint2*>(h[pl]);
       } else {
-        float4 v[6];
+        float4 v[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const float hr = __uint_as_float(__float_as_uint(fr[t]) & 0xffffe000u);
           const float hi = __uint_as_float(__float_as_uint(fi[t]) & 0xffffe000u);
           (&v[0].x)[t] = hr; (&v[1].x)[t] = hi; (&v[2].x)[t] = fr[t] - hr;
-          (&v[3].x)[t] = fi[t] - hi; (&v[4].x)[t] = -hi; (&v[5].x)[t] = -(fi[t] - hi);
+          (&v[3].x)[t] = fi[t] - hi;
         }
 #pragma unroll
-        for (int pl = 0; pl < 6; ++pl) *reinterpret_cast<float4*>(tt + pl * P + o) = v[pl];
+        for (int pl = 0; pl < 4; ++pl) *reinterpret_cast<float4*>(tt + pl * P + o) = v[pl];
       }
     }
     __syncthreads();
@@ -706,10 +701,10 @@ __global__ void k_split_f(const float* Fp, size_t fp_plane, size_t fp_mat, const
 // so that M' = mask(M) - F W is one Gauss-Jordan sweep over K (mask zeroes row and column
 // block K) or, restricted to rows and columns past K, the LU Schur complement.
 // With `split`, planes are {re_hi, im_hi, re_lo, im_lo} (hi = value with the low 13 mantissa
-// bits cleared, exact in TF32; lo = value - hi) and W adds {-im_hi, -im_lo}.
+// bits cleared, exact in TF32; lo = value - hi), for F and W alike.
 template <typename S>
 __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, double vre, double vim,
-                                         int split, bool neg) {
+                                         int split) {
   if (!split) {
     base[off] = (S)vre;
     base[plane + off] = (S)vim;
@@ -725,10 +720,6 @@ __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, doub
     reinterpret_cast<__nv_bfloat16*>(b + plane)[off] = hi;
     reinterpret_cast<__nv_bfloat16*>(b + 2 * plane)[off] = lr;
     reinterpret_cast<__nv_bfloat16*>(b + 3 * plane)[off] = li;
-    if (neg) {
-      reinterpret_cast<__nv_bfloat16*>(b + 4 * plane)[off] = __hneg(hi);
-      reinterpret_cast<__nv_bfloat16*>(b + 5 * plane)[off] = __hneg(li);
-    }
   } else {
     const float fr = (float)vre, fi = (float)vim;
     const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
@@ -738,10 +729,6 @@ __device__ __forceinline__ void store_fw(S* base, size_t plane, size_t off, doub
     b[plane + off] = hi;
     b[2 * plane + off] = fr - hr;
     b[3 * plane + off] = fi - hi;
-    if (neg) {
-      b[4 * plane + off] = -hi;
-      b[5 * plane + off] = -(fi - hi);
-    }
   }
 }
 
@@ -832,7 +819,7 @@ __global__ void __launch_bounds__(256)
       } else {
         vr = (double)ar[a][q]; vi = (double)ai[a][q];
       }
-      store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split, false);
+      store_fw(out, fw_plane, (size_t)i * nb + c, vr, vi, split);
     }
   }
 }
@@ -941,12 +928,12 @@ __global__ void __launch_bounds__(NT)
   }
   if (!TT) return;
   // B operands of the tensor-core prep product F = M[:, K] X as bf16 split planes of -X^T
-  // (re_hi, im_hi, re_lo, im_lo, -im_hi, -im_lo; element [j][r] = -X[r][j]): X = T in the
-  // first half of each of the block's six float-plane slots, X = inv(L) in the second half.
+  // (re_hi, im_hi, re_lo, im_lo; element [j][r] = -X[r][j]): X = T in the
+  // first half of each of the block's float-plane slots, X = inv(L) in the second half.
   // The rows just written are read back through shared memory (the LU is no longer needed).
   __syncthreads();
   const size_t P = (size_t)nb * nb;
-  float* tt = TT + (size_t)mat * 6 * P;
+  float* tt = TT + (size_t)mat * kTtPlanes * P;
   cpx<C>* Sm = LU;  // [nb][nb + 1]
   for (int part = 0; part < 2; ++part) {
     const cpx<C>* src = part == 0 ? outT : outL;
@@ -958,7 +945,7 @@ __global__ void __launch_bounds__(NT)
     __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(tt + (part == 0 ? 0 : P / 2));
     for (int e = tid; e < nb * (nb / 4); e += NT) {
       const int jr = e / (nb / 4), r4 = (e - jr * (nb / 4)) * 4;
-      __nv_bfloat16 h[6][4];
+      __nv_bfloat16 h[4][4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const cpx<C> v = Sm[(size_t)(r4 + t) * (nb + 1) + jr];
@@ -967,12 +954,10 @@ __global__ void __launch_bounds__(NT)
         h[1][t] = __float2bfloat16_rn(fi);
         h[2][t] = __float2bfloat16_rn(fr - __bfloat162float(h[0][t]));
         h[3][t] = __float2bfloat16_rn(fi - __bfloat162float(h[1][t]));
-        h[4][t] = __hneg(h[1][t]);
-        h[5][t] = __hneg(h[3][t]);
       }
       const size_t o = (size_t)jr * nb + r4;
 #pragma unroll
-      for (int pl = 0; pl < 6; ++pl)
+      for (int pl = 0; pl < 4; ++pl)
         *reinterpret_cast<uint2*>(dst + 2 * pl * P + o) = *reinterpret_cast<const uint2*>(h[pl]);
     }
     __syncthreads();
@@ -1056,7 +1041,7 @@ __global__ void __launch_bounds__(256)
       vr = (double)tr[c * 65 + jj];
       vi = (double)ti[c * 65 + jj];
     }
-    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split, true);
+    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split);
   }
 }
 
@@ -1589,14 +1574,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_begin(e, kTrinv, s);
       const size_t smt = sizeof(cpx<C>) * std::max((size_t)kb * kb + kb, (size_t)nb * (nb + 1));
       constexpr int NT = sizeof(C) == 8 ? 512 : 1024;
-      float* TT = piv_tc_prep ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
+      float* TT = piv_tc_prep ? e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb : nullptr;
       k_tinv_warp<S, C, NT><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
                                                   nb, Tinv, TT);
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("pivot-block inverse");
     } else {
       prof_begin(e, kDiag, s);
-      float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * 6 * e.nb * e.nb : nullptr;
+      float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb : nullptr;
       if constexpr (sizeof(C) == 4) {
         k_diag_gjb<512><<<cnt, 512, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb,
                                             b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags);

@@ -116,6 +116,10 @@ struct Engine {
   int* h_flags = nullptr;           // pinned copy of the flags word
 };
 
+// Float-plane slots per block of the -T^T split planes (re_hi, im_hi, re_lo, im_lo; a bf16
+// plane fills the first half of its slot).
+constexpr int kTtPlanes = 4;
+
 // Kernel kinds for per-launch timing.
 enum KernelKind {
   kAssemble = 0, kPanel, kSwap, kTrinv, kPrep, kUpdate, kRefine, kReduce,

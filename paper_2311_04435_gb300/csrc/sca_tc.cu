@@ -3,14 +3,16 @@
 //
 //   M[i, j] <- mask(i, j) M[i, j] - sum_c F[i, c] W[j, c]          (complex, planar)
 //
-// Complex product as one real MMA of width 256: for a 128-row tile of F and a 128-column
-// tile of W, the 128 x 256 real tile [C_re | C_im] is
-//   F_re [W_re | W_im] + F_im [-W_im | W_re],
-// so the B operand of the first product is the 256-row stack (W_re; W_im) and that of the
-// second (-W_im; W_re).  Shared memory holds (-W_im, W_re, W_im) contiguously, and both stacks
-// are windows of it.  Each real product is split as hi*hi + hi*lo + lo*hi with hi = the value
-// truncated to TF32 and lo = value - hi (written by the prep kernel), i.e. 6 MMAs of
-// M=128, N=256, K=8 per K step.
+// Complex product in real MMAs: for a 128-row tile of F and a 128-column tile of W, the
+// 128 x 256 real tile [C_re | C_im] is
+//   F_re [W_re | W_im] + F_im [-W_im | W_re]:
+// the first term is one MMA of width 256 with the 256-row stack (W_re; W_im) as B (the two
+// planes sit next to each other in shared memory), the second two MMAs of width 128 into the
+// two halves of the accumulator, the one with W_im issued with A negated (instruction
+// descriptor bit 13), so no negated copy of W_im is stored or loaded.  Each real product is
+// split as hi*hi + hi*lo + lo*hi with hi = the value truncated to TF32 (or rounded to bf16)
+// and lo = value - hi (written by the prep kernels): 9 MMAs per K step (3 of N = 256, 6 of
+// N = 128), the tensor work of 6 at N = 256.
 //
 // Kernel structure (persistent, one CTA per SM, 192 threads):
 //   warp 0  : TMA producer (cp.async.bulk.tensor, 2-stage shared-memory ring, K = 16 per stage)
@@ -42,7 +44,7 @@ constexpr int kBNc = 128;          // complex W columns per tile (real MMA N = 2
 constexpr int kKS = 16;            // K per pipeline stage (SWIZZLE_64B rows of 64 bytes)
 constexpr int kStages = 2;
 constexpr int kTileBytes = kBM * kKS * 4;             // one 128 x 16 float plane: 8 KB
-constexpr int kStageBytes = 10 * kTileBytes;          // 4 F planes + 6 W planes: 80 KB
+constexpr int kStageBytes = 8 * kTileBytes;           // 4 F planes + 4 W planes: 64 KB
 constexpr int kEpiCols = 32;                          // complex columns per epilogue chunk
 constexpr int kEpiPlaneBytes = kBM * kEpiCols * 4;     // 128 x 32 floats, 16 KB
 constexpr int kEpiBufBytes = 2 * kEpiPlaneBytes;       // re + im planes
@@ -152,34 +154,29 @@ __device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::tf32, D = f32, A = B = tf32, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((256u >> 3) << 17) |
-                            ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+// Instruction descriptor of tcgen05.mma kind::f16 (A = B = bf16) or kind::tf32 (A = B = tf32):
+// D = f32, both operands K-major, M = 128, N = 256 or 128, A optionally negated (bit 13; the
+// imaginary-part products of the complex update).
+template <bool BF, bool N256, bool NEGA>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) | (NEGA ? (1u << 13) : 0u) |
+         (((N256 ? 256u : 128u) >> 3) << 17) | ((128u >> 4) << 24);
 }
-
-// kind::f16 with A = B = bf16, D = f32, both K-major, M = 128, N = 256 (BF16x3 path).
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
-                                ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdescBf16), "r"(acc));
-}
-
 template <bool BF>
-__device__ __forceinline__ void mma_split(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  if constexpr (BF) mma_bf16(d_tmem, a, b, acc);
-  else mma_tf32(d_tmem, a, b, acc);
+__device__ __forceinline__ void mma_d(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                      uint32_t acc) {
+  if constexpr (BF)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -253,13 +250,12 @@ __device__ __forceinline__ void decode_tile(const TcArgs& a, int t, int& mat, in
   tn = rem - i * (i + 1) / 2;
 }
 
-// Shared-memory stage layout (each slot one 128 x 16 float plane, 8 KB, 1024-aligned):
-//   0 F_re_hi  1 F_im_hi  2 F_re_lo  3 F_im_lo
-//   4 -W_im_hi 5 W_re_hi  6 W_im_hi  7 -W_im_lo 8 W_re_lo 9 W_im_lo
-// Global planes: F {0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo};
-//                W {0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo, 4 -im_hi, 5 -im_lo}.
+// Shared-memory stage layout (each slot one 128-row plane of 64-byte K rows, 8 KB,
+// 1024-aligned):
+//   0 F_re_hi  1 F_im_hi  2 F_re_lo  3 F_im_lo  4 W_re_hi  5 W_im_hi  6 W_re_lo  7 W_im_lo
+// Global planes: F and W {0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo}.
 __constant__ int kFPlaneOfSlot[4] = {0, 1, 2, 3};
-__constant__ int kWPlaneOfSlot[6] = {4, 0, 1, 5, 2, 3};
+__constant__ int kWPlaneOfSlot[4] = {0, 1, 2, 3};  // re_hi, im_hi, re_lo, im_lo
 
 // BF: the operand planes are bf16 (BF16x3 on kind::f16, 32 K-elements per 64-byte stage row)
 // instead of TF32-split float32 (16 per row); the stage layout in bytes is the same.
@@ -336,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int s = 0; s < 4; ++s)
             tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKE, frow,
                         (a.mat0 + mat) * a.fplanes + kFPlaneOfSlot[s]);
-          for (int s = 0; s < 6; ++s)
+          for (int s = 0; s < 4; ++s)
             tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKE, wrow,
                         (a.mat0 + mat) * a.wplanes + kWPlaneOfSlot[s]);
           last_parity[stage] = (int)phase;
@@ -379,17 +375,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t fi_hi = sdesc_k64(st + 1 * kTileBytes + off);
             const uint64_t fr_lo = sdesc_k64(st + 2 * kTileBytes + off);
             const uint64_t fi_lo = sdesc_k64(st + 3 * kTileBytes + off);
-            const uint64_t b2_hi = sdesc_k64(st + 4 * kTileBytes + off);  // (-W_im; W_re)
-            const uint64_t b1_hi = sdesc_k64(st + 5 * kTileBytes + off);  // (W_re; W_im)
-            const uint64_t b2_lo = sdesc_k64(st + 7 * kTileBytes + off);
-            const uint64_t b1_lo = sdesc_k64(st + 8 * kTileBytes + off);
+            // B slots: W_re_hi, W_im_hi, W_re_lo, W_im_lo; (W_re; W_im) is one 256-row operand
+            const uint64_t bre_hi = sdesc_k64(st + 4 * kTileBytes + off);
+            const uint64_t bim_hi = sdesc_k64(st + 5 * kTileBytes + off);
+            const uint64_t bre_lo = sdesc_k64(st + 6 * kTileBytes + off);
+            const uint64_t bim_lo = sdesc_k64(st + 7 * kTileBytes + off);
+            constexpr uint32_t kI256 = idesc<BF, true, false>();
+            constexpr uint32_t kI128 = idesc<BF, false, false>();
+            constexpr uint32_t kI128n = idesc<BF, false, true>();
+            const uint32_t d_im = d_tmem + (uint32_t)kBNc;  // imaginary half of the accumulator
             const uint32_t acc0 = (ks > 0 || k8 > 0) ? 1u : 0u;
-            mma_split<BF>(d_tmem, fr_hi, b1_hi, acc0);
-            mma_split<BF>(d_tmem, fr_hi, b1_lo, 1u);
-            mma_split<BF>(d_tmem, fr_lo, b1_hi, 1u);
-            mma_split<BF>(d_tmem, fi_hi, b2_hi, 1u);
-            mma_split<BF>(d_tmem, fi_hi, b2_lo, 1u);
-            mma_split<BF>(d_tmem, fi_lo, b2_hi, 1u);
+            // (re | im) += F_re (W_re; W_im)
+            mma_d<BF>(d_tmem, fr_hi, bre_hi, kI256, acc0);
+            mma_d<BF>(d_tmem, fr_hi, bre_lo, kI256, 1u);
+            mma_d<BF>(d_tmem, fr_lo, bre_hi, kI256, 1u);
+            // re += (-F_im) W_im, im += F_im W_re
+            mma_d<BF>(d_tmem, fi_hi, bim_hi, kI128n, 1u);
+            mma_d<BF>(d_im, fi_hi, bre_hi, kI128, 1u);
+            mma_d<BF>(d_tmem, fi_hi, bim_lo, kI128n, 1u);
+            mma_d<BF>(d_im, fi_hi, bre_lo, kI128, 1u);
+            mma_d<BF>(d_tmem, fi_lo, bim_hi, kI128n, 1u);
+            mma_d<BF>(d_im, fi_lo, bre_hi, kI128, 1u);
           }
           mma_commit(&empty[stage]);  // frees the stage once these MMAs have read it
           if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -748,7 +754,7 @@ sca_status tc_prepare(Engine& e) {
   {
     // F = M[:, K] T on the tensor cores: A = split pivot columns (W scratch planes 0-3, same
     // map as W), B = -T^T planes, output planar into W scratch planes 4, 5.
-    const long long ztt = (long long)e.chunk * 6;
+    const long long ztt = (long long)e.chunk * kTtPlanes;
     // bf16 planes fill half of a float plane slot: the pivoted group's -inv(L)^T planes sit
     // in the second halves
     float* tl = e.tt ? e.tt + (size_t)e.nb * e.nb / 2 : nullptr;
@@ -872,7 +878,7 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   a.per_block = a.tiles_m * a.tiles_n;
   a.tiles = a.per_block * cnt;
   a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W scratch planes 0-3
-  a.wplanes = 6;                             // B: -T^T planes
+  a.wplanes = kTtPlanes;                           // B: -T^T planes
   a.mat0 = m0;
   a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: W scratch planes 4, 5
   a.m_zoff = 4;
@@ -919,7 +925,7 @@ sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, boo
   a.per_block = a.tiles_m * a.tiles_n;
   a.tiles = a.per_block * cnt;
   a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W planes 0-3 (re_hi, im_hi, re_lo, im_lo)
-  a.wplanes = 6;                             // B: -T^T planes
+  a.wplanes = kTtPlanes;                           // B: -T^T planes
   a.mat0 = m0;
   a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: F planes 0-3
   a.m_zoff = 0;
@@ -974,7 +980,7 @@ sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool 
     a.per_block = a.tiles_m * a.tiles_n;
     a.tiles = a.per_block * cnt;
     a.fplanes = (int)(e.fw_mat / e.fw_plane);  // A: W planes 0-3
-    a.wplanes = 6;                             // B: -T^T or -inv(L)^T planes
+    a.wplanes = kTtPlanes;                           // B: -T^T or -inv(L)^T planes
     a.mat0 = m0;
     a.m_zmul = (int)(e.fw_mat / e.fw_plane);   // output: F planes 0-3
     a.m_zoff = 0;

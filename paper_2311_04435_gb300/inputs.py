@@ -97,6 +97,10 @@ WORKLOADS = {
                             note="128 complex 4096x4096 blocks"),
     # 16x16 rerun of the 64x64 parameters (oracle-sized)
     "ionic_16x16_rerun": Workload("ionic_16x16_rerun", 16, 6.0, 0.5, 0.2, 64),
+    # profiling case of the dominant kernels: the 40x40 lattice at T = 1.5 with 8 frequencies
+    # -> 16 blocks of 1600x1600 (328 MB, above the L2), all diagonally dominant (w_0 > 4t)
+    "ionic_40x40_w8": Workload("ionic_40x40_w8", 40, 4.0, 1.0, 1.5, 8,
+                               note="16 complex 1600x1600 blocks, none pivoted"),
 }
 
 
