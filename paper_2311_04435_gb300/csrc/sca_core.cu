@@ -996,52 +996,115 @@ __global__ void __launch_bounds__(256)
         *reinterpret_cast<const uint2*>(h[pl]);
 }
 
-// W^T: 64 columns j x nb per CTA, transposed through shared memory.
+// Eight consecutive entries of the F/W planes starting at element o (8-aligned): re/im planes
+// of S (split 0; only the first n entries), TF32-split float planes (1) or bf16-split planes
+// (2), {re_hi, im_hi, re_lo, im_lo} for both splits (row length a multiple of 8 there).
+template <typename S>
+__device__ __forceinline__ void store_fw8(S* base, size_t plane, size_t o, const float* vr,
+                                          const float* vi, const S* dr, const S* di, int split,
+                                          int n) {
+  if (split == 2) {
+    __nv_bfloat16 h[4][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      h[0][e] = __float2bfloat16_rn(vr[e]);
+      h[1][e] = __float2bfloat16_rn(vi[e]);
+      h[2][e] = __float2bfloat16_rn(vr[e] - __bfloat162float(h[0][e]));
+      h[3][e] = __float2bfloat16_rn(vi[e] - __bfloat162float(h[1][e]));
+    }
+    float* b = reinterpret_cast<float*>(base);
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl)
+      *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(b + pl * plane) + o) =
+          *reinterpret_cast<const uint4*>(h[pl]);
+  } else if (split == 1) {
+    float f[4][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float hr = __uint_as_float(__float_as_uint(vr[e]) & 0xffffe000u);
+      const float hi = __uint_as_float(__float_as_uint(vi[e]) & 0xffffe000u);
+      f[0][e] = hr; f[1][e] = hi; f[2][e] = vr[e] - hr; f[3][e] = vi[e] - hi;
+    }
+    float* b = reinterpret_cast<float*>(base);
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) {
+      float4* d = reinterpret_cast<float4*>(b + pl * plane + o);
+      d[0] = make_float4(f[pl][0], f[pl][1], f[pl][2], f[pl][3]);
+      d[1] = make_float4(f[pl][4], f[pl][5], f[pl][6], f[pl][7]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (e < n) {
+        base[o + e] = dr[e];
+        base[plane + o + e] = di[e];
+      }
+    }
+  }
+}
+
+// W^T: 64 columns j x nb per CTA.  Columns past K of a symmetric block come from the column
+// strip M[j][K] (the upper entries M[K][j] are the transposed lower ones, both unswept) and
+// are copied row by row; the others come from the row strip M[K][j] and are transposed
+// through shared memory.  Each thread converts and writes 8 consecutive entries of a W^T row.
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_prep_w(const S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
              int nb, S* W, size_t fw_plane, size_t fw_mat, int c_begin, int gj, int split,
              int sym) {
   extern __shared__ unsigned char smem_raw[];
-  S* tr = reinterpret_cast<S*>(smem_raw);  // [nb][65]
-  S* ti = tr + (size_t)nb * 65;
+  const int ts = nb + 4;                    // shared row stride (16-byte aligned rows)
+  S* tr = reinterpret_cast<S*>(smem_raw);   // [64][ts]
+  S* ti = tr + (size_t)64 * ts;
   const int mat = blockIdx.y;
   const int j0 = c_begin + blockIdx.x * 64;
   const S* re = M + mat * mat_stride;
   const S* im = re + plane_stride;
-  if (sym && j0 >= k0 + kb) {
-    // columns past K sit in upper tiles: M[K][j] = M[j][K] (both unswept)
-    for (int e = threadIdx.x; e < nb * 64; e += 256) {
-      const int jj = e / nb, c = e - jj * nb;
-      const int j = j0 + jj;
-      const bool in = c < kb && j < N;
-      tr[c * 65 + jj] = in ? re[(size_t)j * ldm + k0 + c] : (S)0;
-      ti[c * 65 + jj] = in ? im[(size_t)j * ldm + k0 + c] : (S)0;
-    }
-  } else {
+  const bool direct = sym && j0 >= k0 + kb;
+  if (!direct) {
     for (int e = threadIdx.x; e < nb * 64; e += 256) {
       const int c = e >> 6, jj = e & 63;
       const int j = j0 + jj;
       const bool in = c < kb && j < N;
-      tr[c * 65 + jj] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
-      ti[c * 65 + jj] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+      tr[jj * ts + c] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
+      ti[jj * ts + c] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
     }
+    __syncthreads();
   }
-  __syncthreads();
   S* out = W + (size_t)mat * fw_mat;
-  for (int e = threadIdx.x; e < nb * 64; e += 256) {
-    const int jj = e / nb, c = e - jj * nb;
+  const int g8 = (nb + 7) / 8;  // the split planes have nb = 128; plain ones may be narrower
+  for (int e = threadIdx.x; e < 64 * g8; e += 256) {
+    const int jj = e / g8, c8 = (e - jj * g8) * 8;
     const int j = j0 + jj;
     if (j >= N) continue;
-    double vr, vi;
+    S dr[8], di[8];
     if (gj && j >= k0 && j < k0 + kb) {
-      vr = (c == j - k0) ? 1.0 : 0.0;
-      vi = 0.0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        dr[t] = (c8 + t == j - k0) ? (S)1 : (S)0;
+        di[t] = (S)0;
+      }
+    } else if (direct) {
+      const S* rr = re + (size_t)j * ldm + k0 + c8;
+      const S* ri = im + (size_t)j * ldm + k0 + c8;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const bool in = c8 + t < kb;
+        dr[t] = in ? rr[t] : (S)0;
+        di[t] = in ? ri[t] : (S)0;
+      }
     } else {
-      vr = (double)tr[c * 65 + jj];
-      vi = (double)ti[c * 65 + jj];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const bool in = c8 + t < nb;
+        dr[t] = in ? tr[jj * ts + c8 + t] : (S)0;
+        di[t] = in ? ti[jj * ts + c8 + t] : (S)0;
+      }
     }
-    store_fw(out, fw_plane, (size_t)j * nb + c, vr, vi, split);
+    float vr[8], vi[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) { vr[t] = (float)dr[t]; vi[t] = (float)di[t]; }
+    store_fw8(out, fw_plane, (size_t)j * nb + c8, vr, vi, dr, di, split, nb - c8);
   }
 }
 
@@ -1559,7 +1622,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       if (err == cudaSuccess) err = cudaStreamWaitEvent(e.aux, e.ev_aux0, 0);
       if (err != cudaSuccess) return cuda_fail(err, "aux fork");
       const int cw = want_grad ? 0 : kend;
-      const size_t smw = 2 * sizeof(S) * (size_t)nb * 65;
+      const size_t smw = 2 * sizeof(S) * (size_t)64 * (nb + 4);
       prof_begin(e, kPrep, e.aux);
       k_prep_w<S><<<dim3((N - cw + 63) / 64, cnt), 256, smw, e.aux>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, cw,
@@ -1602,7 +1665,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
         cudaError_t err = cudaStreamWaitEvent(s, e.ev_aux1, 0);
         if (err != cudaSuccess) return cuda_fail(err, "aux join");
       } else {
-        const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
+        const size_t sm = 2 * sizeof(S) * (size_t)64 * (nb + 4);
         prof_begin(e, kPrep, s);
         k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
             M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
@@ -1646,7 +1709,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
             M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, Tinv, F, fw_plane, e.fw_mat,
             r0, want_grad ? 1 : 0, pivoted ? 1 : 0, split);
       }
-      const size_t sm = 2 * sizeof(S) * (size_t)nb * 65;
+      const size_t sm = 2 * sizeof(S) * (size_t)64 * (nb + 4);
       k_prep_w<S><<<dim3((N - c0 + 63) / 64, cnt), 256, sm, s>>>(
           M, N, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb, W, fw_plane, e.fw_mat, c0,
           want_grad ? 1 : 0, split, 0);
