@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
   constexpr int MAXR = (KB + RS - 1) / RS;
   __shared__ cpx<float> Ms[KB][PW + 1];  // M[:, P], then F in place
   __shared__ cpx<float> Ws[PW][KB];      // W = M[P, :]
-  __shared__ cpx<float> Tp[PW][PW + 1];  // inv(M_PP), in place
+  __shared__ cpx<float> Tb[2][PW][PW + 1];  // inv(M_PP): Gauss-Jordan ping-pong, result in [0]
+  cpx<float>(*Tp)[PW + 1] = Tb[0];
   __shared__ double piv2[KB];
   const int mat = blockIdx.x, tid = threadIdx.x;
   const int j = tid % KB, rg = tid / KB;
@@ -452,38 +453,42 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
         Ws[r - p0][j] = jP ? cpx<float>{(j == r) ? 1.f : 0.f, 0.f} : a[q];
     }
     __syncthreads();
-    // (b) one warp: inv(M_PP) by Gauss-Jordan; lane owns column lane % 16, rows lane / 16 + 2m
-    if (tid < 32) {
+    // (b) four warps: inv(M_PP) by Gauss-Jordan; thread owns column tid % 16 of rows
+    // tid / 16 and tid / 16 + 8, reading one buffer and writing the other (one barrier of the
+    // four warps per pivot)
+    if (tid < 128) {
       const int cl = tid & 15, r0 = tid >> 4;
-      for (int m = 0; m < 8; ++m) Tp[r0 + 2 * m][cl] = Ms[p0 + r0 + 2 * m][cl];
-      __syncwarp();
+      Tb[0][r0][cl] = Ms[p0 + r0][cl];
+      Tb[0][r0 + 8][cl] = Ms[p0 + r0 + 8][cl];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll 1
       for (int cc = 0; cc < PW; ++cc) {
-        const cpx<float> d = Tp[cc][cc];
+        const cpx<float>(*src)[PW + 1] = Tb[cc & 1];
+        cpx<float>(*dst)[PW + 1] = Tb[(cc & 1) ^ 1];
+        const cpx<float> d = src[cc][cc];
         const float m2 = d.re * d.re + d.im * d.im;
         const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
         const cpx<float> dinv = {d.re * rm, -d.im * rm};
         if (tid == 0) piv2[p0 + cc] = (double)d.re * d.re + (double)d.im * d.im;
-        const cpx<float> pr = Tp[cc][cl];  // pivot row, this lane's column
-        cpx<float> nv[8];
+        const cpx<float> pr = src[cc][cl];  // pivot row, this thread's column
+        const cpx<float> u = cmul(pr, dinv);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int r = r0 + 2 * m;
-          const cpx<float> pc = Tp[r][cc];  // pivot column, this row
-          const cpx<float> t = Tp[r][cl];
+        for (int m = 0; m < 2; ++m) {
+          const int r = r0 + 8 * m;
+          const cpx<float> pc = src[r][cc];  // pivot column, this row
+          const cpx<float> t = src[r][cl];
+          cpx<float> nv;
           if (r == cc) {
-            nv[m] = (cl == cc) ? dinv : cmul(t, dinv);
+            nv = (cl == cc) ? dinv : cmul(t, dinv);
           } else if (cl == cc) {
             const cpx<float> q2 = cmul(pc, dinv);
-            nv[m] = {-q2.re, -q2.im};
+            nv = {-q2.re, -q2.im};
           } else {
-            const cpx<float> u = cmul(pr, dinv);
-            nv[m] = {t.re - (pc.re * u.re - pc.im * u.im), t.im - (pc.re * u.im + pc.im * u.re)};
+            nv = {t.re - (pc.re * u.re - pc.im * u.im), t.im - (pc.re * u.im + pc.im * u.re)};
           }
+          dst[r][cl] = nv;
         }
-        __syncwarp();
-#pragma unroll
-        for (int m = 0; m < 8; ++m) Tp[r0 + 2 * m][cl] = nv[m];
-        __syncwarp();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     }
     __syncthreads();
