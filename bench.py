@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--dos-points", type=int, default=128,
                     help="real frequencies of the timed density of states (0 = skip)")
     ap.add_argument("--sm-partition", type=int, default=DEFAULT_SM_PARTITION,
-                    help="SMs kept free of the dominant group's launches (0 = none)")
+                    help="SMs kept free of the dominant group's launches (0 = none, "
+                         "-1 = the library's default for the problem)")
     ap.add_argument("--metro-steps", type=int, default=10,
                     help="timed Metropolis steps (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
@@ -129,7 +130,7 @@ def peaks():
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
 DEFAULT_PREC = "bf16x3"
-DEFAULT_SM_PARTITION = 0  # SMs kept free of the dominant group's launches (0: priorities only)
+DEFAULT_SM_PARTITION = -1  # the library's default (8 SMs for 1024 <= N <= 2048, >= 64 dominant blocks)
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 update launches of one
 # step of the 16-block workload ionic_40x40_w8, divided by 16; traffic grows with the blocks),
@@ -228,7 +229,8 @@ def run_ours(args):
     # ---------------- device-resident timing (inputs resident in HBM)
     ctx = api.Context(params)
     ctx.set_stream(stream)
-    partition = list(ctx.set_sm_partition(args.sm_partition)) if args.sm_partition else [0, 0]
+    partition = list(ctx.set_sm_partition(args.sm_partition) if args.sm_partition >= 0
+                     else ctx.sm_partition())
     ctx.adam_init(adam)
     ctx.adam_step(args.warmup)
     l0 = api.kernel_launches()
@@ -273,7 +275,7 @@ def run_ours(args):
     phi0 = np.ascontiguousarray(inputs.seed_phi(wl.seed, params.N))
     ctx2 = api.Context(params)
     ctx2.set_stream(stream)
-    if args.sm_partition:
+    if args.sm_partition >= 0:
         ctx2.set_sm_partition(args.sm_partition)
     ctx2.adam_init(adam, phi0)
     ctx2.adam_step(max(1, args.warmup))

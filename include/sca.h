@@ -322,8 +322,10 @@ sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
  * `pivoted_sms` SMs (rounded up by the driver to its granularity, 8 on this GPU), so the
  * pivoted chain never waits for a dominant CTA to leave an SM.  Modes: 1 the pivoted group
  * may still use any SM (highest stream priority), 2 it is confined to its own set as well.
- * pivoted_sms = 0 removes the partition (the default: the dominant group's persistent
- * tensor-core launches then leave 8 SMs free, and priorities do the rest).  Needs the
+ * pivoted_sms = 0 removes the partition (the dominant group's persistent tensor-core launches
+ * then leave 8 SMs free, and priorities do the rest).  Contexts with 1024 <= N <= 2048 and at
+ * least 64 dominant blocks start with a partition of 8 SMs in mode 1 when the driver grants it.
+ * Needs the
  * tensor-core path; results do not depend on the partition (tile order and reductions are
  * fixed).  SCA_ECUDA when the driver refuses the partition; the context then keeps its
  * ordinary streams.  sca_sm_partition reports the SM counts in use (0, 0 without one). */

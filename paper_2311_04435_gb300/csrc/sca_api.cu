@@ -24,6 +24,12 @@ thread_local std::string t_err;
 // SMs the dominant group's persistent tensor-core launches leave free while the pivoted
 // group runs beside them on its own (high-priority) stream.
 constexpr int kDefaultSmReserve = 8;
+// Problems with 1024 <= N <= 2048 and at least 64 dominant blocks start with an SM partition
+// that keeps the dominant group's launches off this many SMs (sca_set_sm_partition changes
+// it): the dominant group keeps the 144 SMs its persistent launches use anyway, and the
+// pivoted chain's 8 SMs no longer fill up with the dominant group's other kernels.  At larger
+// N the dominant group's work dwarfs the chain and the partition only costs.
+constexpr int kDefaultPartitionSms = 8;
 }
 
 void set_error(const std::string& msg) { t_err = msg; }
@@ -202,6 +208,8 @@ sca_status allocate(Engine& e) {
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }
   err = cudaEventCreateWithFlags(&e.ev_join2, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "join event"); }
+  if (e.tc && e.piv_blocks > 0 && e.N >= 1024 && e.N <= 2048 && e.B - e.piv_blocks >= 64)
+    (void)partition_setup(e, kDefaultPartitionSms, 1);  // ordinary streams if refused
   return SCA_OK;
 }
 

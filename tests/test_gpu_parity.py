@@ -87,6 +87,25 @@ def test_larger_block_20x20_matches_oracle(prec):
     assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+def test_many_dominant_blocks_match_oracle(prec):
+    """80 blocks of 256 x 256 (12 pivoted, 68 dominant): Omega (gradient and LU-only passes)
+    and the gradient match the oracle, and a repeated evaluation is bit-identical."""
+    p = api.Params(16, 40, U=4.0, T=0.1, delta=0.5, prec=prec)
+    assert 2 * p.n_omega - api.pivoted_blocks(p) >= 64
+    phi = inputs.seed_phi(5, p.N)
+    with api.Context(p) as c:
+        om, g = c.grad(phi)
+        om2, g2 = c.grad(phi)
+        om_lu = c.potential(phi)
+    o_om, o_g = oracle.omega_grad(oparams(p), phi)
+    t = tol(prec)
+    assert om == pytest.approx(o_om, rel=t["om"])
+    assert om_lu == pytest.approx(o_om, rel=t["om"])
+    assert np.max(np.abs(g - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
+    assert om2 == om and np.array_equal(g2, g)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_disorder_site_energy_and_half_convention(prec):
     p = api.Params(6, 6, U=3.0, T=0.2, delta=0.9, prec=prec, ionic="half")
