@@ -67,6 +67,47 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
   if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
 }
 
+// Zero fill and assembly in one pass, one warp per row (16-byte zero stores): blocks
+// [0, full_blocks) get whole rows; the later ones (symmetric dominant blocks, lower tiles
+// only) get the columns up to the end of the row's diagonal tile of width `tile`: their
+// strictly upper tiles are never read before k_mirror overwrites them.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_assemble_rows(S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0, Lattice la0,
+                    double* ld, int* perm, int full_blocks, int tile) {
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
+  const int N = la.N, L = la.L;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i < N) {
+    const int end = mat < full_blocks ? N : min(N, (i / tile + 1) * tile);
+    S* rr = M + mat * mat_stride + (size_t)i * ldm;
+    S* ri = rr + plane_stride;
+    constexpr int V = 16 / (int)sizeof(S);  // N and the tile width are multiples of V
+    for (int c = lane * V; c < end; c += 32 * V) {
+      *reinterpret_cast<uint4*>(rr + c) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(ri + c) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const double w = la.zshift ? la.zshift[2 * n + 1] : (2.0 * n + 1.0) * kPi * la.T;
+      const double zr = la.zshift ? la.zshift[2 * n] : la.mu;
+      const int x = i / L, y = i - x * L;
+      const int nbr[4] = {((x + 1) % L) * L + y, ((x + L - 1) % L) * L + y, x * L + (y + 1) % L,
+                          x * L + (y + L - 1) % L};
+      // bonds accumulate: for L = 2 the +x and -x neighbours are the same site
+      for (int k = 0; k < 4; ++k)
+        if (nbr[k] < end) rr[nbr[k]] += (S)la.t;
+      rr[i] = (S)(zr - site_energy(la, i, sg));
+      ri[i] = (S)w;
+      perm[(size_t)mat * N + i] = i;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ld[b] = 0.0;
+}
+
 // --------------------------------------------------------- panel-local update
 // Two-level blocking of the pivoted group: an outer panel of width kbo is factorised by
 // shared-memory sub-panels of width kbi; after each sub-panel [s0, s0+kbi) the rest of the outer
@@ -647,9 +688,13 @@ __global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size
 template <typename S>
 __global__ void k_mirror(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride) {
   __shared__ S tr[32][33], ti[32][33];
-  const int mat = blockIdx.z;
-  const int bi = blockIdx.y, bj = blockIdx.x;  // destination tile (bi, bj), bi <= bj
-  if (bi > bj) return;
+  const int mat = blockIdx.y;
+  // destination tile (bi, bj), bi <= bj, from the linear index t = bj (bj + 1) / 2 + bi
+  const int t = blockIdx.x;
+  int bj = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+  while (bj * (bj + 1) / 2 > t) --bj;
+  const int bi = t - bj * (bj + 1) / 2;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -1737,7 +1782,8 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   if (sym && want_grad) {  // the fully swept inverse is symmetric: fill the upper tiles
     const int nt = (N + 31) / 32;
     prof_begin(e, kPrep, s);
-    k_mirror<S><<<dim3(nt, nt, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride);
+    k_mirror<S><<<dim3(nt * (nt + 1) / 2, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
+                                                             e.plane_stride);
     prof_end(e, kPrep, s);
     SCA_LAUNCH_CHECK("mirror");
   }
@@ -1752,13 +1798,16 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
   S* M = static_cast<S*>(e.M);
   cudaError_t err = cudaMemsetAsync(e.flags, 0, sizeof(int), s);
   if (err != cudaSuccess) return cuda_fail(err, "flags reset");
+  // dominant blocks on the tensor cores are eliminated symmetrically (lower tiles only)
+  bool sym_dom = e.tc && e.tt != nullptr && e.nb % 4 == 0;
+  if (const char* v = std::getenv("SCA_SYM"))
+    if (std::atoi(v) == 0) sym_dom = false;
   for (int b0 = 0; b0 < e.B; b0 += e.chunk) {
     const int cnt = std::min(e.chunk, e.B - b0);
+    const int npiv = std::max(0, std::min(cnt, e.piv_blocks - b0));
     prof_begin(e, kAssemble, s);
-    err = cudaMemsetAsync(M, 0, (size_t)cnt * e.mat_stride * sizeof(S), s);
-    if (err != cudaSuccess) return cuda_fail(err, "assemble zero fill");
-    k_assemble<S><<<dim3((N + 127) / 128, cnt), 128, 0, s>>>(M, e.ldm, e.mat_stride,
-                                                              e.plane_stride, b0, la, e.ld, e.perm);
+    k_assemble_rows<S><<<dim3((N + 7) / 8, cnt), 256, 0, s>>>(
+        M, e.ldm, e.mat_stride, e.plane_stride, b0, la, e.ld, e.perm, sym_dom ? npiv : cnt, e.nb);
     prof_end(e, kAssemble, s);
     SCA_LAUNCH_CHECK("assemble");
     if (e.tc) {
