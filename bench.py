@@ -134,9 +134,8 @@ DEFAULT_SM_PARTITION = -1  # the library's default (8 SMs for 1024 <= N <= 2048,
 # DRAM traffic of one symmetric dominant-group update launch, per block (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 update launches of one
 # step of the 16-block workload ionic_40x40_w8, divided by 16; traffic grows with the blocks),
-# for the kernel as captured (profiles/): BF16x3 344.5 MB per 16-block launch.  3xTF32 has no
-# capture of the current kernel, so its traffic is reported as null.
-UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 344.5e6 / 16}
+# for the kernel as captured (profiles/): BF16x3 344.5 MB, 3xTF32 404.0 MB per 16-block launch.
+UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 344.5e6 / 16, "3xtf32": 404.0e6 / 16}
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
