@@ -245,15 +245,9 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     P[r * ps + c] = {(C)re[o], (C)im[o]};
   }
   __syncthreads();
-  for (int c = 0; c < kb; ++c) {
-    // |z|^2 in the compute type: the pivot is the stored entry of largest modulus
-    C best = (C)-1;
-    int bi = m;
-    for (int r = c + tid; r < m; r += NT) {
-      const cpx<C> z = P[r * ps + c];
-      const C v = z.re * z.re + z.im * z.im;
-      if (v > best) { best = v; bi = r; }
-    }
+  // argmax of |z|^2 over rows >= c of column c: thread-local candidates, then warp shuffles,
+  // then every warp reduces the per-warp winners itself (no broadcast barrier)
+  auto pick = [&](C best, int bi, int c) -> int {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const C ov = __shfl_down_sync(0xffffffffu, best, off);
@@ -262,19 +256,26 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     }
     if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
     __syncthreads();
-    if (warp == 0) {
-      best = (lane < NT / 32) ? red_v[lane] : (C)-1;
-      bi = (lane < NT / 32) ? red_i[lane] : m;
+    best = (lane < NT / 32) ? red_v[lane] : (C)-1;
+    bi = (lane < NT / 32) ? red_i[lane] : m;
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const C ov = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) s_p = (bi < m) ? bi : c;
+    for (int off = 16; off > 0; off >>= 1) {
+      const C ov = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    __syncthreads();
-    const int p = s_p;
+    return bi < m ? bi : c;
+  };
+  C best = (C)-1;
+  int bi = m;
+  for (int r = tid; r < m; r += NT) {
+    const cpx<C> z = P[r * ps];
+    const C v = z.re * z.re + z.im * z.im;
+    if (v > best) { best = v; bi = r; }
+  }
+  int p = pick(best, bi, 0);
+  for (int c = 0; c < kb; ++c) {
+    // red_v / red_i are read by every warp above; the next writes come after a barrier
     if (p != c)
       for (int j = tid; j < kb; j += NT) {
         const cpx<C> t = P[c * ps + j];
@@ -290,6 +291,9 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     const C m2 = d.re * d.re + d.im * d.im;
     const cpx<C> inv = (m2 > (C)0) ? cpx<C>{d.re / m2, -d.im / m2} : cpx<C>{(C)0, (C)0};
     if (tid == 0) piv2[c] = (double)d.re * d.re + (double)d.im * d.im;
+    // eliminate below the pivot; the new column c+1 feeds the next pivot search
+    best = (C)-1;
+    bi = m;
     for (int r = c + 1 + tid; r < m; r += NT) {
       const cpx<C> l = cmul(P[r * ps + c], inv);
       P[r * ps + c] = l;
@@ -298,8 +302,17 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
         P[r * ps + j].re -= l.re * u.re - l.im * u.im;
         P[r * ps + j].im -= l.re * u.im + l.im * u.re;
       }
+      if (c + 1 < kb) {
+        const cpx<C> z = P[r * ps + c + 1];
+        const C v = z.re * z.re + z.im * z.im;
+        if (v > best) { best = v; bi = r; }
+      }
     }
-    __syncthreads();
+    if (c + 1 < kb) {
+      p = pick(best, bi, c + 1);
+    } else {
+      __syncthreads();
+    }
   }
   for (int e = tid; e < m * kb; e += NT) {
     const int r = e / kb, c = e - r * kb;
