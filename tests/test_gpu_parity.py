@@ -390,6 +390,35 @@ def test_profile_kinds_and_group_spans():
     assert after == {k: (0.0, 0) for k in after}
 
 
+def test_profile_timeline_file(tmp_path, monkeypatch):
+    """SCA_PROFILE_TRACE: every profiled launch of a call appears in the timeline file with its
+    kind, stream, start and duration; the per-kind totals match the file."""
+    trace = tmp_path / "timeline.txt"
+    monkeypatch.setenv("SCA_PROFILE_TRACE", str(trace))
+    p = api.Params(20, 8, U=6.0, T=0.1, delta=0.5, prec="bf16x3")
+    with api.Context(p) as c:
+        c.profile(True)
+        c.grad(inputs.seed_phi(0, p.N))
+        prof = c.profile_read()
+        c.profile(False)
+    lines = trace.read_text().strip().splitlines()
+    assert lines[0].startswith("# collection of")
+    recs = [ln.split() for ln in lines[1:] if not ln.startswith("#")]
+    kinds = {}
+    for k, stream, start, dur in recs:
+        assert float(start) >= 0.0 and float(dur) >= 0.0 and int(stream) >= 0
+        kinds.setdefault(k, [0, 0.0])
+        kinds[k][0] += 1
+        kinds[k][1] += float(dur)
+    for k, (ms, n) in prof.items():
+        if n:
+            assert kinds[k][0] == n
+            assert kinds[k][1] == pytest.approx(ms, rel=1e-3, abs=1e-3)
+    # the two groups run on different streams
+    streams = {k: s for k, s, _, _ in recs}
+    assert streams["span_pivoted"] != streams["span_dominant"]
+
+
 @pytest.mark.parametrize("mode", ["dominant", "both"])
 def test_sm_partition_leaves_results_unchanged(mode):
     """SM partitions (green contexts) only move launches between SMs: Omega and the
