@@ -1455,6 +1455,30 @@ __global__ void __launch_bounds__(256)
 // (all at the phi the gradient was taken at) [5] number of updates applied (accumulates).
 // slots (optional): the workspace slot of each of the B blocks, in block order.
 constexpr int RT = 1024;
+// g_i = 2 phi_i / U - 2T sum_b gd[slot(b), i], b ascending, one thread per site: the B-term
+// sums are float64 chains (a slow pipe on this GPU), so they are spread over N / 128 CTAs
+// instead of the single reduction CTA.  slots (optional): the workspace slot of each block.
+__device__ __forceinline__ void grad_sites(int N, int B, const int* slots, const double* gd,
+                                           const double* phi, double U, double T, double* g_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc = 0.0;
+  for (int b = 0; b < B; ++b) acc += gd[(size_t)(slots ? slots[b] : b) * N + i];
+  g_out[i] = 2.0 * phi[i] / U - 2.0 * T * acc;
+}
+
+__global__ void __launch_bounds__(128)
+    k_grad_sites(int N, int B, const double* gd, const double* phi, double U, double T,
+                 double* g_out) {
+  grad_sites(N, B, nullptr, gd, phi, U, T, g_out);
+}
+
+__global__ void __launch_bounds__(128)
+    k_grad_sites_batch(int N, const ReqDesc* rq, const double* gd) {
+  const ReqDesc r = rq[blockIdx.y];
+  grad_sites(N, r.nblocks, r.slots, gd, r.phi, r.U, r.T, r.g);
+}
+
 __device__ __forceinline__ void reduce_body(
     int N, int L, int B, const int* slots, const double* ld, const double* gd,
     const double* phi, double* phi_out, double* m, double* v, double* g_out, double* omega_out,
@@ -1472,13 +1496,10 @@ __device__ __forceinline__ void reduce_body(
     q += ph * ph;
     st += ((x + y) & 1) ? -ph : ph;
     ab += fabs(ph);
-    if (want_grad) {
-      double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += gd[(size_t)(slots ? slots[b] : b) * N + i];
-      const double g = 2.0 * ph / U - 2.0 * T * acc;
+    if (want_grad) {  // g_i from k_grad_sites
+      const double g = g_out[i];
       if (!isfinite(g)) bad = true;
       gm = fmax(gm, fabs(g));
-      g_out[i] = g;
     }
   }
   s_q[tid] = q; s_gm[tid] = gm; s_st[tid] = st; s_ab[tid] = ab;
@@ -1970,6 +1991,10 @@ sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d
   const bool want_grad = (d_grad != nullptr) || (adam != nullptr);
   double* g = d_grad ? d_grad : e.d_g;
   prof_begin(e, kReduce, s);
+  if (want_grad) {
+    k_grad_sites<<<(e.N + 127) / 128, 128, 0, s>>>(e.N, e.B, e.gd, d_phi, e.p.U, e.p.T, g);
+    SCA_LAUNCH_CHECK("gradient sums");
+  }
   k_reduce<<<1, RT, 0, s>>>(e.N, e.L, e.B, e.ld, e.gd, d_phi, adam ? e.d_phi : nullptr, e.d_m,
                             e.d_v, g, d_omega, e.d_status, e.flags, e.p.U, e.p.T,
                             want_grad ? 1 : 0, adam ? 1 : 0, adam ? adam->lr_over_bc1 : 0.0,
@@ -1983,6 +2008,8 @@ sca_status run_reduce(Engine& e, const double* d_phi, double* d_omega, double* d
 
 sca_status run_reduce_batch(Engine& e, const ReqDesc* rq, int nreq, cudaStream_t s) {
   prof_begin(e, kReduce, s);
+  k_grad_sites_batch<<<dim3((e.N + 127) / 128, nreq), 128, 0, s>>>(e.N, rq, e.gd);
+  SCA_LAUNCH_CHECK("gradient sums");
   k_reduce_batch<<<nreq, RT, 0, s>>>(e.N, e.L, rq, e.ld, e.gd, e.flags);
   prof_end(e, kReduce, s);
   SCA_LAUNCH_CHECK("reduce batch");
