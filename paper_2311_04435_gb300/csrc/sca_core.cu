@@ -480,6 +480,7 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
   __shared__ cpx<float> Tb[2][PW][PW + 1];  // inv(M_PP): Gauss-Jordan ping-pong, result in [0]
   cpx<float>(*Tp)[PW + 1] = Tb[0];
   __shared__ double piv2[KB];
+  __shared__ cpx<float> pivd[KB];  // the pivots; |pivot|^2 in float64 after the sweep
   const int mat = blockIdx.x, tid = threadIdx.x;
   const int j = tid % KB, rg = tid / KB;
   const float* re = M + mat * mat_stride;
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
         const float m2 = d.re * d.re + d.im * d.im;
         const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
         const cpx<float> dinv = {d.re * rm, -d.im * rm};
-        if (tid == 0) piv2[p0 + cc] = (double)d.re * d.re + (double)d.im * d.im;
+        if (tid == 0) pivd[p0 + cc] = d;
         const cpx<float> pr = src[cc][cl];  // pivot row, this thread's column
         const cpx<float> u = cmul(pr, dinv);
 #pragma unroll
@@ -603,6 +604,9 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
     __syncthreads();
   }
   {
+    for (int k = tid; k < kb; k += NT)
+      piv2[k] = (double)pivd[k].re * pivd[k].re + (double)pivd[k].im * pivd[k].im;
+    __syncthreads();
     const double s = logdet_sum<NT>(piv2, kb, flags);  // padded pivots are 1
     if (tid == 0) ld[b0 + mat] += s;
   }
@@ -1251,8 +1255,9 @@ __global__ void __launch_bounds__(256)
 //   Re(x^T A x) = sum_j [a_j (Re x_j^2) - w_n Im x_j^2 + 2t Re(x_j (x_{j+x} + x_{j+y}))].
 // The residual it cancels against is ~1e-6 of its size, so it is evaluated to about 2^-44
 // relative: products of the stored float32 values are split exactly with FMA (TwoProduct)
-// and summed in double-float (TwoSum) arithmetic on the FP32 pipes; the float64 result is
-// formed once per row.  One warp per row, the row scattered into natural order in shared
+// and summed in double-float (TwoSum) arithmetic on the FP32 pipes, except for 32-site chunks
+// far from site i, whose terms are bounded as in k_refine_direct and summed in float32; the
+// float64 result is formed once per row.  One warp per row, the row scattered into natural order in shared
 // memory, a_j cached per CTA as a double-float pair.
 template <typename S>
 __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0,
@@ -1284,33 +1289,53 @@ __global__ void k_refine(const S* M, int ldm, size_t mat_stride, size_t plane_st
   __syncthreads();
   const double w = (2.0 * n + 1.0) * kPi * la.T;
   const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
+  const float small = 0x1.0p-18f / (float)N;  // the float32 bound of k_refine_direct
   const int dxs = 32 / L, dys = 32 % L;  // advance of (x, y) when j grows by 32
   for (int i = blockIdx.x * nwarps + warp; i < N; i += gridDim.x * nwarps) {
     for (int r = lane; r < N; r += 32)
       x[sperm[r]] = {re[(size_t)i * ldm + r], im[(size_t)i * ldm + r]};
     __syncwarp();
     dsf acc = {0.f, 0.f};
+    float accf = 0.f;
     int xx = lane / L, yy = lane - (lane / L) * L;
-    for (int j = lane; j < N; j += 32) {
+    for (int j0 = 0; j0 < N; j0 += 32) {  // warp-uniform trip count
+      const int j = j0 + lane;
+      const bool in = j < N;
       const int jx = (xx + 1 == L) ? yy : j + L;
       const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
-      const float a = (float)x[j].re, bq = (float)x[j].im;
-      const float ax = (float)x[jx].re, bx = (float)x[jx].im;
-      const float ay = (float)x[jy].re, by = (float)x[jy].im;
-      const dsf q = ds_sub(two_prod(a, a), two_prod(bq, bq));   // Re x_j^2
-      const dsf ab = two_prod(a, bq);                            // Im x_j^2 / 2
-      const dsf u = ds_add(ds_sub(two_prod(a, ax), two_prod(bq, bx)),
-                           ds_sub(two_prod(a, ay), two_prod(bq, by)));
-      const dsf e = ds_add(ds_sub(ds_mul(adiag[j], q), ds_mul(w2, ab)), ds_mul(t2, u));
-      acc = ds_add(acc, e);
+      const float a = in ? (float)x[j].re : 0.f, bq = in ? (float)x[j].im : 0.f;
+      const float ax = in ? (float)x[jx].re : 0.f, bx = in ? (float)x[jx].im : 0.f;
+      const float ay = in ? (float)x[jy].re : 0.f, by = in ? (float)x[jy].im : 0.f;
+      const dsf ad = in ? adiag[j] : dsf{0.f, 0.f};
       yy += dys;
       xx += dxs;
       if (yy >= L) { yy -= L; xx += 1; }
+      const float aa = fabsf(a), ba = fabsf(bq);
+      const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
+                       t2a * (aa * (fabsf(ax) + fabsf(ay)) + ba * (fabsf(bx) + fabsf(by)));
+      if (__any_sync(0xffffffffu, !(sj <= small))) {
+        const dsf q = ds_sub(two_prod(a, a), two_prod(bq, bq));   // Re x_j^2
+        const dsf ab = two_prod(a, bq);                            // Im x_j^2 / 2
+        const dsf u = ds_add(ds_sub(two_prod(a, ax), two_prod(bq, bx)),
+                             ds_sub(two_prod(a, ay), two_prod(bq, by)));
+        const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, u));
+        acc = ds_add(acc, e);
+      } else {
+        accf += ad.h * (a * a - bq * bq) - w2f * (a * bq) + t2f * (a * (ax + ay) - bq * (bx + by));
+      }
     }
-    double qsum = (double)acc.h + (double)acc.l;
+    acc = ds_add(acc, dsf{accf, 0.f});
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, off);
-    if (lane == 0) gd[(size_t)b * N + i] = sg * (2.0 * (double)x[i].re - qsum);
+    for (int off = 16; off > 0; off >>= 1) {
+      const dsf o = {__shfl_xor_sync(0xffffffffu, acc.h, off),
+                     __shfl_xor_sync(0xffffffffu, acc.l, off)};
+      acc = ds_add(acc, o);
+    }
+    if (lane == 0) {
+      const double qsum = (double)acc.h + (double)acc.l;
+      gd[(size_t)b * N + i] = sg * (2.0 * (double)x[i].re - qsum);
+    }
     __syncwarp();
   }
 }
