@@ -477,8 +477,7 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
   constexpr int MAXR = (KB + RS - 1) / RS;
   __shared__ cpx<float> Ms[KB][PW + 1];  // M[:, P], then F in place
   __shared__ cpx<float> Ws[PW][KB];      // W = M[P, :]
-  __shared__ cpx<float> Tb[2][PW][PW + 1];  // inv(M_PP): Gauss-Jordan ping-pong, result in [0]
-  cpx<float>(*Tp)[PW + 1] = Tb[0];
+  __shared__ cpx<float> Tp[PW][PW + 1];  // inv(M_PP)
   __shared__ double piv2[KB];
   __shared__ cpx<float> pivd[KB];  // the pivots; |pivot|^2 in float64 after the sweep
   const int mat = blockIdx.x, tid = threadIdx.x;
@@ -508,43 +507,47 @@ __global__ void __launch_bounds__(NT) k_diag_gjb(const float* M, int ldm, size_t
         Ws[r - p0][j] = jP ? cpx<float>{(j == r) ? 1.f : 0.f, 0.f} : a[q];
     }
     __syncthreads();
-    // (b) four warps: inv(M_PP) by Gauss-Jordan; thread owns column tid % 16 of rows
-    // tid / 16 and tid / 16 + 8, reading one buffer and writing the other (one barrier of the
-    // four warps per pivot)
-    if (tid < 128) {
+    // (b) one warp: inv(M_PP) by Gauss-Jordan in registers; lane owns column lane % 16 of
+    // rows lane / 16 + 2 m, and the pivot row, column and entry of each step come by shuffle
+    if (tid < 32) {
       const int cl = tid & 15, r0 = tid >> 4;
-      Tb[0][r0][cl] = Ms[p0 + r0][cl];
-      Tb[0][r0 + 8][cl] = Ms[p0 + r0 + 8][cl];
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll 1
+      cpx<float> v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = Ms[p0 + r0 + 2 * m][cl];
+#pragma unroll
       for (int cc = 0; cc < PW; ++cc) {
-        const cpx<float>(*src)[PW + 1] = Tb[cc & 1];
-        cpx<float>(*dst)[PW + 1] = Tb[(cc & 1) ^ 1];
-        const cpx<float> d = src[cc][cc];
+        const int own = (cc & 1) * 16;  // lanes holding row cc, in slot cc / 2
+        cpx<float> d, pr, pc[8];
+        d.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cc);
+        d.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cc);
+        pr.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cl);  // pivot row, my column
+        pr.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cl);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {  // pivot column, my rows
+          pc[m].re = __shfl_sync(0xffffffffu, v[m].re, r0 * 16 + cc);
+          pc[m].im = __shfl_sync(0xffffffffu, v[m].im, r0 * 16 + cc);
+        }
         const float m2 = d.re * d.re + d.im * d.im;
         const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
         const cpx<float> dinv = {d.re * rm, -d.im * rm};
         if (tid == 0) pivd[p0 + cc] = d;
-        const cpx<float> pr = src[cc][cl];  // pivot row, this thread's column
         const cpx<float> u = cmul(pr, dinv);
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-          const int r = r0 + 8 * m;
-          const cpx<float> pc = src[r][cc];  // pivot column, this row
-          const cpx<float> t = src[r][cl];
-          cpx<float> nv;
+        for (int m = 0; m < 8; ++m) {
+          const int r = r0 + 2 * m;
           if (r == cc) {
-            nv = (cl == cc) ? dinv : cmul(t, dinv);
+            v[m] = (cl == cc) ? dinv : cmul(v[m], dinv);
           } else if (cl == cc) {
-            const cpx<float> q2 = cmul(pc, dinv);
-            nv = {-q2.re, -q2.im};
+            const cpx<float> q2 = cmul(pc[m], dinv);
+            v[m] = {-q2.re, -q2.im};
           } else {
-            nv = {t.re - (pc.re * u.re - pc.im * u.im), t.im - (pc.re * u.im + pc.im * u.re)};
+            v[m] = {v[m].re - (pc[m].re * u.re - pc[m].im * u.im),
+                    v[m].im - (pc[m].re * u.im + pc[m].im * u.re)};
           }
-          dst[r][cl] = nv;
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) Tp[r0 + 2 * m][cl] = v[m];
     }
     __syncthreads();
     // (c) F = M[:, P] inv(M_PP) (rows of P: -inv(M_PP)), in place of M[:, P]: four threads
