@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(256)
 // held in registers (lane l keeps columns l, l + 32, ...; the pivot entry of a step comes by
 // shuffle), so a step needs no barrier.  Warp w of W takes the pairs (row r of T, row r of
 // inv(L)) for r = w, w + W, ..., whose lengths add up to 2 kb steps.
-template <typename S, typename C, int NT>
+template <typename S, typename C, int NT, bool FULL>
 __global__ void __launch_bounds__(NT)
     k_tinv_warp(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
                 int nb, cpx<C>* Tinv, float* TT) {
@@ -954,9 +954,9 @@ __global__ void __launch_bounds__(NT)
               if (lane == jj) { xr[q] = yr; xi[q] = yi; }
               const cpx<C>* u = LU + (size_t)j * kb;
 #pragma unroll
-              for (int q2 = q; q2 < KQ; ++q2) {
+              for (int q2 = q; q2 < KQ; ++q2) {  // k > j holds past chunk q
                 const int k = q2 * 32 + lane;
-                if (k > j && k < kb) {
+                if ((q2 > q || lane > jj) && (FULL || k < kb)) {
                   const cpx<C> uv = u[k];
                   xr[q2] -= yr * uv.re - yi * uv.im;
                   xi[q2] -= yr * uv.im + yi * uv.re;
@@ -977,9 +977,9 @@ __global__ void __launch_bounds__(NT)
             const C yi = __shfl_sync(0xffffffffu, xi[q], jj);
             const cpx<C>* l = LU + (size_t)j * kb;
 #pragma unroll
-            for (int q2 = 0; q2 <= q; ++q2) {
+            for (int q2 = 0; q2 <= q; ++q2) {  // k < j holds before chunk q
               const int k = q2 * 32 + lane;
-              if (k < j) {
+              if (q2 < q || lane < jj) {
                 const cpx<C> lv = l[k];
                 xr[q2] -= yr * lv.re - yi * lv.im;
                 xi[q2] -= yr * lv.im + yi * lv.re;
@@ -1749,9 +1749,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_begin(e, kTrinv, s);
       const size_t smt = sizeof(cpx<C>) * std::max((size_t)kb * kb + kb, (size_t)nb * (nb + 1));
       constexpr int NT = sizeof(C) == 8 ? 512 : 1024;
+      constexpr int NBMAX = sizeof(C) == 8 ? 64 : 128;
       float* TT = piv_tc_prep ? e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb : nullptr;
-      k_tinv_warp<S, C, NT><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
-                                                  nb, Tinv, TT);
+      if (kb == NBMAX)
+        k_tinv_warp<S, C, NT, true><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride, e.plane_stride,
+                                                          k0, kb, nb, Tinv, TT);
+      else
+        k_tinv_warp<S, C, NT, false><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride,
+                                                           e.plane_stride, k0, kb, nb, Tinv, TT);
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("pivot-block inverse");
     } else {
@@ -1969,7 +1974,9 @@ sca_status set_smem_limits() {
   cudaError_t err;
   if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
   if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
-  if ((err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024>)) != cudaSuccess) return cuda_fail(err, "smem tinv");
+  if ((err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, true>)) != cudaSuccess ||
+      (err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, false>)) != cudaSuccess)
+    return cuda_fail(err, "smem tinv");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
   done = true;
   return SCA_OK;
