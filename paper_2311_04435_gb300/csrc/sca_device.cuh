@@ -89,8 +89,8 @@ __device__ __forceinline__ dsf ds_of(double v) {
 }
 
 
-// sum_k 0.5 ln(mag2[k]) over k < n: logs in parallel, then summed by thread 0 in index order
-// (deterministic); returns the sum to thread 0 only.  Flags non-positive / non-finite moduli.
+// sum_k 0.5 ln(mag2[k]) over k < n: logs in parallel, then a pairwise reduction in a fixed
+// order (deterministic); every thread gets the sum.  Flags non-positive / non-finite moduli.
 template <int NT>
 __device__ double logdet_sum(double* mag2, int n, int* flags) {
   for (int k = threadIdx.x; k < n; k += NT) {
@@ -100,10 +100,18 @@ __device__ double logdet_sum(double* mag2, int n, int* flags) {
     mag2[k] = 0.5 * log(ok ? m : 1.0);
   }
   __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < n; ++k) s += mag2[k];
-  return s;
+  // pairwise sums in a fixed order (float64 adds are a slow pipe here: a serial chain of n
+  // of them by one thread would cost more than the logs)
+  int w = 1;
+  while (w < n) w <<= 1;
+  for (int h = w >> 1; h > 0; h >>= 1) {
+    for (int k = threadIdx.x; k < h; k += NT)
+      if (k + h < n) mag2[k] += mag2[k + h];
+    __syncthreads();
+  }
+  const double total = n > 0 ? mag2[0] : 0.0;
+  __syncthreads();  // every thread has read the sum before the caller reuses the buffer
+  return total;
 }
 
 
