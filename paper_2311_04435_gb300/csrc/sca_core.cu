@@ -113,43 +113,77 @@ __global__ void __launch_bounds__(256)
 // shared-memory sub-panels of width kbi; after each sub-panel [s0, s0+kbi) the rest of the outer
 // panel (columns [s0+kbi, c_end)) is brought up to date as in a right-looking LU:
 //   U12 = inv(L11) A12  (rows [s0, s0+kbi), k_swap_trsm)   then   A22 -= L21 U12  (rows >= s0+kbi).
-// k_gemm_panel: A22[r][c] -= sum_k L21[r][k] U12[k][c] for rows r >= s0+kbi (64 per CTA),
-// columns [s0+kbi, c_end), K = kbi <= 16; U12 staged in shared memory.
+// k_gemm_panel: A22[r][c] -= sum_k L21[r][k] U12[k][c] for rows r >= s0+kbi (kGemmPanelRows
+// per CTA), columns [s0+kbi, c_end), K = kbi <= 16; L21 and U12 staged in shared memory.
+constexpr int kGemmPanelRows = 32;
 template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     k_gemm_panel(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
                  int c_end) {
   constexpr int NCMAX = sizeof(C) == 8 ? 64 : 128;
+  constexpr int RSTEP = 256 / NCMAX;               // rows covered by one pass of the CTA
+  constexpr int MA = kGemmPanelRows / RSTEP;       // A22 entries per thread
+  constexpr int MU = 16 / RSTEP;                   // U12 entries per thread
+  constexpr int ML = kGemmPanelRows * 16 / 256;    // L21 entries per thread
   __shared__ cpx<C> Us[16][NCMAX];
-  __shared__ cpx<C> Ls[64][17];
+  __shared__ cpx<C> Ls[kGemmPanelRows][17];
   const int mat = blockIdx.y;
   const int c0 = s0 + kbi, nc = c_end - c0;
-  const int r0 = c0 + blockIdx.x * 64;
+  const int r0 = c0 + blockIdx.x * kGemmPanelRows;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
-  for (int e = threadIdx.x; e < kbi * nc; e += 256) {
-    const int k = e / nc, c = e - k * nc;
-    const size_t o = (size_t)(s0 + k) * ldm + c0 + c;
-    Us[k][c] = {(C)re[o], (C)im[o]};
+  // a thread owns one column c and every RSTEP-th row; all its global loads are issued before
+  // any is used, so a CTA waits one memory round trip instead of one per entry
+  const int c = threadIdx.x % NCMAX, rl = threadIdx.x / NCMAX;
+  const bool cin = c < nc;
+  cpx<C> uv[MU], lv[ML], av[MA];
+#pragma unroll
+  for (int t = 0; t < MU; ++t) {
+    const int k = rl + RSTEP * t;
+    if (cin && k < kbi) {
+      const size_t o = (size_t)(s0 + k) * ldm + c0 + c;
+      uv[t] = {(C)re[o], (C)im[o]};
+    }
   }
-  for (int e = threadIdx.x; e < 64 * kbi; e += 256) {
-    const int r = e / kbi, k = e - r * kbi;
-    const int gr = r0 + r;
-    Ls[r][k] = (gr < N) ? cpx<C>{(C)re[(size_t)gr * ldm + s0 + k], (C)im[(size_t)gr * ldm + s0 + k]}
-                        : cpx<C>{(C)0, (C)0};
+#pragma unroll
+  for (int t = 0; t < ML; ++t) {
+    const int e = threadIdx.x + 256 * t;
+    const int gr = r0 + (e >> 4), k = e & 15;
+    lv[t] = (gr < N && k < kbi)
+                ? cpx<C>{(C)re[(size_t)gr * ldm + s0 + k], (C)im[(size_t)gr * ldm + s0 + k]}
+                : cpx<C>{(C)0, (C)0};
+  }
+#pragma unroll
+  for (int t = 0; t < MA; ++t) {
+    const int gr = r0 + rl + RSTEP * t;
+    if (cin && gr < N) {
+      const size_t o = (size_t)gr * ldm + c0 + c;
+      av[t] = {(C)re[o], (C)im[o]};
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < MU; ++t) {
+    const int k = rl + RSTEP * t;
+    if (cin && k < kbi) Us[k][c] = uv[t];
+  }
+#pragma unroll
+  for (int t = 0; t < ML; ++t) {
+    const int e = threadIdx.x + 256 * t;
+    Ls[e >> 4][e & 15] = lv[t];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * nc; e += 256) {
-    const int r = e / nc, c = e - r * nc;
-    const int gr = r0 + r;
+  if (!cin) return;
+#pragma unroll
+  for (int t = 0; t < MA; ++t) {
+    const int r = rl + RSTEP * t, gr = r0 + r;
     if (gr >= N) continue;
-    const size_t o = (size_t)gr * ldm + c0 + c;
-    cpx<C> a = {(C)re[o], (C)im[o]};
+    cpx<C> a = av[t];
     for (int k = 0; k < kbi; ++k) {
       const cpx<C> l = Ls[r][k], u = Us[k][c];
       a.re -= l.re * u.re - l.im * u.im;
       a.im -= l.re * u.im + l.im * u.re;
     }
+    const size_t o = (size_t)gr * ldm + c0 + c;
     re[o] = (S)a.re;
     im[o] = (S)a.im;
   }
@@ -169,6 +203,7 @@ __global__ void __launch_bounds__(128)
   constexpr int TMAX = 16;   // widest sub-panel that leaves outer-panel columns behind
   __shared__ cpx<C> Ls[TMAX][TMAX + 1];
   __shared__ int sp[KMAX];
+  __shared__ int mv_dst[2 * TMAX], mv_src[2 * TMAX], s_nmv;
   const int mat = blockIdx.y;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
@@ -182,24 +217,76 @@ __global__ void __launch_bounds__(128)
   for (int t = threadIdx.x; t < kbi && t < KMAX; t += blockDim.x)
     sp[t] = piv[(size_t)mat * N + s0 + t];
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // for a sub-panel of at most TMAX columns, compose its interchanges into one list of row
+    // moves (row dst takes the old content of row src) over the at most 2 kbi rows they touch
+    int nmv = -1;
+    if (kbi <= TMAX) {
+      int row[2 * TMAX], from[2 * TMAX], ns = kbi;
+      for (int x = 0; x < kbi; ++x) row[x] = s0 + x, from[x] = x;
+      for (int cc = 0; cc < kbi; ++cc) {
+        const int p = sp[cc];
+        if (p == s0 + cc) continue;
+        int q = p - s0;
+        if (q >= kbi) {
+          q = kbi;
+          while (q < ns && row[q] != p) ++q;
+          if (q == ns) row[ns] = p, from[ns] = ns, ++ns;
+        }
+        const int t = from[cc];
+        from[cc] = from[q];
+        from[q] = t;
+      }
+      nmv = 0;
+      for (int x = 0; x < ns; ++x)
+        if (from[x] != x) mv_dst[nmv] = row[x], mv_src[nmv] = row[from[x]], ++nmv;
+    }
+    s_nmv = nmv;
+  }
+  __syncthreads();
   const int j = jstart + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N || (j >= s0 && j < s0 + kbi)) return;
-  for (int cc = 0; cc < kbi && cc < KMAX; ++cc) {
-    const int p = sp[cc];
-    if (p != s0 + cc) {
-      const size_t a = (size_t)(s0 + cc) * ldm + j, q = (size_t)p * ldm + j;
-      const S xr = re[a], xi = im[a];
-      re[a] = re[q]; im[a] = im[q];
-      re[q] = xr; im[q] = xi;
+  const int nmv = s_nmv;
+  if (nmv >= 0) {
+    // every load of the column's moves before any store: one memory round trip
+    S vr[2 * TMAX], vi[2 * TMAX];
+#pragma unroll
+    for (int t = 0; t < 2 * TMAX; ++t)
+      if (t < nmv) {
+        const size_t q = (size_t)mv_src[t] * ldm + j;
+        vr[t] = re[q];
+        vi[t] = im[q];
+      }
+#pragma unroll
+    for (int t = 0; t < 2 * TMAX; ++t)
+      if (t < nmv) {
+        const size_t a = (size_t)mv_dst[t] * ldm + j;
+        re[a] = vr[t];
+        im[a] = vi[t];
+      }
+  } else {
+    for (int cc = 0; cc < kbi && cc < KMAX; ++cc) {
+      const int p = sp[cc];
+      if (p != s0 + cc) {
+        const size_t a = (size_t)(s0 + cc) * ldm + j, q = (size_t)p * ldm + j;
+        const S xr = re[a], xi = im[a];
+        re[a] = re[q]; im[a] = im[q];
+        re[q] = xr; im[q] = xi;
+      }
     }
   }
   if (!tr || j < s0 + kbi || j >= c_end) return;
   cpx<C> u[TMAX];
 #pragma unroll
+  for (int r = 0; r < TMAX; ++r)
+    if (r < kbi) {
+      const size_t o = (size_t)(s0 + r) * ldm + j;
+      u[r] = {(C)re[o], (C)im[o]};
+    }
+#pragma unroll
   for (int r = 0; r < TMAX; ++r) {
     if (r >= kbi) break;
-    const size_t o = (size_t)(s0 + r) * ldm + j;
-    cpx<C> acc = {(C)re[o], (C)im[o]};
+    cpx<C> acc = u[r];
 #pragma unroll
     for (int k = 0; k < TMAX; ++k) {
       if (k >= r) break;
@@ -208,6 +295,7 @@ __global__ void __launch_bounds__(128)
       acc.im -= t.im;
     }
     u[r] = acc;
+    const size_t o = (size_t)(s0 + r) * ldm + j;
     re[o] = (S)acc.re;
     im[o] = (S)acc.im;
   }
@@ -1717,8 +1805,9 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
         SCA_LAUNCH_CHECK("swap");
         if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
           prof_begin(e, kPanelUpd, s);
-          k_gemm_panel<S, C><<<dim3((N - s0 - kbi + 63) / 64, cnt), 256, 0, s>>>(
-              M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, kend);
+          const int gx = (N - s0 - kbi + kGemmPanelRows - 1) / kGemmPanelRows;
+          k_gemm_panel<S, C><<<dim3(gx, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
+                                                           e.plane_stride, s0, kbi, kend);
           prof_end(e, kPanelUpd, s);
           SCA_LAUNCH_CHECK("panel update");
         }
