@@ -1988,33 +1988,48 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
         if ((err = cudaStreamWaitEvent(sd, e.ev_fork, 0)) != cudaSuccess) return cuda_fail(err, "fork");
       }
     }
-    sca_status st;
+    sca_status st = SCA_OK;
     // While both groups run, the dominant group's persistent tensor-core launches leave
     // sm_reserve SMs to the pivoted group's kernels (with partitions: each group's
     // tensor-core launches take one CTA per SM of its partition).
-    e.tc_cap = parted && e.part_side ? e.part_sms[0] : 0;
-    const int span_p = np > 0 ? prof_span_begin(e, kSpanPiv, sp) : -1;
-    if (np > 0) {
-      NvtxRange range("sca.pivoted_group");
-      if ((st = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp)) != SCA_OK)
-        return st;
-    }
-    prof_span_end(e, span_p, sp);
+    auto pivoted_group = [&]() -> sca_status {
+      e.tc_cap = parted && e.part_side ? e.part_sms[0] : 0;
+      const int span_p = np > 0 ? prof_span_begin(e, kSpanPiv, sp) : -1;
+      sca_status r = SCA_OK;
+      if (np > 0) {
+        NvtxRange range("sca.pivoted_group");
+        r = run_group<S, C>(e, b0, 0, np, true, e.nb, e.tc, want_grad, sp);
+      }
+      e.tc_cap = 0;
+      if (r == SCA_OK) prof_span_end(e, span_p, sp);
+      return r;
+    };
+    auto dominant_group = [&]() -> sca_status {
+      if (parted) {
+        e.tc_cap = e.part_sms[1];
+        if (e.aux) e.aux = e.part_aux;
+      } else if (fork && e.sm_reserve > 0 && e.tmap) {
+        e.tc_cap = tc_sms(e) - e.sm_reserve;
+      }
+      const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, sd) : -1;
+      sca_status r = SCA_OK;
+      if (nd > 0) {
+        NvtxRange range("sca.dominant_group");
+        r = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, sd);
+      }
+      e.tc_cap = 0;
+      e.aux = aux_saved;
+      if (r == SCA_OK) prof_span_end(e, span_d, sd);
+      return r;
+    };
+    // On their own streams the dominant group is enqueued first: its few long launches then
+    // start at once, while the pivoted group's many short ones are still being enqueued (the
+    // host stays ahead of that chain on the device).
     if (parted) {
-      e.tc_cap = e.part_sms[1];
-      if (e.aux) e.aux = e.part_aux;
-    } else if (fork && e.sm_reserve > 0 && e.tmap) {
-      e.tc_cap = tc_sms(e) - e.sm_reserve;
+      if ((st = dominant_group()) != SCA_OK || (st = pivoted_group()) != SCA_OK) return st;
+    } else {
+      if ((st = pivoted_group()) != SCA_OK || (st = dominant_group()) != SCA_OK) return st;
     }
-    const int span_d = nd > 0 ? prof_span_begin(e, kSpanDom, sd) : -1;
-    if (nd > 0) {
-      NvtxRange range("sca.dominant_group");
-      st = run_group<S, C>(e, b0 + np, np, nd, false, e.nb, e.tc, want_grad, sd);
-    }
-    e.tc_cap = 0;
-    e.aux = aux_saved;
-    if (st != SCA_OK) return st;
-    prof_span_end(e, span_d, sd);
     if (fork) {
       if (want_grad && refine_stage && !e.dos_mode) {  // each group refines its own blocks
         if ((st = launch_refine<S>(e, la, b0, 0, np, sp)) != SCA_OK) return st;
