@@ -113,6 +113,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   // narrower than nb: the outer panel is factorised in sub-panels of at most 16 columns
   if (nbp < e.nb) nbp = std::min(nbp, 16);
   e.nb_piv = nbp;
+  if (const char* v = std::getenv("SCA_DIAG_TC")) e.diag_tc = std::atoi(v) != 0;
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;
   if (const char* v = std::getenv("SCA_MAX_BLOCKS_RESIDENT")) {

@@ -1220,49 +1220,91 @@ __global__ void __launch_bounds__(256)
   const S* im = re + plane_stride;
   const bool direct = sym && j0 >= k0 + kb;
   if (!direct) {
-    for (int e = threadIdx.x; e < nb * 64; e += 256) {
-      const int c = e >> 6, jj = e & 63;
-      const int j = j0 + jj;
-      const bool in = c < kb && j < N;
-      tr[jj * ts + c] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
-      ti[jj * ts + c] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+    // the row strip's loads go out eight at a time before their shared-memory stores
+    constexpr int LU = 8;
+    for (int e0 = threadIdx.x; e0 < nb * 64; e0 += 256 * LU) {
+      S xr[LU], xi[LU];
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int e = e0 + 256 * u;
+        const int c = e >> 6, j = j0 + (e & 63);
+        const bool in = e < nb * 64 && c < kb && j < N;
+        xr[u] = in ? re[(size_t)(k0 + c) * ldm + j] : (S)0;
+        xi[u] = in ? im[(size_t)(k0 + c) * ldm + j] : (S)0;
+      }
+#pragma unroll
+      for (int u = 0; u < LU; ++u) {
+        const int e = e0 + 256 * u;
+        if (e < nb * 64) {
+          tr[(e & 63) * ts + (e >> 6)] = xr[u];
+          ti[(e & 63) * ts + (e >> 6)] = xi[u];
+        }
+      }
     }
     __syncthreads();
   }
   S* out = W + (size_t)mat * fw_mat;
   const int g8 = (nb + 7) / 8;  // the split planes have nb = 128; plain ones may be narrower
-  for (int e = threadIdx.x; e < 64 * g8; e += 256) {
-    const int jj = e / g8, c8 = (e - jj * g8) * 8;
-    const int j = j0 + jj;
-    if (j >= N) continue;
-    S dr[8], di[8];
-    if (gj && j >= k0 && j < k0 + kb) {
+  // IT groups of 8 entries per thread: every load of the IT groups is issued before the first
+  // conversion and store
+  constexpr int IT = sizeof(S) == 4 ? 4 : 2;
+  for (int e0 = threadIdx.x; e0 < 64 * g8; e0 += 256 * IT) {
+    S dr[IT][8], di[IT][8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        dr[t] = (c8 + t == j - k0) ? (S)1 : (S)0;
-        di[t] = (S)0;
-      }
-    } else if (direct) {
-      const S* rr = re + (size_t)j * ldm + k0 + c8;
-      const S* ri = im + (size_t)j * ldm + k0 + c8;
+    for (int u = 0; u < IT; ++u) {
+      const int e = e0 + 256 * u;
+      const int jj = e / g8, c8 = (e - jj * g8) * 8;
+      const int j = j0 + jj;
+      if (e >= 64 * g8 || j >= N) continue;
+      if (gj && j >= k0 && j < k0 + kb) {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const bool in = c8 + t < kb;
-        dr[t] = in ? rr[t] : (S)0;
-        di[t] = in ? ri[t] : (S)0;
-      }
-    } else {
+        for (int t = 0; t < 8; ++t) {
+          dr[u][t] = (c8 + t == j - k0) ? (S)1 : (S)0;
+          di[u][t] = (S)0;
+        }
+      } else if (direct) {
+        const S* rr = re + (size_t)j * ldm + k0 + c8;
+        const S* ri = im + (size_t)j * ldm + k0 + c8;
+        if (sizeof(S) == 4 && c8 + 8 <= kb &&
+            ((reinterpret_cast<uintptr_t>(rr) | reinterpret_cast<uintptr_t>(ri)) & 15) == 0) {
+          const float4* vr4 = reinterpret_cast<const float4*>(rr);
+          const float4* vi4 = reinterpret_cast<const float4*>(ri);
+          const float4 a0 = vr4[0], a1 = vr4[1], b0 = vi4[0], b1 = vi4[1];
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const bool in = c8 + t < nb;
-        dr[t] = in ? tr[jj * ts + c8 + t] : (S)0;
-        di[t] = in ? ti[jj * ts + c8 + t] : (S)0;
+          for (int t = 0; t < 8; ++t) {
+            dr[u][t] = (S)av[t];
+            di[u][t] = (S)bv[t];
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const bool in = c8 + t < kb;
+            dr[u][t] = in ? rr[t] : (S)0;
+            di[u][t] = in ? ri[t] : (S)0;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const bool in = c8 + t < nb;
+          dr[u][t] = in ? tr[jj * ts + c8 + t] : (S)0;
+          di[u][t] = in ? ti[jj * ts + c8 + t] : (S)0;
+        }
       }
     }
-    float vr[8], vi[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) { vr[t] = (float)dr[t]; vi[t] = (float)di[t]; }
-    store_fw8(out, fw_plane, (size_t)j * nb + c8, vr, vi, dr, di, split, nb - c8);
+    for (int u = 0; u < IT; ++u) {
+      const int e = e0 + 256 * u;
+      const int jj = e / g8, c8 = (e - jj * g8) * 8;
+      const int j = j0 + jj;
+      if (e >= 64 * g8 || j >= N) continue;
+      float vr[8], vi[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) { vr[t] = (float)dr[u][t]; vi[t] = (float)di[u][t]; }
+      store_fw8(out, fw_plane, (size_t)j * nb + c8, vr, vi, dr[u], di[u], split, nb - c8);
+    }
   }
 }
 
@@ -1852,8 +1894,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_begin(e, kDiag, s);
       float* TT = (tcg && e.tt) ? e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb : nullptr;
       if constexpr (sizeof(C) == 4) {
-        k_diag_gjb<512><<<cnt, 512, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb, nb,
-                                            b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags);
+        if (tcg && e.tmap && nb == 128 && e.diag_tc) {
+          sca_status st = tc_diag(M, e.ldm, e.mat_stride, e.plane_stride, cnt, k0, kb, nb, b0,
+                                  e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags, s);
+          if (st != SCA_OK) return st;
+        } else {
+          k_diag_gjb<512><<<cnt, 512, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0, kb,
+                                              nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags);
+        }
       } else {
         k_diag_gj<S, C, 768><<<cnt, 768, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
                                                   kb, nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0,

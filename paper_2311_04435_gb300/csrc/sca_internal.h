@@ -55,6 +55,7 @@ struct Engine {
   int L = 0, N = 0, B = 0;
   int nb = 0;            // Gauss-Jordan / LU block width (diagonally dominant blocks)
   int nb_piv = 0;        // block width of the pivoted group (shared-memory panel)
+  bool diag_tc = true;   // dominant pivot-block inverses on the tensor cores (nb = 128)
   int piv_planned = 0;   // piv_blocks under partial pivoting
   int piv_blocks = 0;    // blocks b < piv_blocks need partial pivoting (omega_n <= 4|t|)
   int ldm = 0;           // row stride of a block plane (elements)
@@ -203,6 +204,11 @@ sca_status tc_reset_counters(Engine& e, cudaStream_t s);  // before each chunk's
 // F = M[:, K] T on the tensor cores into W scratch planes 4, 5 (rows >= r0).
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s);
 // the pivoted group's prep product (BF16x3): rows [r0, k0+kb) times T, rows below times inv(L)
+// Pivot-block inverse of dominant blocks on the tensor cores (nb = 128, float32 blocks): the
+// outputs of the register Gauss-Jordan kernel (T, -T^T split planes, ld += ln|det|).
+sca_status tc_diag(const float* M, int ldm, size_t mat_stride, size_t plane_stride, int cnt, int k0,
+                   int kb, int nb, int b0, double* ld, void* Tinv, float* TT, int tt_bf16,
+                   int* flags, cudaStream_t s);
 sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
                        cudaStream_t s);
 // Prep product of the symmetric dominant blocks: F = S (W^T T) written as the four TF32

@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include "sca_internal.h"
+#include "sca_device.cuh"
 
 namespace sca {
 namespace {
@@ -633,6 +634,387 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------ pivot-block inverse on the tensor cores
+// Gauss-Jordan inverse T = inv(M_KK) of one 128 x 128 diagonally dominant pivot block per CTA
+// (no pivoting), the tableau resident in TMEM: lane r = row r, columns 0-127 the real and
+// 128-255 the imaginary parts.  It is swept in 8 panels P of 16 pivots; per panel
+//   1. the rows of P go to shared memory and one warp inverts M_PP in registers (its pivots
+//      are those of the LU, so ln|det M_KK| is the same sum);
+//   2. every thread forms its row of F = M[:, P] inv(M_PP) in float32 (rows of P:
+//      -inv(M_PP)), and the rows and columns of P are zeroed in TMEM;
+//   3. M <- mask(M) - F W (W = M[P, :] with the identity in the columns of P) as real MMAs
+//      of M = 128, N = 256, K = 32: A = [F_re | F_im], B rows c: [W_re; -W_im] and rows
+//      128 + c: [W_im; W_re], split TF32 (hi*hi + hi*lo + lo*hi), A negated by the
+//      instruction descriptor, accumulating into the tableau.
+// Two CTAs fit on one SM (256 TMEM columns and ~101 KB of shared memory each), so a launch
+// over all dominant blocks is a single wave.  Outputs as the register kernel: T (complex,
+// row-major nb x nb, zero outside kb), the -T^T split planes, ld += ln|det M_KK|.
+constexpr int kDgThreads = 128;
+constexpr int kDgA = 0;                         // A: sub-tile (re, im) x (hi, lo), 128 x 64 B
+constexpr int kDgB = 4 * 8192;                  // B: sub-tile (k < 16, k >= 16) x (hi, lo), 256 x 64 B
+constexpr int kDgTp = kDgB + 4 * 16384;         // inv(M_PP): 16 x 17 complex
+constexpr int kDgPiv = kDgTp + 16 * 17 * 8;     // the 128 pivots (complex)
+constexpr int kDgPiv2 = kDgPiv + 128 * 8;       // |pivot|^2 (double)
+constexpr int kDgBar = kDgPiv2 + 128 * 8;       // mbarrier, TMEM address, abort flag
+constexpr int kDgSmem = kDgBar + 64 + 1024;     // + alignment slack
+constexpr int kDgRowStride = 129;               // complex row stride of the panel rows (in A)
+constexpr uint32_t kDgTmemCols = 256;
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// One 64-byte K-major operand row of 16 floats, TF32-split into the hi and lo planes, in the
+// 64-byte swizzle (16-byte chunk q of row r at chunk q ^ ((r >> 1) & 3)).
+__device__ __forceinline__ void dg_store_row(unsigned char* hi, unsigned char* lo, int row,
+                                             const float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = __uint_as_float(__float_as_uint(v[4 * q + e]) & 0xffffe000u);
+      l[e] = v[4 * q + e] - h[e];
+    }
+    const int off = row * 64 + ((q ^ ((row >> 1) & 3)) << 4);
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+__global__ void __launch_bounds__(kDgThreads, 2)
+    k_diag_tc(const float* M, int ldm, long long mat_stride, long long plane_stride, int k0,
+              int kb, int b0, double* ld, float2* Tinv, float* TT, int tt_bf16, int* flags) {
+  constexpr int KB = 128, PW = 16;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* opA = sm + kDgA;
+  unsigned char* opB = sm + kDgB;
+  float2* wrow = reinterpret_cast<float2*>(sm + kDgA);  // rows of P, [16][kDgRowStride]
+  float2* tp = reinterpret_cast<float2*>(sm + kDgTp);   // inv(M_PP), [16][17]
+  float2* pivd = reinterpret_cast<float2*>(sm + kDgPiv);
+  double* piv2 = reinterpret_cast<double*>(sm + kDgPiv2);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kDgBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kDgBar + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kDgBar + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mat = blockIdx.x, r = tid;
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kDgTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lane quarter
+  const float* re = M + (long long)mat * mat_stride;
+  const float* im = re + plane_stride;
+
+  // the pivot block into TMEM (identity outside kb)
+#pragma unroll 1
+  for (int c0 = 0; c0 < KB; c0 += 32) {
+    uint32_t vr[32], vi[32];
+    if (r < kb && c0 + 32 <= kb) {
+      const float4* pr = reinterpret_cast<const float4*>(re + (size_t)(k0 + r) * ldm + k0 + c0);
+      const float4* pi = reinterpret_cast<const float4*>(im + (size_t)(k0 + r) * ldm + k0 + c0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 a4 = pr[q], b4 = pi[q];
+        vr[4 * q] = __float_as_uint(a4.x); vr[4 * q + 1] = __float_as_uint(a4.y);
+        vr[4 * q + 2] = __float_as_uint(a4.z); vr[4 * q + 3] = __float_as_uint(a4.w);
+        vi[4 * q] = __float_as_uint(b4.x); vi[4 * q + 1] = __float_as_uint(b4.y);
+        vi[4 * q + 2] = __float_as_uint(b4.z); vi[4 * q + 3] = __float_as_uint(b4.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int c = c0 + i;
+        const bool in = r < kb && c < kb;
+        const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+        vr[i] = __float_as_uint(in ? re[o] : (r == c ? 1.f : 0.f));
+        vi[i] = __float_as_uint(in ? im[o] : 0.f);
+      }
+    }
+    __syncwarp();  // the warp-collective store after a lane-dependent branch
+    tmem_st32(trow + (uint32_t)c0, vr);
+    tmem_st32(trow + (uint32_t)(KB + c0), vi);
+  }
+  tmem_st_wait();
+
+  constexpr uint32_t kIdNeg = idesc<false, true, true>();  // tf32, N = 256, A negated
+  uint32_t phase = 0;
+  bool ok = true;
+#pragma unroll 1
+  for (int p0 = 0; p0 < KB && ok; p0 += PW) {
+    const bool rP = (unsigned)(r - p0) < (unsigned)PW;
+    // my row's entries in the panel's columns
+    uint32_t xr[16], xi[16];
+    tmem_ld16(trow + (uint32_t)p0, xr);
+    tmem_ld16(trow + (uint32_t)(KB + p0), xi);
+    tmem_ld_wait();
+    // the panel's rows to shared memory; in TMEM they are zeroed (mask)
+    if (warp == (p0 >> 5)) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < KB; c0 += 32) {
+        uint32_t ur[32], ui[32];
+        tmem_ld32(trow + (uint32_t)c0, ur);
+        tmem_ld32(trow + (uint32_t)(KB + c0), ui);
+        tmem_ld_wait();
+        if (rP) {
+          float2* w = wrow + (r - p0) * kDgRowStride + c0;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            w[i] = make_float2(__uint_as_float(ur[i]), __uint_as_float(ui[i]));
+            ur[i] = 0u;
+            ui[i] = 0u;
+          }
+        }
+        __syncwarp();
+        tmem_st32(trow + (uint32_t)c0, ur);
+        tmem_st32(trow + (uint32_t)(KB + c0), ui);
+      }
+      tmem_st_wait();
+    }
+    __syncthreads();
+    // warp 0: inv(M_PP) by Gauss-Jordan in registers; lane owns column lane % 16 of rows
+    // lane / 16 + 2 m; the pivot row, column and entry of each step come by shuffle
+    if (warp == 0) {
+      const int cl = lane & 15, q0 = lane >> 4;
+      cpx<float> v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float2 t = wrow[(q0 + 2 * m) * kDgRowStride + p0 + cl];
+        v[m] = {t.x, t.y};
+      }
+#pragma unroll
+      for (int cc = 0; cc < PW; ++cc) {
+        const int own = (cc & 1) * 16;
+        cpx<float> d, pr, pc[8];
+        d.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cc);
+        d.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cc);
+        pr.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cl);
+        pr.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cl);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          pc[m].re = __shfl_sync(0xffffffffu, v[m].re, q0 * 16 + cc);
+          pc[m].im = __shfl_sync(0xffffffffu, v[m].im, q0 * 16 + cc);
+        }
+        const float m2 = d.re * d.re + d.im * d.im;
+        const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
+        const cpx<float> dinv = {d.re * rm, -d.im * rm};
+        if (lane == 0) pivd[p0 + cc] = make_float2(d.re, d.im);
+        const cpx<float> u = cmul(pr, dinv);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int rr = q0 + 2 * m;
+          if (rr == cc) {
+            v[m] = (cl == cc) ? dinv : cmul(v[m], dinv);
+          } else if (cl == cc) {
+            const cpx<float> q2 = cmul(pc[m], dinv);
+            v[m] = {-q2.re, -q2.im};
+          } else {
+            v[m] = {v[m].re - (pc[m].re * u.re - pc[m].im * u.im),
+                    v[m].im - (pc[m].re * u.im + pc[m].im * u.re)};
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) tp[(q0 + 2 * m) * 17 + cl] = make_float2(v[m].re, v[m].im);
+    }
+    // B from the panel's rows: thread c builds rows c and 128 + c of both K sub-tiles
+    {
+      const int c = tid;
+      const bool cP = (unsigned)(c - p0) < (unsigned)PW;
+      float wr[16], wi[16], nwi[16];
+#pragma unroll
+      for (int k = 0; k < PW; ++k) {
+        const float2 w = cP ? make_float2(k == c - p0 ? 1.f : 0.f, 0.f)
+                            : wrow[k * kDgRowStride + c];
+        wr[k] = w.x;
+        wi[k] = w.y;
+        nwi[k] = -w.y;
+      }
+      dg_store_row(opB + 0 * 16384, opB + 1 * 16384, c, wr);
+      dg_store_row(opB + 0 * 16384, opB + 1 * 16384, KB + c, wi);
+      dg_store_row(opB + 2 * 16384, opB + 3 * 16384, c, nwi);
+      dg_store_row(opB + 2 * 16384, opB + 3 * 16384, KB + c, wr);
+    }
+    __syncthreads();  // inv(M_PP) ready; the panel rows are no longer read (A reuses them)
+    // my row of F into A
+    {
+      float fr[16], fi[16];
+      if (rP) {
+#pragma unroll
+        for (int k = 0; k < PW; ++k) {
+          const float2 t = tp[(r - p0) * 17 + k];
+          fr[k] = -t.x;
+          fi[k] = -t.y;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < PW; ++k) { fr[k] = 0.f; fi[k] = 0.f; }
+#pragma unroll
+        for (int m = 0; m < PW; ++m) {
+          const float xre = __uint_as_float(xr[m]), xim = __uint_as_float(xi[m]);
+#pragma unroll
+          for (int k = 0; k < PW; ++k) {
+            const float2 t = tp[m * 17 + k];
+            fr[k] += xre * t.x - xim * t.y;
+            fi[k] += xre * t.y + xim * t.x;
+          }
+        }
+      }
+      dg_store_row(opA + 0 * 8192, opA + 1 * 8192, r, fr);
+      dg_store_row(opA + 2 * 8192, opA + 3 * 8192, r, fi);
+    }
+    __syncwarp();
+    {  // the panel's columns of my row zeroed (mask)
+      uint32_t z[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z[i] = 0u;
+      tmem_st16(trow + (uint32_t)p0, z);
+      tmem_st16(trow + (uint32_t)(KB + p0), z);
+    }
+    tmem_st_wait();
+    fence_proxy_async();  // the operand stores, visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int sub = 0; sub < 2; ++sub) {
+#pragma unroll
+        for (int k8 = 0; k8 < 2; ++k8) {
+          const uint32_t off = (uint32_t)(k8 * 32);
+          const uint64_t a_hi = sdesc_k64(smem_u32(opA + (2 * sub) * 8192) + off);
+          const uint64_t a_lo = sdesc_k64(smem_u32(opA + (2 * sub + 1) * 8192) + off);
+          const uint64_t b_hi = sdesc_k64(smem_u32(opB + (2 * sub) * 16384) + off);
+          const uint64_t b_lo = sdesc_k64(smem_u32(opB + (2 * sub + 1) * 16384) + off);
+          mma_d<false>(tmem, a_hi, b_hi, kIdNeg, 1u);
+          mma_d<false>(tmem, a_hi, b_lo, kIdNeg, 1u);
+          mma_d<false>(tmem, a_lo, b_hi, kIdNeg, 1u);
+        }
+      }
+      mma_commit(mbar);
+    }
+    const bool done = mbar_wait(mbar, phase, abort_flag);
+    phase ^= 1u;
+    tc_fence_after();
+    ok = __syncthreads_and(done ? 1 : 0) != 0;
+  }
+  if (!ok) {
+    // a wait ran out: the last commit may still be outstanding; wait for it (bounded)
+    volatile int drain_abort = 0;
+    if (tid == 0) {
+      (void)mbar_wait(mbar, phase ^ 1u, &drain_abort);
+      atomicOr(flags, 2);
+    }
+  } else {
+    for (int k = tid; k < kb; k += kDgThreads) {
+      const float2 d = pivd[k];
+      piv2[k] = (double)d.x * d.x + (double)d.y * d.y;
+    }
+    __syncthreads();
+    const double lsum = logdet_sum<kDgThreads>(piv2, kb, flags);
+    if (tid == 0) ld[b0 + mat] += lsum;
+    // T (row r) and the -T^T split planes (column r of W_T: coalesced across the warp)
+    float2* T = Tinv + (size_t)mat * 2 * KB * KB;
+    constexpr size_t P = (size_t)KB * KB;
+    float* tt = TT ? TT + (size_t)mat * kTtPlanes * P : nullptr;
+#pragma unroll 1
+    for (int c0 = 0; c0 < KB; c0 += 32) {
+      uint32_t ur[32], ui[32];
+      tmem_ld32(trow + (uint32_t)c0, ur);
+      tmem_ld32(trow + (uint32_t)(KB + c0), ui);
+      tmem_ld_wait();
+      float4* trw = reinterpret_cast<float4*>(T + (size_t)r * KB + c0);
+#pragma unroll
+      for (int i = 0; i < 32; i += 2) {
+        const int j = c0 + i;
+        const bool in0 = r < kb && j < kb, in1 = r < kb && j + 1 < kb;
+        trw[i / 2] = make_float4(in0 ? __uint_as_float(ur[i]) : 0.f,
+                                 in0 ? __uint_as_float(ui[i]) : 0.f,
+                                 in1 ? __uint_as_float(ur[i + 1]) : 0.f,
+                                 in1 ? __uint_as_float(ui[i + 1]) : 0.f);
+      }
+      if (tt) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int j = c0 + i;
+          const bool in = r < kb && j < kb;
+          const float fr = in ? -__uint_as_float(ur[i]) : 0.f;
+          const float fi = in ? -__uint_as_float(ui[i]) : 0.f;
+          const size_t o = (size_t)j * KB + r;
+          if (tt_bf16) {
+            const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi = __float2bfloat16_rn(fi);
+            reinterpret_cast<__nv_bfloat16*>(tt)[o] = hr;
+            reinterpret_cast<__nv_bfloat16*>(tt + P)[o] = hi;
+            reinterpret_cast<__nv_bfloat16*>(tt + 2 * P)[o] =
+                __float2bfloat16_rn(fr - __bfloat162float(hr));
+            reinterpret_cast<__nv_bfloat16*>(tt + 3 * P)[o] =
+                __float2bfloat16_rn(fi - __bfloat162float(hi));
+          } else {
+            const float hr = __uint_as_float(__float_as_uint(fr) & 0xffffe000u);
+            const float hi = __uint_as_float(__float_as_uint(fi) & 0xffffe000u);
+            tt[o] = hr;
+            tt[P + o] = hi;
+            tt[2 * P + o] = fr - hr;
+            tt[3 * P + o] = fi - hi;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kDgTmemCols)
+                 : "memory");
+  }
+}
+
 // ----------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -1001,6 +1383,29 @@ sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool 
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "tcgen05 pivoted prep launch");
   }
+  return SCA_OK;
+}
+
+sca_status tc_diag(const float* M, int ldm, size_t mat_stride, size_t plane_stride, int cnt, int k0,
+                   int kb, int nb, int b0, double* ld, void* Tinv, float* TT, int tt_bf16,
+                   int* flags, cudaStream_t s) {
+  if (nb != 128 || kb < 1 || kb > nb) {
+    set_error("tensor-core pivot-block inverse needs nb = 128");
+    return SCA_EINVAL;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDgSmem);
+    if (err != cudaSuccess) return cuda_fail(err, "tensor-core pivot-block inverse set-up");
+    attr = true;
+  }
+  if (cnt <= 0) return SCA_OK;
+  k_diag_tc<<<cnt, kDgThreads, kDgSmem, s>>>(M, ldm, (long long)mat_stride,
+                                               (long long)plane_stride, k0, kb, b0, ld,
+                                               static_cast<float2*>(Tinv), TT, tt_bf16, flags);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "tensor-core pivot-block inverse launch");
   return SCA_OK;
 }
 
