@@ -826,14 +826,19 @@ __global__ void __launch_bounds__(kDgThreads, 2)
         const float2 t = wrow[(q0 + 2 * m) * kDgRowStride + p0 + cl];
         v[m] = {t.x, t.y};
       }
-#pragma unroll
+      // a rolled loop (the unrolled one is fetch-bound: one warp runs it once per panel)
+#pragma unroll 1
       for (int cc = 0; cc < PW; ++cc) {
-        const int own = (cc & 1) * 16;
+        const int own = (cc & 1) * 16, slot = cc >> 1;
+        cpx<float> vs = v[0];
+#pragma unroll
+        for (int m = 1; m < 8; ++m)
+          if (m == slot) vs = v[m];
         cpx<float> d, pr, pc[8];
-        d.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cc);
-        d.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cc);
-        pr.re = __shfl_sync(0xffffffffu, v[cc >> 1].re, own + cl);
-        pr.im = __shfl_sync(0xffffffffu, v[cc >> 1].im, own + cl);
+        d.re = __shfl_sync(0xffffffffu, vs.re, own + cc);
+        d.im = __shfl_sync(0xffffffffu, vs.im, own + cc);
+        pr.re = __shfl_sync(0xffffffffu, vs.re, own + cl);
+        pr.im = __shfl_sync(0xffffffffu, vs.im, own + cl);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
           pc[m].re = __shfl_sync(0xffffffffu, v[m].re, q0 * 16 + cc);
@@ -843,19 +848,21 @@ __global__ void __launch_bounds__(kDgThreads, 2)
         const float rm = (m2 > 0.f) ? 1.f / m2 : 0.f;
         const cpx<float> dinv = {d.re * rm, -d.im * rm};
         if (lane == 0) pivd[p0 + cc] = make_float2(d.re, d.im);
+        // new entries: pivot row u = v inv(d) (pivot: inv(d)), pivot column -v inv(d), others
+        // v - pc u; chosen by scalar selects (a branch per row serialises the warp)
         const cpx<float> u = cmul(pr, dinv);
+        const bool b = cl == cc;
+        const float yr = b ? dinv.re : u.re, yi = b ? dinv.im : u.im;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-          const int rr = q0 + 2 * m;
-          if (rr == cc) {
-            v[m] = (cl == cc) ? dinv : cmul(v[m], dinv);
-          } else if (cl == cc) {
-            const cpx<float> q2 = cmul(pc[m], dinv);
-            v[m] = {-q2.re, -q2.im};
-          } else {
-            v[m] = {v[m].re - (pc[m].re * u.re - pc[m].im * u.im),
-                    v[m].im - (pc[m].re * u.im + pc[m].im * u.re)};
-          }
+          const bool a = q0 + 2 * m == cc;
+          const float q2r = pc[m].re * dinv.re - pc[m].im * dinv.im;
+          const float q2i = pc[m].re * dinv.im + pc[m].im * dinv.re;
+          const float upr = v[m].re - (pc[m].re * u.re - pc[m].im * u.im);
+          const float upi = v[m].im - (pc[m].re * u.im + pc[m].im * u.re);
+          const float xr = b ? -q2r : upr, xi = b ? -q2i : upi;
+          v[m].re = a ? yr : xr;
+          v[m].im = a ? yi : xi;
         }
       }
 #pragma unroll
@@ -880,32 +887,44 @@ __global__ void __launch_bounds__(kDgThreads, 2)
       dg_store_row(opB + 2 * 16384, opB + 3 * 16384, KB + c, wr);
     }
     __syncthreads();  // inv(M_PP) ready; the panel rows are no longer read (A reuses them)
-    // my row of F into A
-    {
-      float fr[16], fi[16];
+    // my row of F into A, four columns (one 16-byte chunk of each operand row) at a time
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+      float fr[4], fi[4];
       if (rP) {
 #pragma unroll
-        for (int k = 0; k < PW; ++k) {
-          const float2 t = tp[(r - p0) * 17 + k];
+        for (int k = 0; k < 4; ++k) {
+          const float2 t = tp[(r - p0) * 17 + 4 * g + k];
           fr[k] = -t.x;
           fi[k] = -t.y;
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < PW; ++k) { fr[k] = 0.f; fi[k] = 0.f; }
+        for (int k = 0; k < 4; ++k) { fr[k] = 0.f; fi[k] = 0.f; }
 #pragma unroll
         for (int m = 0; m < PW; ++m) {
           const float xre = __uint_as_float(xr[m]), xim = __uint_as_float(xi[m]);
 #pragma unroll
-          for (int k = 0; k < PW; ++k) {
-            const float2 t = tp[m * 17 + k];
+          for (int k = 0; k < 4; ++k) {
+            const float2 t = tp[m * 17 + 4 * g + k];
             fr[k] += xre * t.x - xim * t.y;
             fi[k] += xre * t.y + xim * t.x;
           }
         }
       }
-      dg_store_row(opA + 0 * 8192, opA + 1 * 8192, r, fr);
-      dg_store_row(opA + 2 * 8192, opA + 3 * 8192, r, fi);
+      float hr[4], lr[4], hi[4], li[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        hr[k] = __uint_as_float(__float_as_uint(fr[k]) & 0xffffe000u);
+        lr[k] = fr[k] - hr[k];
+        hi[k] = __uint_as_float(__float_as_uint(fi[k]) & 0xffffe000u);
+        li[k] = fi[k] - hi[k];
+      }
+      const int off = r * 64 + ((g ^ ((r >> 1) & 3)) << 4);
+      *reinterpret_cast<float4*>(opA + 0 * 8192 + off) = make_float4(hr[0], hr[1], hr[2], hr[3]);
+      *reinterpret_cast<float4*>(opA + 1 * 8192 + off) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+      *reinterpret_cast<float4*>(opA + 2 * 8192 + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<float4*>(opA + 3 * 8192 + off) = make_float4(li[0], li[1], li[2], li[3]);
     }
     __syncwarp();
     {  // the panel's columns of my row zeroed (mask)
