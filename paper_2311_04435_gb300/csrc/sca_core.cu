@@ -327,10 +327,42 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   int* s_val = s_pos + 2 * kb;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
-  for (int e = tid; e < m * kb; e += NT) {
-    const int r = e / kb, c = e - r * kb;
-    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    P[r * ps + c] = {(C)re[o], (C)im[o]};
+  if (sizeof(S) == 4 && kb % 4 == 0 && k0 % 4 == 0 && ldm % 4 == 0) {
+    // float4 loads of 4 consecutive entries of one plane, LB of them in flight per thread
+    constexpr int LB = 8;
+    const int q4 = kb / 4, per_row = 2 * q4, tot = m * per_row;
+    for (int e0 = tid; e0 < tot; e0 += NT * LB) {
+      float4 v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int e = e0 + NT * u;
+        if (e < tot) {
+          const int r = e / per_row, x = e - r * per_row;
+          const int pl = x / q4, c4 = (x - pl * q4) * 4;
+          const S* src = (pl == 0 ? re : im) + (size_t)(k0 + r) * ldm + k0 + c4;
+          v[u] = *reinterpret_cast<const float4*>(src);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int e = e0 + NT * u;
+        if (e < tot) {
+          const int r = e / per_row, x = e - r * per_row;
+          const int pl = x / q4, c4 = (x - pl * q4) * 4;
+          C* dst = reinterpret_cast<C*>(P + r * ps + c4) + pl;  // .re or .im of 4 entries
+          dst[0] = (C)v[u].x;
+          dst[2] = (C)v[u].y;
+          dst[4] = (C)v[u].z;
+          dst[6] = (C)v[u].w;
+        }
+      }
+    }
+  } else {
+    for (int e = tid; e < m * kb; e += NT) {
+      const int r = e / kb, c = e - r * kb;
+      const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+      P[r * ps + c] = {(C)re[o], (C)im[o]};
+    }
   }
   __syncthreads();
   // argmax of |z|^2 over rows >= c of column c: thread-local candidates, then warp shuffles,

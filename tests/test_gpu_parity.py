@@ -314,6 +314,33 @@ def test_symmetric_update_matches_full_update(monkeypatch):
     assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 2 * t["g"] * max(1.0, np.abs(o_gd).max())
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+def test_tensor_core_pivot_block_inverse_matches_register_kernel(prec, monkeypatch):
+    """The dominant pivot-block inverse on the tensor cores (tableau in TMEM, split-TF32
+    rank-16 updates) and the register Gauss-Jordan kernel give log-dets, diag(G), Omega and the
+    gradient that match the oracle and each other.  400 x 400 blocks: three full 128-wide pivot
+    blocks and a ragged 16-wide last one (identity padding inside the 128 x 128 tableau)."""
+    p = api.Params(20, 10, U=4.0, T=0.1, delta=0.5, prec=prec)
+    phi = inputs.seed_phi(9, p.N)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCA_DIAG_TC", flag)
+        with api.Context(p) as c:
+            ld, gd = c.blocks(phi, grad=True)
+            om_lu = c.potential(phi)
+            om, g = c.grad(phi)
+        res[flag] = (ld, gd, om_lu, om, g)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    for ld, gd, om_lu, om, g in res.values():
+        assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+        assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+        assert om == pytest.approx(o_om, rel=t["om"]) and om_lu == pytest.approx(o_om, rel=t["om"])
+        assert np.max(np.abs(g - o_g)) <= t["g"] * max(1.0, np.abs(o_g).max()) * 10
+    assert np.allclose(res["1"][0], res["0"][0], rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 2 * t["g"] * max(1.0, np.abs(o_gd).max())
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_no_pivoting_matches_oracle(prec):
     """Every block eliminated without interchanges (complex-symmetric elimination), including
