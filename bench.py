@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--sm-partition", type=int, default=DEFAULT_SM_PARTITION,
                     help="SMs kept free of the dominant group's launches (0 = none, "
                          "-1 = the library's default for the problem)")
+    ap.add_argument("--sm-partition-mode", default="dominant",
+                    choices=["dominant", "both", "alternate"],
+                    help="partition mode when --sm-partition > 0")
     ap.add_argument("--metro-steps", type=int, default=10,
                     help="timed Metropolis steps (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
@@ -228,8 +231,8 @@ def run_ours(args):
     # ---------------- device-resident timing (inputs resident in HBM)
     ctx = api.Context(params)
     ctx.set_stream(stream)
-    partition = list(ctx.set_sm_partition(args.sm_partition) if args.sm_partition >= 0
-                     else ctx.sm_partition())
+    partition = list(ctx.set_sm_partition(args.sm_partition, args.sm_partition_mode)
+                     if args.sm_partition >= 0 else ctx.sm_partition())
     ctx.adam_init(adam)
     ctx.adam_step(args.warmup)
     l0 = api.kernel_launches()
@@ -275,7 +278,7 @@ def run_ours(args):
     ctx2 = api.Context(params)
     ctx2.set_stream(stream)
     if args.sm_partition >= 0:
-        ctx2.set_sm_partition(args.sm_partition)
+        ctx2.set_sm_partition(args.sm_partition, args.sm_partition_mode)
     ctx2.adam_init(adam, phi0)
     ctx2.adam_step(max(1, args.warmup))
     torch.cuda.synchronize()
@@ -405,6 +408,8 @@ def run_ours(args):
                                    f"{2 * wl.n_omega} complex {params.N}x{params.N} blocks",
                        "prec": prec, "parallelism": f"replicas x{world}",
                        "sm_partition": partition,
+                       "sm_partition_mode": (args.sm_partition_mode if args.sm_partition > 0
+                                             else "library default"),
                        "l2": "inputs larger than L2 (blocks resident in HBM, "
                              f"{api.workspace_bytes(params) / 1e9:.1f} GB)",
                        "final_omega": om, "final_gmax": gm},

@@ -321,15 +321,22 @@ sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
  * partition, every launch of the dominant group stays on the SMs outside a set of
  * `pivoted_sms` SMs (rounded up by the driver to its granularity, 8 on this GPU), so the
  * pivoted chain never waits for a dominant CTA to leave an SM.  Modes: 1 the pivoted group
- * may still use any SM (highest stream priority), 2 it is confined to its own set as well.
+ * may still use any SM (highest stream priority), 2 it is confined to its own set as well,
+ * 3 as 1, and the dominant group's pivot-block inverses and prep products run on a second
+ * partition that leaves twice as many SMs to the pivoted group, its updates on the first (in
+ * between the two sizes, which the driver's 8-SM granularity does not offer).
  * pivoted_sms = 0 removes the partition (the dominant group's persistent tensor-core launches
  * then leave 8 SMs free, and priorities do the rest).  Contexts with 1024 <= N <= 2048 and at
- * least 64 dominant blocks start with a partition of 8 SMs in mode 1 when the driver grants it.
+ * least 64 dominant blocks start with a partition of 8 SMs in mode 3 when the driver grants it.
  * Needs the
  * tensor-core path; results do not depend on the partition (tile order and reductions are
  * fixed).  SCA_ECUDA when the driver refuses the partition; the context then keeps its
  * ordinary streams.  sca_sm_partition reports the SM counts in use (0, 0 without one). */
-typedef enum { SCA_PARTITION_DOMINANT = 1, SCA_PARTITION_BOTH = 2 } sca_partition_mode;
+typedef enum {
+  SCA_PARTITION_DOMINANT = 1,
+  SCA_PARTITION_BOTH = 2,
+  SCA_PARTITION_ALTERNATE = 3
+} sca_partition_mode;
 sca_status sca_set_sm_partition(sca_ctx* ctx, int32_t pivoted_sms, int32_t mode);
 sca_status sca_sm_partition(sca_ctx* ctx, int32_t* pivoted_sms, int32_t* dominant_sms);
 

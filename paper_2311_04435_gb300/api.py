@@ -260,8 +260,11 @@ class Context:
     def set_sm_partition(self, pivoted_sms: int = 0, mode: str = "dominant"):
         """Keep the dominant group's launches off `pivoted_sms` SMs (green contexts); mode
         'dominant' leaves the pivoted group free to use any SM, 'both' confines it to its
-        set.  0 removes the partition.  Returns the SM counts in use (pivoted, dominant)."""
-        modes = {"dominant": 1, "both": 2}
+        set, 'alternate' is 'dominant' with the dominant group's pivot-block inverses and
+        prep products on a second partition that leaves twice as many SMs free (the library's
+        default where it sets one).  0 removes the partition.
+        Returns the SM counts in use (pivoted, dominant)."""
+        modes = {"dominant": 1, "both": 2, "alternate": 3}
         if mode not in modes:
             raise ValueError(f"partition mode must be one of {sorted(modes)}")
         check(_lib.lib().sca_set_sm_partition(self._h, int(pivoted_sms), modes[mode]))

@@ -114,6 +114,7 @@ sca_status plan(const sca_params& p, Engine& e) {
   if (nbp < e.nb) nbp = std::min(nbp, 16);
   e.nb_piv = nbp;
   if (const char* v = std::getenv("SCA_DIAG_TC")) e.diag_tc = std::atoi(v) != 0;
+  if (const char* v = std::getenv("SCA_ALT_POLICY")) e.alt_policy = std::min(3, std::max(1, std::atoi(v)));
   e.ldm = (int)round_up((size_t)e.N, 32);
   e.chunk = e.B;
   if (const char* v = std::getenv("SCA_MAX_BLOCKS_RESIDENT")) {
@@ -210,7 +211,7 @@ sca_status allocate(Engine& e) {
   err = cudaEventCreateWithFlags(&e.ev_join2, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "join event"); }
   if (e.tc && e.piv_blocks > 0 && e.N >= 1024 && e.N <= 2048 && e.B - e.piv_blocks >= 64)
-    (void)partition_setup(e, kDefaultPartitionSms, 1);  // ordinary streams if refused
+    (void)partition_setup(e, kDefaultPartitionSms, 3);  // ordinary streams if refused
   return SCA_OK;
 }
 
@@ -818,8 +819,9 @@ sca_status sca_set_pivoting(sca_ctx* c, int32_t mode) {
 }
 
 sca_status sca_set_sm_partition(sca_ctx* c, int32_t pivoted_sms, int32_t mode) {
-  if (!c || pivoted_sms < 0 || (pivoted_sms > 0 && mode != SCA_PARTITION_DOMINANT &&
-                                mode != SCA_PARTITION_BOTH)) {
+  if (!c || pivoted_sms < 0 ||
+      (pivoted_sms > 0 && mode != SCA_PARTITION_DOMINANT && mode != SCA_PARTITION_BOTH &&
+       mode != SCA_PARTITION_ALTERNATE)) {
     set_error("bad context, SM count or partition mode");
     return SCA_EINVAL;
   }

@@ -1850,9 +1850,36 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   bool sym = tcg && !pivoted && e.tt != nullptr;
   if (const char* v = std::getenv("SCA_SYM"))
     if (std::atoi(v) == 0) sym = false;
+  // SM partition mode 3: some of the dominant group's launches run on the second partition
+  // (more SMs left to the pivoted group), by step and phase (alt_policy); each switch of
+  // stream is ordered by an event
+  const bool alt = !pivoted && e.alt_on && e.dom_alt && e.aux_alt && e.ev_alt;
+  const cudaStream_t s_home = s, aux_home = e.aux;
+  const int cap_home = e.tc_cap;
+  auto switch_to = [&](bool second) -> cudaError_t {
+    const cudaStream_t next = second ? e.dom_alt : s_home;
+    e.aux = second ? e.aux_alt : aux_home;
+    e.tc_cap = second ? e.alt_sms : cap_home;
+    if (next == s) return cudaSuccess;
+    cudaError_t err = cudaEventRecord(e.ev_alt, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(next, e.ev_alt, 0);
+    s = next;
+    return err;
+  };
   for (int k0 = 0; k0 < N; k0 += nb) {
     const int kb = std::min(nb, N - k0);
     const int kend = k0 + kb;
+    const bool odd = ((k0 / nb) & 1) != 0;
+    // policy 1: odd steps on the second partition; 2 (default): every step's pivot-block
+    // inverse and prep products there, the updates (HBM-bound, they want every SM) on the
+    // first; 3: both (odd steps whole, even steps' prep there).  40x40: all three within
+    // 0.1 ms of each other, 0.5 ms faster than mode 1; 1 and 3 cost the update 0.02 of HBM.
+    const bool pre2 = alt && (e.alt_policy == 1 ? odd : true);
+    const bool upd2 = alt && (e.alt_policy == 2 ? false : odd);
+    if (alt) {
+      const cudaError_t err = switch_to(pre2);
+      if (err != cudaSuccess) return cuda_fail(err, "partition switch");
+    }
     if (pivoted) {
       // outer panel [k0, kend) factorised by shared-memory sub-panels of width nbi
       const int nbi = std::min(e.nb_piv, kb);
@@ -2002,6 +2029,10 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       prof_end(e, pivoted ? kPrepPiv : kPrep, s);
       SCA_LAUNCH_CHECK("prep");
     }
+    if (alt) {
+      const cudaError_t err = switch_to(upd2);
+      if (err != cudaSuccess) return cuda_fail(err, "partition switch");
+    }
     const int ukind = pivoted ? kUpdatePiv : kUpdate;
     prof_begin(e, ukind, s);
     if (tcg) {
@@ -2014,6 +2045,10 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       SCA_LAUNCH_CHECK("update");
     }
     prof_end(e, ukind, s);
+  }
+  if (alt) {
+    const cudaError_t err = switch_to(false);
+    if (err != cudaSuccess) return cuda_fail(err, "partition switch");
   }
   if (sym && want_grad) {  // the fully swept inverse is symmetric: fill the upper tiles
     const int nt = (N + 31) / 32;
@@ -2088,6 +2123,7 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       if (parted) {
         e.tc_cap = e.part_sms[1];
         if (e.aux) e.aux = e.part_aux;
+        e.alt_on = e.dom_alt != nullptr;
       } else if (fork && e.sm_reserve > 0 && e.tmap) {
         e.tc_cap = tc_sms(e) - e.sm_reserve;
       }
@@ -2099,6 +2135,7 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       }
       e.tc_cap = 0;
       e.aux = aux_saved;
+      e.alt_on = false;
       if (r == SCA_OK) prof_span_end(e, span_d, sd);
       return r;
     };

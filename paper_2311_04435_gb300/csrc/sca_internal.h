@@ -106,6 +106,14 @@ struct Engine {
   cudaStream_t dom = nullptr, part_aux = nullptr, part_side = nullptr;
   cudaEvent_t ev_join2 = nullptr;
   int part_sms[2] = {0, 0};
+  // mode 3: a second dominant partition that leaves twice as many SMs free; the dominant
+  // group's elimination steps alternate between the two (odd steps on dom_alt / aux_alt)
+  void* green_alt = nullptr;
+  cudaStream_t dom_alt = nullptr, aux_alt = nullptr;
+  cudaEvent_t ev_alt = nullptr;
+  int alt_sms = 0;     // SMs of the second dominant partition
+  bool alt_on = false; // set while the dominant group runs on its partition streams
+  int alt_policy = 2;  // which launches use the second partition (run_group)
   int* tc_counters = nullptr;       // tile counters of the tensor-core launches of one pass
   int tc_next = 0;
   int tc_cap = 0;                   // CTA cap of the next tensor-core launches (0: one per SM)

@@ -65,9 +65,85 @@ __global__ void k_partition_probe(int* flag) {
 
 }  // namespace
 
+namespace {
+
+// A green context over all SMs but `free_sms` and two streams on it (probed with one launch
+// each and joined back to `join`).  False leaves nothing behind.
+bool make_rest_ctx(int free_sms, cudaStream_t join, int* flag, CUgreenCtx* ctx, CUstream* s0,
+                   CUstream* s1, int* rest_sms) {
+  const GreenApi& g = api();
+  int ordinal = 0;
+  if (cudaGetDevice(&ordinal) != cudaSuccess) return false;
+  CUdevice dev;
+  CUdevResource all, part, rest;
+  std::memset(&all, 0, sizeof(all));
+  std::memset(&part, 0, sizeof(part));
+  std::memset(&rest, 0, sizeof(rest));
+  unsigned groups = 1;
+  if (g.device_get(&dev, ordinal) != CUDA_SUCCESS) return false;
+  if (g.get_resource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) return false;
+  if ((unsigned)free_sms >= all.sm.smCount) return false;
+  if (g.split(&part, &groups, &all, &rest, 0, (unsigned)free_sms) != CUDA_SUCCESS || groups != 1 ||
+      rest.sm.smCount == 0)
+    return false;
+  CUdevResourceDesc dd = nullptr;
+  if (g.make_desc(&dd, &rest, 1) != CUDA_SUCCESS) return false;
+  CUgreenCtx gd = nullptr;
+  CUstream a = nullptr, b = nullptr;
+  bool good = g.ctx_create(&gd, dd, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS;
+  good = good && g.stream_create(&a, gd, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+  good = good && g.stream_create(&b, gd, CU_STREAM_NON_BLOCKING, 0) == CUDA_SUCCESS;
+  cudaEvent_t ev = nullptr;
+  good = good && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+  for (CUstream st : {a, b}) {
+    if (!good) break;
+    k_partition_probe<<<1, 32, 0, (cudaStream_t)st>>>(flag);
+    good = cudaGetLastError() == cudaSuccess && cudaEventRecord(ev, (cudaStream_t)st) == cudaSuccess &&
+           cudaStreamWaitEvent(join, ev, 0) == cudaSuccess &&
+           cudaStreamSynchronize(join) == cudaSuccess &&
+           cudaStreamSynchronize((cudaStream_t)st) == cudaSuccess;
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (good) good = cudaMemset(flag, 0, sizeof(int)) == cudaSuccess;
+  if (!good) {
+    (void)cudaGetLastError();
+    for (CUstream st : {a, b})
+      if (st) g.stream_destroy(st);
+    if (gd) g.ctx_destroy(gd);
+    return false;
+  }
+  *ctx = gd;
+  *s0 = a;
+  *s1 = b;
+  *rest_sms = (int)rest.sm.smCount;
+  return true;
+}
+
+}  // namespace
+
 bool partition_setup(Engine& e, int piv_sms, int mode) {
   const GreenApi& g = api();
-  if (!g.ok || piv_sms <= 0 || (mode != 1 && mode != 2)) return false;
+  if (!g.ok || piv_sms <= 0 || (mode != 1 && mode != 2 && mode != 3)) return false;
+  if (mode == 3) {
+    // mode 1, plus a second dominant partition with twice the free SMs for odd steps
+    if (!partition_setup(e, piv_sms, 1)) return false;
+    CUgreenCtx ga = nullptr;
+    CUstream sa = nullptr, sb = nullptr;
+    int rest = 0;
+    if (cudaEventCreateWithFlags(&e.ev_alt, cudaEventDisableTiming) != cudaSuccess ||
+        !make_rest_ctx(2 * e.part_sms[0], e.side, e.flags + 1, &ga, &sa, &sb, &rest) ||
+        rest >= e.part_sms[1]) {
+      (void)cudaGetLastError();
+      if (ga) g.ctx_destroy(ga);
+      partition_release(e);
+      return false;
+    }
+    e.green_alt = ga;
+    e.dom_alt = (cudaStream_t)sa;
+    e.aux_alt = (cudaStream_t)sb;
+    e.alt_sms = rest;
+    return true;
+  }
   int ordinal = 0;
   if (cudaGetDevice(&ordinal) != cudaSuccess) return false;
   CUdevice dev;
@@ -131,6 +207,22 @@ bool partition_setup(Engine& e, int piv_sms, int mode) {
 void partition_release(Engine& e) {
   const GreenApi& g = api();
   if (!g.ok) return;
+  for (cudaStream_t* st : {&e.dom_alt, &e.aux_alt})
+    if (*st) {
+      cudaStreamSynchronize(*st);
+      g.stream_destroy((CUstream)*st);
+      *st = nullptr;
+    }
+  if (e.green_alt) {
+    g.ctx_destroy((CUgreenCtx)e.green_alt);
+    e.green_alt = nullptr;
+  }
+  if (e.ev_alt) {
+    cudaEventDestroy(e.ev_alt);
+    e.ev_alt = nullptr;
+  }
+  e.alt_sms = 0;
+  e.alt_on = false;
   for (cudaStream_t* s : {&e.dom, &e.part_aux, &e.part_side})
     if (*s) {
       cudaStreamSynchronize(*s);

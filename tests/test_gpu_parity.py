@@ -446,7 +446,7 @@ def test_profile_timeline_file(tmp_path, monkeypatch):
     assert streams["span_pivoted"] != streams["span_dominant"]
 
 
-@pytest.mark.parametrize("mode", ["dominant", "both"])
+@pytest.mark.parametrize("mode", ["dominant", "both", "alternate"])
 def test_sm_partition_leaves_results_unchanged(mode):
     """SM partitions (green contexts) only move launches between SMs: Omega and the
     gradient are bit-identical with and without them, and removing one restores the plain
