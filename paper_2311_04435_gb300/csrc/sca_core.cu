@@ -1919,7 +1919,8 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     bool w_aux = false;
     if (sym && !last_lu && e.aux) {
       // the W^T planes do not depend on the pivot-block inverse: build them on the auxiliary
-      // stream while the inverse runs (its second wave leaves SMs idle)
+      // stream while the inverse runs (both are short; side by side or in sequence they take
+      // the same time, and the stream keeps them independent of each other)
       cudaError_t err = cudaEventRecord(e.ev_aux0, s);
       if (err == cudaSuccess) err = cudaStreamWaitEvent(e.aux, e.ev_aux0, 0);
       if (err != cudaSuccess) return cuda_fail(err, "aux fork");
