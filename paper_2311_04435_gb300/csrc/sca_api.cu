@@ -211,7 +211,10 @@ sca_status allocate(Engine& e) {
   err = cudaEventCreateWithFlags(&e.ev_join2, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "join event"); }
   if (e.tc && e.piv_blocks > 0 && e.N >= 1024 && e.N <= 2048 && e.B - e.piv_blocks >= 64)
-    (void)partition_setup(e, kDefaultPartitionSms, 3);  // ordinary streams if refused
+    // two dominant partitions (mode 3); one if the driver refuses the second; ordinary
+    // streams if it refuses both
+    if (!partition_setup(e, kDefaultPartitionSms, 3))
+      (void)partition_setup(e, kDefaultPartitionSms, 1);
   return SCA_OK;
 }
 
