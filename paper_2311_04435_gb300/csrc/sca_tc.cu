@@ -826,7 +826,8 @@ __global__ void __launch_bounds__(kDgThreads, 2)
         const float2 t = wrow[(q0 + 2 * m) * kDgRowStride + p0 + cl];
         v[m] = {t.x, t.y};
       }
-      // a rolled loop (the unrolled one is fetch-bound: one warp runs it once per panel)
+      // a rolled loop: the pivot's slot is picked by selects and the row update below has no
+      // branches, so one short body serves all 16 pivots
 #pragma unroll 1
       for (int cc = 0; cc < PW; ++cc) {
         const int own = (cc & 1) * 16, slot = cc >> 1;
