@@ -11,6 +11,12 @@ partial pivoting, explicit inverse columns, a Jacobi eigenvalue route and
 explicit Adam); this file compiles it with gcc and exposes it through ctypes.
 Every function documents the passage of the paper it follows in the C source.
 
+A second, numpy-level route (``omega_grad_spectral`` / ``adam_run_spectral``) takes the
+same Omega and gradient from the eigenvalues of H_sigma (LAPACK's symmetric eigensolver
+through ``numpy.linalg.eigh`` as the library step): one diagonalisation per spin replaces
+the n_omega LU factorisations, which lets the oracle run Adam to convergence on lattices
+of 256..400 sites in seconds.
+
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle_pins.py`` (Fourier closed forms at phi = 0 and for a
 staggered field, the eigenvalue route, finite differences, the Hartree-Fock
@@ -21,6 +27,7 @@ through the per-step quantities above ("parity unpinned" for the basin itself).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -270,3 +277,65 @@ def adam_run(p: Params, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, grad_tol=0.0,
     if history:
         return out + (oh[: steps.value + 1 if steps.value < max_steps else max_steps], gh[: steps.value + 1 if steps.value < max_steps else max_steps])
     return out
+
+
+# ------------------------------------------------------------ spectral route (numpy)
+
+def omega_grad_spectral(p: Params, phi, eps_extra=None):
+    """Omega and dOmega/dphi from the eigen-decomposition H_sigma = V diag(e) V^T.
+
+    Eq. 2 with a real symmetric H_sigma: det[(i w_n + mu) I - H_sigma] = prod_a (i w_n + mu - e_a),
+    so with x_a = mu - e_a
+        ln|det A_{n,sigma}| = 1/2 sum_a ln(w_n^2 + x_a^2),
+        Re G_{n sigma, ii}  = sum_a V_ia^2 x_a / (w_n^2 + x_a^2),
+    and Omega = sum_i phi_i^2/U - 2T sum_{n,sigma} ln|det A_{n,sigma}|,
+        g_i = 2 phi_i/U - 2T sum_{n,sigma} sigma Re G_{n sigma, ii}
+    (the n >= 0 half of the Matsubara sum with the factor 2, as in the LU route).  H_sigma is
+    the LU route's own Eq. 1 matrix (orc_hamiltonian); numpy.linalg.eigh is the library step."""
+    N = p.L * p.L
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    w = np.array([omega_n(p, n) for n in range(p.n_omega)])
+    om = float(np.sum(phi * phi) / p.U)
+    g = 2.0 * phi / p.U
+    for sg in (1, -1):
+        e, V = np.linalg.eigh(hamiltonian(p, phi, sg, eps_extra))
+        x = p.mu - e
+        den = w[None, :] ** 2 + x[:, None] ** 2          # (a, n)
+        om -= 2.0 * p.T * 0.5 * float(np.log(den).sum())
+        f = (x[:, None] / den).sum(axis=1)               # sum over n of Re 1/(i w_n + x_a)
+        g -= 2.0 * p.T * sg * ((V * V) @ f)
+    assert g.shape == (N,)
+    return om, g
+
+
+def adam_run_spectral(p: Params, phi0, lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, grad_tol=0.0,
+                      max_steps=100, eps_extra=None):
+    """Adam (Sec. II: ADAM on V(phi); Kingma & Ba 2014, PyTorch's arithmetic order, as
+    orc_adam_run) on the spectral-route gradient, from phi0.  The loop evaluates Omega and g at
+    phi_k, stops when max|g| < grad_tol or after max_steps updates, else applies update k+1.
+    Returns (phi, updates applied, Omega and max|g| at the final phi)."""
+    phi = np.array(phi0, dtype=np.float64, copy=True)
+    m = np.zeros_like(phi)
+    v = np.zeros_like(phi)
+    k = 0
+    while True:
+        om, g = omega_grad_spectral(p, phi, eps_extra)
+        gm = float(np.abs(g).max())
+        if gm < grad_tol or k >= max_steps:
+            break
+        k += 1
+        step = lr / (1.0 - beta1 ** k)
+        sbc2 = math.sqrt(1.0 - beta2 ** k)
+        m = beta1 * m + (1.0 - beta1) * g
+        v = beta2 * v + (1.0 - beta2) * g * g
+        phi -= step * m / (np.sqrt(v) / sbc2 + eps)
+    return phi, k, om, gm
+
+
+def staggered_order(phi, L: int):
+    """The two readings of |phi| (the paper leaves the reduction open): the staggered
+    magnetisation |N^-1 sum_i s_i phi_i| and the mean magnitude N^-1 sum_i |phi_i|."""
+    x, y = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    s = np.where((x + y) % 2 == 0, 1.0, -1.0).reshape(-1)
+    phi = np.asarray(phi, dtype=np.float64)
+    return float(abs(np.mean(s * phi))), float(np.mean(np.abs(phi)))

@@ -456,3 +456,84 @@ def test_paper_trend_neel_temperature_grows_with_U():
     assert phi_star(4.0, 0.6) > 0.5 and phi_star(6.0, 0.6) > 0.5
     assert phi_star(4.0, 1.0) < 1e-3 < 1.0 < phi_star(6.0, 1.0)
     assert phi_star(6.0, 1.5) < 1e-3
+
+
+# ------------------------------------------------- spectral route (Adam to convergence) ---
+
+@pytest.mark.parametrize("L,ionic", [(4, 0), (6, 1)])
+def test_spectral_route_matches_lu_route(L, ionic):
+    """The eigenvalue route of omega_grad_spectral against the dense-LU route (itself pinned by
+    the closed forms and LAPACK above) at a random field with a random site potential."""
+    p = oracle.make_params(L, 9, U=4.0, T=0.08, delta=0.6, mu=0.2, ionic=ionic)
+    phi = inputs.random_phi(40 + L, L * L, 1.3)
+    ee = inputs.random_phi(50 + L, L * L, 0.7)
+    om_s, g_s = oracle.omega_grad_spectral(p, phi, ee)
+    om_l, g_l = oracle.omega_grad(p, phi, ee)
+    assert om_s == pytest.approx(om_l, rel=1e-12)
+    assert np.max(np.abs(g_s - g_l)) <= 1e-11 * max(1.0, np.abs(g_l).max())
+
+
+def test_spectral_adam_follows_lu_adam():
+    """adam_run_spectral against orc_adam_run (the C loop, pinned against torch.optim.Adam):
+    the same 150 updates from the same start with disorder agree to rounding."""
+    p = oracle.make_params(4, 16, U=6.0, T=0.1, delta=0.3)
+    ee = inputs.random_phi(3, 16, 0.4)
+    phi0 = inputs.seed_phi(3, 16)
+    phi_s, k_s, om_s, gm_s = oracle.adam_run_spectral(p, phi0, lr=0.02, max_steps=150, eps_extra=ee)
+    phi_l, k_l, om_l, gm_l = oracle.adam_run(p, lr=0.02, max_steps=150, phi0=phi0, eps_extra=ee)
+    assert k_s == k_l == 150
+    assert np.max(np.abs(phi_s - phi_l)) < 1e-11
+    assert om_s == pytest.approx(om_l, rel=1e-12)
+
+
+def test_spectral_adam_gate_counts_like_lu_adam():
+    """The convergence gate: both loops stop at the same update when max|g| falls below the
+    tolerance, and report Omega and max|g| at the final field."""
+    p = oracle.make_params(4, 16, U=6.0, T=0.1)
+    phi0 = inputs.neel_phi(4, 1.0) + 0.05 * inputs.seed_phi(9, 16)
+    r_s = oracle.adam_run_spectral(p, phi0, lr=0.02, grad_tol=1e-5, max_steps=2000)
+    r_l = oracle.adam_run(p, lr=0.02, grad_tol=1e-5, max_steps=2000, phi0=phi0)
+    assert r_s[1] == r_l[1] < 2000
+    assert r_s[3] < 1e-5 and r_l[3] < 1e-5
+    assert np.max(np.abs(r_s[0] - r_l[0])) < 1e-11
+
+
+def test_spectral_adam_from_neel_reaches_closed_form_minimum():
+    """An 8x8 ionic lattice started from a perturbed Neel field converges to the uniform AF
+    minimum of the staggered closed form: the root a* of d(Omega/N)/da for phi_i = a s_i,
+        2a/U - T sum_{sigma,n} N^-1 sum_k 2 sigma (Delta + sigma a) / (w_n^2 + eps_k^2 + (Delta + sigma a)^2)."""
+    from scipy.optimize import brentq
+
+    L, U, T, M, De = 8, 6.0, 0.1, 32, 0.5
+    p = oracle.make_params(L, M, U=U, T=T, delta=De)
+    phi0 = inputs.neel_phi(L, 1.0) + 0.1 * inputs.seed_phi(7, L * L)
+    phi, k, om, gm = oracle.adam_run_spectral(p, phi0, lr=0.01, grad_tol=1e-9, max_steps=5000)
+    e2 = bz_eps(L) ** 2
+    w2 = ((2 * np.arange(M) + 1) * math.pi * T) ** 2
+
+    def dcurve(a):
+        out = 2 * a / U
+        for sg in (1, -1):
+            D = De + sg * a
+            out -= T * np.sum(2 * sg * D / (w2[:, None] + e2[None, :] + D * D)) / (L * L)
+        return out
+
+    a_star = brentq(dcurve, 0.5, 4.0, xtol=1e-15, rtol=1e-15)
+    stag, mean = oracle.staggered_order(phi, L)
+    assert gm < 1e-9 and k < 5000
+    # max|g| < 1e-9 leaves phi within ~1e-9 / (smallest curvature) of the minimum
+    assert stag == pytest.approx(a_star, abs=1e-8) and mean == pytest.approx(a_star, abs=1e-8)
+    om_star = _omega_staggered_curve(L, U, T, De, M, np.array([a_star]))[0]
+    assert om / (L * L) == pytest.approx(om_star, rel=1e-12)
+
+
+def test_staggered_order_readings():
+    """stag|phi| and mean|phi| (reading c9): equal for a Neel field, different for a field
+    with a domain wall, zero stag for a uniform one."""
+    L = 4
+    neel = inputs.neel_phi(L, 0.7)
+    assert oracle.staggered_order(neel, L) == pytest.approx((0.7, 0.7))
+    wall = neel.copy()
+    wall[: L * L // 2] *= -1.0
+    assert oracle.staggered_order(wall, L) == pytest.approx((0.0, 0.7))
+    assert oracle.staggered_order(np.full(L * L, 0.3), L)[0] == pytest.approx(0.0)
