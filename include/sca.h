@@ -177,6 +177,16 @@ sca_status sca_adam_init(sca_ctx* ctx, const sca_adam* adam, const double* phi0_
  * Errors: SCA_ENOSTATE (no sca_adam_init), SCA_ENONFINITE, SCA_ECUDA. */
 sca_status sca_adam_step(sca_ctx* ctx, int32_t nsteps, double* omega, double* gmax);
 
+/* Runs Adam on the context's resident state with the convergence gate of sca_solve: each
+ * update is applied only while max|g| >= grad_tol (the settings of sca_adam_init or
+ * sca_set_state), and the call returns once an evaluation finds max|g| < grad_tol or after
+ * max_steps >= 0 updates.  *steps receives the updates this call applied; *omega and *gmax
+ * receive Omega and max|g| at the final phi (any may be NULL).  Unlike sca_solve it keeps the
+ * context's site energies (sca_set_site_energy), pivoting mode and stream.  Errors:
+ * SCA_EINVAL, SCA_ENOSTATE (no sca_adam_init), SCA_ENONFINITE, SCA_ETIMEOUT, SCA_ECUDA. */
+sca_status sca_adam_run(sca_ctx* ctx, int32_t max_steps, int32_t* steps, double* omega,
+                        double* gmax);
+
 /* Copies the current phi (N doubles) to host memory. */
 sca_status sca_get_phi(sca_ctx* ctx, double* phi_out);
 
@@ -232,6 +242,23 @@ sca_status sca_request_times(sca_server* srv, uint64_t req_id, double* submit_s,
 /* Stops the loop (in-flight requests are abandoned) and frees everything. */
 void sca_server_destroy(sca_server* srv);
 
+/* A server without a worker thread, for replaying an arrival trace deterministically: the
+ * caller drives it with sca_server_step, and its clock is virtual (the times of
+ * sca_request_times are the now_s values of the steps, and a submission is stamped with the
+ * clock of the last step).  Admission, batching and retirement are those of the threaded
+ * server, so a replay of the same submissions and steps gives the same admission order,
+ * in-flight counts, update counts, times and results, bit for bit.  Errors as
+ * sca_server_create. */
+sca_status sca_server_create_manual(uint64_t hbm_budget_bytes, int32_t max_slots,
+                                    sca_server** out);
+
+/* One round of a manual server at virtual time now_s (non-decreasing): admission of queued
+ * requests, one batch of gated Adam updates for every request in flight, retirement of the
+ * finished ones.  *in_flight and *queued (may be NULL) receive the requests running and
+ * waiting after the round.  Runs on the calling thread and returns when the round is done.
+ * Errors: SCA_EINVAL (not a manual server, clock running backwards). */
+sca_status sca_server_step(sca_server* srv, double now_s, int32_t* in_flight, int32_t* queued);
+
 /* ------------------------------------------------------ allocation-free ---- */
 
 /* Omega and dOmega/dphi like sca_grad_dev, without allocating any memory.  (The paper has
@@ -246,8 +273,10 @@ void sca_server_destroy(sca_server* srv);
  *    library holds until the process exits.  The blocks are processed in chunks that fit
  *    it; a problem whose single block (plus the per-block log-dets and diagonals) does not
  *    fit is rejected with SCA_EINVAL and a message, before anything is enqueued.
- *  - The first call on each device looks up the array's device address (set-up on the
- *    calling thread's current device); make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the calling thread's current device
+ *    (a host-side query that allocates and enqueues nothing; the address follows the device's
+ *    context, which cudaDeviceReset re-creates).  The first call in a process on a device also
+ *    loads the library's device code there: make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents behind; the call
  *    clears what must start at zero.  Calls that overlap on the GPU (other streams or
  *    threads) race on the array and give wrong results: serialise them.

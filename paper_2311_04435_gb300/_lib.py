@@ -58,6 +58,7 @@ SIGNATURES = [
     ("sca_debug_assemble", ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.c_int32, _dp]),
     ("sca_adam_init", ctypes.c_int, [_vp, _AP, _dp]),
     ("sca_adam_step", ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp]),
+    ("sca_adam_run", ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _dp, _dp]),
     ("sca_get_phi", ctypes.c_int, [_vp, _dp]),
     ("sca_get_state", ctypes.c_int, [_vp, _dp, _dp, _dp, _i32p]),
     ("sca_set_state", ctypes.c_int, [_vp, _AP, _dp, _dp, _dp, ctypes.c_int32]),
@@ -67,6 +68,8 @@ SIGNATURES = [
     ("sca_poll", ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _i32p, _dp]),
     ("sca_request_times", ctypes.c_int, [_vp, ctypes.c_uint64, _dp, _dp, _dp, _dp]),
     ("sca_server_destroy", None, [_vp]),
+    ("sca_server_create_manual", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    ("sca_server_step", ctypes.c_int, [_vp, ctypes.c_double, _i32p, _i32p]),
     ("sca_grad_noalloc_dev", ctypes.c_int, [_PP, _vp, _vp, _vp, _vp]),
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
     ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),

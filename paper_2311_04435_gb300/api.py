@@ -302,6 +302,16 @@ class Context:
         check(_lib.lib().sca_adam_step(self._h, int(nsteps), ctypes.byref(om), ctypes.byref(gm)))
         return om.value, gm.value
 
+    def adam_run(self, max_steps: int):
+        """Gated Adam until max|g| < grad_tol or max_steps updates (sca_adam_run): returns
+        (updates applied, Omega, max|g|) at the final phi."""
+        self._bump()
+        om, gm = ctypes.c_double(), ctypes.c_double()
+        steps = ctypes.c_int32()
+        check(_lib.lib().sca_adam_run(self._h, int(max_steps), ctypes.byref(steps), ctypes.byref(om),
+                                      ctypes.byref(gm)))
+        return int(steps.value), om.value, gm.value
+
     def phi(self) -> np.ndarray:
         out = np.zeros(self.N)
         check(_lib.lib().sca_get_phi(self._h, _ptr(out)))
@@ -393,10 +403,17 @@ def sca_potential(phi, handle: Context):
 class Server:
     """Continuous-batching solve server (sca_server_*)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, manual: bool = False):
+        """manual=True: no worker thread; drive the rounds with step(now_s) (virtual clock)."""
         self._h = ctypes.c_void_p()
-        check(_lib.lib().sca_server_create(ctypes.c_uint64(int(hbm_budget_bytes)), int(max_slots),
-                                           ctypes.byref(self._h)))
+        create = _lib.lib().sca_server_create_manual if manual else _lib.lib().sca_server_create
+        check(create(ctypes.c_uint64(int(hbm_budget_bytes)), int(max_slots), ctypes.byref(self._h)))
+
+    def step(self, now_s: float):
+        """One round of a manual server at virtual time now_s: (in flight, queued) after it."""
+        fl, q = ctypes.c_int32(), ctypes.c_int32()
+        check(_lib.lib().sca_server_step(self._h, float(now_s), ctypes.byref(fl), ctypes.byref(q)))
+        return fl.value, q.value
 
     def submit(self, params: Params, adam: AdamConfig) -> int:
         rid = ctypes.c_uint64()

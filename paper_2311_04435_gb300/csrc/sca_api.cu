@@ -34,6 +34,34 @@ constexpr int kDefaultPartitionSms = 8;
 
 void set_error(const std::string& msg) { t_err = msg; }
 
+uint64_t current_context_id() {
+  typedef int (*CtxGetCurrentFn)(void**);
+  typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+  static std::atomic<CtxGetCurrentFn> get_current{nullptr};
+  static std::atomic<CtxGetIdFn> get_id{nullptr};
+  static std::atomic<int> tried{0};
+  if (!tried.load(std::memory_order_acquire)) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current.store(reinterpret_cast<CtxGetCurrentFn>(p));
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id.store(reinterpret_cast<CtxGetIdFn>(p));
+    (void)cudaGetLastError();
+    tried.store(1, std::memory_order_release);
+  }
+  CtxGetCurrentFn gc = get_current.load();
+  CtxGetIdFn gi = get_id.load();
+  if (!gc || !gi) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (gc(&ctx) != 0 || !ctx || gi(ctx, &id) != 0) return 0;
+  return (uint64_t)id;
+}
+
 sca_status cuda_fail(cudaError_t e, const char* where) {
   (void)cudaGetLastError();  // a failed call also records itself as the thread's last error
   set_error(std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
@@ -687,6 +715,37 @@ sca_status enqueue_adam(sca_ctx* c, int32_t n) {
   return SCA_OK;
 }
 
+// Gated Adam on the context's resident state until max|g| < grad_tol or max_steps updates.
+// The device gates each update on max|g| >= grad_tol and counts the updates it applied
+// (status[5]); once converged phi no longer moves, so batches may overshoot safely.  On return
+// h_status holds Omega and max|g| at the final phi and *applied the updates of this call.
+sca_status run_adam_gated(sca_ctx* c, int32_t max_steps, int32_t* applied) {
+  sca_status st = sync_status(c, c->stream);
+  if (st != SCA_OK) return st;
+  const double base = c->e.h_status[5];
+  const int32_t batch = 16;
+  int32_t launched = 0;
+  bool converged = false;
+  while (launched < max_steps && !converged) {
+    const int32_t n = std::min(batch, max_steps - launched);
+    if ((st = enqueue_adam(c, n)) != SCA_OK) return st;
+    launched += n;
+    if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+    if ((st = check_finite(c)) != SCA_OK) return st;
+    converged = c->e.h_status[5] - base < (double)launched;
+  }
+  const double done = c->e.h_status[5] - base;
+  if (!converged) {  // Omega and max|g| at the final phi
+    if ((st = run_blocks(c->e, c->e.d_phi, true, c->stream)) != SCA_OK) return st;
+    if ((st = run_reduce(c->e, c->e.d_phi, c->e.d_omega, c->e.d_g, nullptr, c->stream)) != SCA_OK)
+      return st;
+    if ((st = sync_status(c, c->stream)) != SCA_OK) return st;
+    if ((st = check_finite(c)) != SCA_OK) return st;
+  }
+  *applied = (int32_t)done;
+  return SCA_OK;
+}
+
 // Omega and max|g| at the current phi (no update), synchronised into h_status.
 sca_status final_eval(sca_ctx* c) {
   sca_status st = run_blocks(c->e, c->e.d_phi, true, c->stream);
@@ -766,35 +825,29 @@ sca_status sca_solve(const sca_params* params, const sca_adam* adam, const doubl
   sca_ctx* c = nullptr;
   if ((st = sca_create(params, &c)) != SCA_OK) return st;
   if ((st = sca_adam_init(c, adam, phi0_host)) != SCA_OK) { sca_destroy(c); return st; }
-  // The device gates each update on max|g| >= grad_tol and counts the updates it applied
-  // (status[5]); once converged phi no longer moves, so batches may overshoot safely.
-  const int32_t batch = 16;
-  int32_t launched = 0;
-  bool converged = false;
-  while (launched < adam->max_steps && !converged) {
-    const int32_t n = std::min(batch, adam->max_steps - launched);
-    if ((st = enqueue_adam(c, n)) != SCA_OK) { sca_destroy(c); return st; }
-    launched += n;
-    if ((st = sync_status(c, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
-    if ((st = check_finite(c)) != SCA_OK) { sca_destroy(c); return st; }
-    converged = c->e.h_status[5] < (double)launched;
-  }
-  // Omega and max|g| at the final phi.
-  if (!converged) {
-    if ((st = run_blocks(c->e, c->e.d_phi, true, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
-    if ((st = run_reduce(c->e, c->e.d_phi, c->e.d_omega, c->e.d_g, nullptr, c->stream)) != SCA_OK) {
-      sca_destroy(c);
-      return st;
-    }
-    if ((st = sync_status(c, c->stream)) != SCA_OK) { sca_destroy(c); return st; }
-    if ((st = check_finite(c)) != SCA_OK) { sca_destroy(c); return st; }
-  }
+  int32_t applied = 0;
+  if ((st = run_adam_gated(c, adam->max_steps, &applied)) != SCA_OK) { sca_destroy(c); return st; }
   if (omega) *omega = c->e.h_status[0];
   if (gmax) *gmax = c->e.h_status[1];
-  if (steps) *steps = (int32_t)c->e.h_status[5];
+  if (steps) *steps = applied;
   if (phi_out) st = sca_get_phi(c, phi_out);
   sca_destroy(c);
   return st;
+}
+
+sca_status sca_adam_run(sca_ctx* c, int32_t max_steps, int32_t* steps, double* omega,
+                        double* gmax) {
+  NvtxRange range("sca_adam_run");
+  if (!c) { set_error("ctx is NULL"); return SCA_EINVAL; }
+  if (!c->adam_ready) { set_error("sca_adam_init has not been called"); return SCA_ENOSTATE; }
+  if (max_steps < 0) { set_error("max_steps must be >= 0"); return SCA_EINVAL; }
+  int32_t applied = 0;
+  sca_status st = run_adam_gated(c, max_steps, &applied);
+  if (st != SCA_OK) return st;
+  if (steps) *steps = applied;
+  if (omega) *omega = c->e.h_status[0];
+  if (gmax) *gmax = c->e.h_status[1];
+  return SCA_OK;
 }
 
 sca_status sca_set_stream(sca_ctx* c, void* stream) {

@@ -2191,8 +2191,8 @@ cudaError_t allow_max_smem(K* kernel) {
 
 template <typename S, typename C>
 sca_status set_smem_limits() {
-  static bool done = false;
-  if (done) return SCA_OK;
+  static ContextOnce once;
+  if (once.done()) return SCA_OK;
   cudaError_t err;
   if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
   if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
@@ -2200,7 +2200,7 @@ sca_status set_smem_limits() {
       (err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, false>)) != cudaSuccess)
     return cuda_fail(err, "smem tinv");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
-  done = true;
+  once.mark();
   return SCA_OK;
 }
 

@@ -309,17 +309,18 @@ sca_status fused_prepare(Engine& e) {
   if ((err = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(err, "fused set-up");
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return cuda_fail(err, "fused set-up");
-  // The limit is a property of the kernel shared by every context: set it once to the largest
-  // size any eligible problem needs; occupancy below uses this context's size.
-  static bool limit_set[2] = {false, false};
-  if (!limit_set[e.fp64 ? 1 : 0]) {
+  // The limit is a property of the kernel shared by every context on a device: set it once per
+  // CUDA context to the largest size any eligible problem needs; occupancy below uses this
+  // context's size.
+  static ContextOnce limit_set[2];
+  if (!limit_set[e.fp64 ? 1 : 0].done()) {
     const size_t smax = fused_smem(nmax, e.fp64);
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax)) !=
         cudaSuccess) {
       (void)cudaGetLastError();
       return SCA_OK;  // not eligible
     }
-    limit_set[e.fp64 ? 1 : 0] = true;
+    limit_set[e.fp64 ? 1 : 0].mark();
   }
   if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FT, sm)) != cudaSuccess ||
       per < 1) {

@@ -23,6 +23,35 @@ struct NvtxRange {
 
 constexpr int kMaxFusedSteps = 16;  // Adam iterations per fused persistent launch
 
+// Identity of the calling thread's current CUDA context: the driver's unique context id
+// (cuCtxGetId, fetched at run time so that the library does not link libcuda), 0 when there is
+// no current context or the driver lacks the call.
+uint64_t current_context_id();
+
+// One-time set-up per CUDA context.  cudaFuncSetAttribute and similar calls act on the current
+// context's copy of a kernel: a process that uses several GPUs repeats them on each, and a
+// context that is re-created (after cudaDeviceReset) needs them again.  Each device keeps the
+// id of the last context it was set up in; setting an attribute twice is harmless, so two
+// threads may both run a set-up, and devices past 63 (or an unknown context) are set up on
+// every call.
+struct ContextOnce {
+  std::atomic<uint64_t> ids[64]{};
+  static int device() {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+  }
+  bool done() const {
+    const int d = device();
+    const uint64_t id = current_context_id();
+    return d >= 0 && d < 64 && id != 0 && ids[d].load(std::memory_order_acquire) == id;
+  }
+  // call after the set-up (which makes the device's context current if it was not)
+  void mark() {
+    const int d = device();
+    if (d >= 0 && d < 64) ids[d].store(current_context_id(), std::memory_order_release);
+  }
+};
+
 // Counts every kernel launched through the library (sca_kernel_launches()).
 extern std::atomic<uint64_t> g_launches;
 
@@ -276,4 +305,5 @@ sca_status sync_status(sca_ctx* c, cudaStream_t s);  // status -> pinned host, s
 sca_status check_finite(sca_ctx* c);                 // status -> SCA_ENONFINITE / ETIMEOUT
 sca_status enqueue_adam(sca_ctx* c, int32_t n);      // n gated Adam iterations, no sync
 sca_status final_eval(sca_ctx* c);                   // Omega, max|g| at phi (synchronised)
+sca_status run_adam_gated(sca_ctx* c, int32_t max_steps, int32_t* applied);  // sca_adam_run
 }  // namespace sca

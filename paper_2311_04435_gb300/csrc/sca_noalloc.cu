@@ -11,7 +11,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "sca_internal.h"
@@ -20,33 +19,21 @@ namespace sca {
 namespace {
 
 constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Device address of g_scratch for the current device (looked up once per device; in host code
-// the symbol itself is only a host-side stand-in).
+// Device address of g_scratch on the calling thread's current device.  In host code the symbol
+// itself is only a host-side stand-in, so every call asks the runtime for the address: a
+// host-side query that allocates nothing and enqueues nothing.  It is not cached, because the
+// address belongs to the device's current context and moves when that context is re-created
+// (after cudaDeviceReset, for example).
 sca_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("sca_grad_noalloc_dev: device index out of range");
-    return SCA_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    err = cudaGetSymbolAddress(&p, g_scratch);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(scratch)");
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  const cudaError_t err = cudaGetSymbolAddress(&p, g_scratch);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(scratch)");
+  *out = p;
   return SCA_OK;
 }
 
@@ -72,8 +59,9 @@ extern "C" sca_status sca_grad_noalloc_dev(const sca_params* params, const doubl
   plan(*params, e);
   e.tc = false;
   const size_t S = e.fp64 ? 8 : 4;
-  // Fixed part: status, Omega scratch, flags, ld (B), gd (B x N).
-  const size_t fixed = al256(8 * sizeof(double)) * 2 + al256(16) + al256((size_t)e.B * 8) +
+  // Fixed part: status, flags, ld (B), gd (B x N).  (Omega goes straight to the caller's
+  // d_omega, so the engine's Omega scratch is not carved.)
+  const size_t fixed = al256(8 * sizeof(double)) + al256(16) + al256((size_t)e.B * 8) +
                        al256((size_t)e.B * e.N * 8);
   // Per resident block: block planes, F, W, Tinv, piv, perm, diagonal table.
   const size_t per_block = e.mat_stride * S + 2 * e.fw_mat * S + 2 * (size_t)e.nb * e.nb * 2 * S +
@@ -97,7 +85,6 @@ extern "C" sca_status sca_grad_noalloc_dev(const sca_params* params, const doubl
     return q;
   };
   e.d_status = static_cast<double*>(take(8 * sizeof(double)));
-  e.d_omega = static_cast<double*>(take(8 * sizeof(double)));
   e.flags = static_cast<int*>(take(16));
   e.ld = static_cast<double*>(take((size_t)e.B * 8));
   e.gd = static_cast<double*>(take((size_t)e.B * e.N * 8));

@@ -93,11 +93,15 @@ struct sca_server {
   bool stop = false;
   std::thread worker;
   std::chrono::steady_clock::time_point t0;
+  bool manual = false;   // no worker thread: sca_server_step runs each round (virtual clock)
+  double vclock = 0.0;   // the virtual clock of a manual server (seconds)
 
   double now() const {
+    if (manual) return vclock;
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   void run();
+  bool round_once(bool idle_wait);
   void finish(Request* r, sca_status st);
   void run_buckets(std::vector<Request*>& active, std::vector<Request*>& still);
 };
@@ -232,7 +236,17 @@ void sca_server::run_buckets(std::vector<Request*>& active, std::vector<Request*
 
 void sca_server::run() {
   cudaSetDevice(device);
-  while (true) {
+  while (round_once(true)) {
+  }
+  for (Request* r : active) finish(r, SCA_ECUDA);
+  active.clear();
+}
+
+// One admission pass and one round of every request in flight.  Returns false once the server
+// stops (the worker then abandons what is still in flight).  idle_wait: with nothing to do,
+// wait briefly for a submission (the worker thread) instead of returning at once.
+bool sca_server::round_once(bool idle_wait) {
+  {
     std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lock(mu);
@@ -262,13 +276,13 @@ void sca_server::run() {
         admitted.push_back(r);
       }
       if (active.empty() && admitted.empty()) {
-        if (stop) break;
-        cv.wait_for(lock, std::chrono::milliseconds(20));
-        continue;
+        if (stop) return false;
+        if (idle_wait) cv.wait_for(lock, std::chrono::milliseconds(20));
+        return true;
       }
       if (stop) {
         for (Request* r : admitted) active.push_back(r);
-        break;
+        return false;
       }
     }
     for (Request* r : admitted) {
@@ -335,8 +349,7 @@ void sca_server::run() {
     }
     active.swap(still);
   }
-  for (Request* r : active) finish(r, SCA_ECUDA);
-  active.clear();
+  return true;
 }
 
 extern "C" {
@@ -362,6 +375,52 @@ sca_status sca_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, sca_s
   }
   s->worker = std::thread([s] { s->run(); });
   *out = s;
+  return SCA_OK;
+}
+
+sca_status sca_server_create_manual(uint64_t hbm_budget_bytes, int32_t max_slots,
+                                    sca_server** out) {
+  if (!out || max_slots < 1 || hbm_budget_bytes == 0) {
+    sca::set_error("sca_server_create_manual: need out != NULL, max_slots >= 1, budget > 0");
+    return SCA_EINVAL;
+  }
+  *out = nullptr;
+  sca_server* s = new (std::nothrow) sca_server();
+  if (!s) {
+    sca::set_error("host allocation failed");
+    return SCA_ENOMEM;
+  }
+  s->budget = hbm_budget_bytes;
+  s->slots = max_slots;
+  s->manual = true;
+  cudaError_t err = cudaGetDevice(&s->device);
+  if (err != cudaSuccess) {
+    delete s;
+    return sca::cuda_fail(err, "cudaGetDevice");
+  }
+  *out = s;
+  return SCA_OK;
+}
+
+sca_status sca_server_step(sca_server* s, double now_s, int32_t* in_flight, int32_t* queued) {
+  if (!s || !s->manual) {
+    sca::set_error("sca_server_step: needs a server from sca_server_create_manual");
+    return SCA_EINVAL;
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!(now_s >= s->vclock)) {
+      sca::set_error("sca_server_step: the virtual clock must not run backwards");
+      return SCA_EINVAL;
+    }
+    s->vclock = now_s;
+  }
+  cudaError_t err = cudaSetDevice(s->device);
+  if (err != cudaSuccess) return sca::cuda_fail(err, "cudaSetDevice");
+  s->round_once(false);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (in_flight) *in_flight = (int32_t)s->active.size();
+  if (queued) *queued = (int32_t)s->queue.size();
   return SCA_OK;
 }
 

@@ -1413,12 +1413,12 @@ sca_status tc_diag(const float* M, int ldm, size_t mat_stride, size_t plane_stri
     set_error("tensor-core pivot-block inverse needs nb = 128");
     return SCA_EINVAL;
   }
-  static bool attr = false;
-  if (!attr) {
+  static ContextOnce attr;
+  if (!attr.done()) {
     cudaError_t err =
         cudaFuncSetAttribute(k_diag_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDgSmem);
     if (err != cudaSuccess) return cuda_fail(err, "tensor-core pivot-block inverse set-up");
-    attr = true;
+    attr.mark();
   }
   if (cnt <= 0) return SCA_OK;
   k_diag_tc<<<cnt, kDgThreads, kDgSmem, s>>>(M, ldm, (long long)mat_stride,
