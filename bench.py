@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--workload", default="ionic_40x40")
     ap.add_argument("--prec", default=None,
                     help="fp32 | 3xtf32 | bf16x3 (default: bf16x3)")
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 steps (0 = skip)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (0 = skip)")
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="timed steps of the no-pivoting variant (0 = skip)")
     ap.add_argument("--dos-points", type=int, default=128,
@@ -54,8 +54,11 @@ def parse():
                     help="timed Metropolis steps (0 = skip)")
     ap.add_argument("--cpu-blocks", type=int, default=0, help="oracle sample size (0 = #cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve", type=int, default=0,
-                    help="serving sweep: replay this many requests of the seeded trace")
+    ap.add_argument("--serve", type=int, default=512,
+                    help="serving sweep beside the step timing: replay this many requests of "
+                         "the seeded trace (0 = skip)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="print only the serving sweep's own JSON line")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-steps", type=int, default=5000)
@@ -139,6 +142,18 @@ DEFAULT_SM_PARTITION = -1  # the library's default (8 SMs for 1024 <= N <= 2048,
 # step of the 16-block workload ionic_40x40_w8, divided by 16; traffic grows with the blocks),
 # for the kernel as captured (profiles/): BF16x3 344.5 MB, 3xTF32 404.0 MB per 16-block launch.
 UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 344.5e6 / 16, "3xtf32": 404.0e6 / 16}
+# sha256 (first 16 hex digits) of csrc/sca_tc.cu when those counters were taken: the traffic
+# is reported only while the update kernel's source is unchanged, else null.
+UPDATE_TRAFFIC_SOURCE_SHA16 = None
+
+
+def tc_source_sha16():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2311_04435_gb300", "csrc", "sca_tc.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
@@ -268,9 +283,18 @@ def run_ours(args):
     launch_s = (upd_ms / 1e3) / max(upd_n, 1)  # average duration of one update launch
     traffic = None
     per_block = UPDATE_BYTES_PER_BLOCK_N1600.get(prec)
-    if sym and params.N == 1600 and per_block:
+    src_sha = tc_source_sha16()
+    if sym and params.N == 1600 and per_block and src_sha == UPDATE_TRAFFIC_SOURCE_SHA16:
         traffic = round(per_block * n_dom, 0)  # bytes per launch
+    traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 16-block capture "
+                    "(workload ionic_40x40_w8) per block, times the dominant blocks; reported "
+                    f"only for the kernel source it was taken on (sca_tc.cu sha16 "
+                    f"{UPDATE_TRAFFIC_SOURCE_SHA16}; this run {src_sha})")
     per_kernel = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
+    # per-block log-dets and sigma Re G_ii of the seeded start field, for the error against
+    # the oracle on the blocks the CPU baseline samples
+    phi_s = inputs.seed_phi(wl.seed, params.N)
+    blk_gpu = ctx.blocks(phi_s, grad=True) if rank == 0 and not args.no_cpu_baseline else None
     ctx.close()
 
     # ---------------- end to end through the public API with host buffers
@@ -295,6 +319,7 @@ def run_ours(args):
 
     # ---------------- FP64 path beside it
     fp64 = None
+    blk_64 = None
     if args.fp64_steps > 0 and rank == 0:
         p64 = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, prec="fp64")
         c64 = api.Context(p64)
@@ -308,6 +333,7 @@ def run_ours(args):
         a1.record(stream)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1) / args.fp64_steps
+        blk_64 = c64.blocks(phi_s, grad=True) if blk_gpu is not None else None
         c64.close()
         fp64 = {"steps_per_s": round(1e3 / ms64, 5), "ms_per_step": round(ms64, 2),
                 "timed_steps": args.fp64_steps, "warmup": 1,
@@ -392,8 +418,20 @@ def run_ours(args):
                  "acceptance": round(float(acc.mean()), 3), "timed_steps": args.metro_steps}
 
     cpu = None
+    mixed_vs_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, wl)
+        cpu, sample, o_ld, o_gd = cpu_baseline(args, wl, with_blocks=True)
+        mixed_vs_oracle = {"blocks": [int(b) for b in sample],
+                           prec: block_errors(blk_gpu, sample, o_ld, o_gd)}
+        if blk_64 is not None:
+            mixed_vs_oracle["fp64"] = block_errors(blk_64, sample, o_ld, o_gd)
+        mixed_vs_oracle["note"] = ("per-block ln|det A_b| and sigma Re G_b,ii at the seeded "
+                                   "start field against the FP64 oracle on the CPU baseline's "
+                                   "sample of blocks")
+
+    serve = None
+    if rank == 0 and args.serve > 0 and world == 1:
+        serve = serve_sweep(args)
 
     if rank == 0:
         line = {
@@ -415,7 +453,8 @@ def run_ours(args):
                        "final_omega": om, "final_gmax": gm},
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": roofline_for(prec, fl_blk * n_dom, by_blk * n_dom, launch_s, traffic),
+            "roofline": dict(roofline_for(prec, fl_blk * n_dom, by_blk * n_dom, launch_s, traffic),
+                             traffic_source=traffic_note),
             "kernels_ms_one_step": per_kernel,
             "fp64_path": fp64,
             "no_pivoting_variant": nopiv,
@@ -424,6 +463,8 @@ def run_ours(args):
             "metropolis": metro,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "mixed_vs_oracle": mixed_vs_oracle,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -431,7 +472,19 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(args, wl, steps_timed=1):
+def block_errors(blk, sample, o_ld, o_gd):
+    """Largest errors of the GPU's per-block ld and sigma Re G_ii on the sampled blocks."""
+    import numpy as np
+    ld, gd = blk
+    d_ld = np.abs(ld[sample] - o_ld)
+    d_gd = np.abs(gd[sample] - o_gd)
+    return {"ld_max_abs_err": float(d_ld.max()),
+            "ld_max_rel_err": float((d_ld / np.maximum(1.0, np.abs(o_ld))).max()),
+            "gdiag_max_abs_err": float(d_gd.max()),
+            "gdiag_scale": float(max(1.0, np.abs(o_gd).max()))}
+
+
+def cpu_baseline(args, wl, steps_timed=1, with_blocks=False):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: as many blocks
     as host threads (LU + inverse columns each), scaled to a full step."""
     import numpy as np
@@ -447,12 +500,16 @@ def cpu_baseline(args, wl, steps_timed=1):
     phi = inputs.seed_phi(wl.seed, wl.L * wl.L)
     blocks = np.linspace(0, B - 1, nblk).astype(np.int32)
     t0 = time.perf_counter()
-    oracle.blocks_sample(p, phi, blocks)
+    o_ld, o_gd = oracle.blocks_sample(p, phi, blocks)
     dt = time.perf_counter() - t0
     per_step = dt * B / nblk
-    return {"value": round(1.0 / per_step, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nblk} of {B} blocks (dense LU + inverse columns, FP64), "
-                      f"{dt:.1f} s, scaled to a full step"}
+    out = {"value": round(1.0 / per_step, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{nblk} of {B} blocks (dense LU + inverse columns, FP64), "
+                     f"{dt:.1f} s, scaled to a full step",
+           "sample_s": round(dt, 3), "sample_blocks": int(nblk)}
+    if with_blocks:
+        return out, blocks, o_ld, o_gd
+    return out
 
 
 def run_reference(args):
@@ -465,16 +522,23 @@ def run_reference(args):
     wl = inputs.WORKLOADS[args.workload]
     import oracle
     cores = oracle.num_threads()
-    per = []
+    per, wall = [], []
     for k in range(args.warmup + args.steps):
         r = cpu_baseline(argparse.Namespace(cpu_blocks=args.cpu_blocks or cores), wl)
         if k >= args.warmup:
             per.append(1.0 / r["value"])
+            wall.append(r["sample_s"])
     total = sum(per)
     value = args.steps / total
+    # each timed step is a bounded sample of the workload's blocks: ms_per_step is the measured
+    # time of one sample, value the full-step rate extrapolated from it (blocks are independent)
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+            "ms_per_step": round(1e3 * sum(wall) / args.steps, 1),
+            "ms_per_full_step_extrapolated": round(1e3 * total / args.steps, 1),
+            "value_basis": "full steps/s extrapolated from the timed sample of each step "
+                           f"({r['sample_blocks']} of {2 * wl.n_omega} blocks)",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 start field)",
             "config": {"workload": args.workload, "impl": "FP64 CPU oracle (C, OpenMP)"},
@@ -486,15 +550,22 @@ def run_reference(args):
 
 
 def run_serve(args):
+    """--serve-only: the serving sweep's own JSON line."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    line = serve_sweep(args)
+    print(json.dumps(line), flush=True)
+
+
+def serve_sweep(args):
     """Serving sweep: the seeded mixed-size Poisson trace replayed in real time through
     sca_submit / sca_poll; solves/s and p50/p99 latency (submit -> finish)."""
     import numpy as np
-    import torch
 
     from paper_2311_04435_gb300 import api, inputs
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     trace = inputs.serving_trace(args.serve, rate_per_s=args.serve_rate)
     prec = args.prec or DEFAULT_PREC
     reqs = [(api.Params(r.L, r.n_omega, U=r.U, T=r.T, delta=r.delta, prec=prec),
@@ -540,14 +611,14 @@ def run_serve(args):
         "converged": conv, "mean_steps": round(float(np.mean(steps)), 1),
         "wall_s": round(wall, 2), "gpu_launches": int(launches),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.serve > 0:
+    elif args.serve_only:
         run_serve(args)
     else:
         run_ours(args)

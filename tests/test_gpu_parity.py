@@ -129,21 +129,33 @@ def test_seeded_start_field_is_bit_exact():
 
 
 def test_adam_trajectory_4x4_matches_oracle():
-    """4x4 Hubbard, U=6, T=0.1, 64 frequencies, seed 0, lr=0.01: 300 Adam steps."""
-    p = api.Params(4, 64, U=6.0, T=0.1)
-    steps = 300
-    ad = api.AdamConfig(lr=0.01, max_steps=steps, seed=0)
-    phi_o, k, om_o, gm_o, oh, gh = oracle.adam_run(oparams(p), lr=0.01, max_steps=steps, seed=0,
-                                                   history=True)
+    """The 4x4 Hubbard workload (U=6, Delta=0, T=0.1, 64 frequencies: 128 blocks of 16 x 16,
+    seed 0, lr=0.01) for its full 2000 Adam steps on the FP64 path: Omega, max|g|, phi and the
+    two |phi| readings against the oracle's run."""
+    wl = inputs.WORKLOADS["hubbard_4x4"]
+    p = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta)
+    steps = wl.steps
+    assert steps == 2000
+    ad = api.AdamConfig(lr=wl.lr, max_steps=steps, seed=wl.seed)
+    phi_o, k, om_o, gm_o, oh, gh = oracle.adam_run(oparams(p), lr=wl.lr, max_steps=steps,
+                                                   seed=wl.seed, history=True)
     with api.Context(p) as c:
         c.adam_init(ad)
         om1, gm1 = c.adam_step(1)
         assert om1 == pytest.approx(oh[0], rel=1e-12)
         assert gm1 == pytest.approx(gh[0], rel=1e-10)
-        om, gm = c.adam_step(steps - 1)
+        om, gm = c.adam_step(299)
+        assert om == pytest.approx(oh[299], rel=1e-10)
+        om, gm = c.adam_step(steps - 300)
         phi = c.phi()
+        om_end, g_end = c.grad(phi)
     assert om == pytest.approx(oh[steps - 1], rel=1e-10)
     assert np.max(np.abs(phi - phi_o)) < 1e-9
+    assert om_end == pytest.approx(om_o, rel=1e-10)
+    assert abs(np.abs(g_end).max() - gm_o) <= 1e-10 * max(1.0, gm_o)
+    stag, mean = oracle.staggered_order(phi, wl.L)
+    stag_o, mean_o = oracle.staggered_order(phi_o, wl.L)
+    assert abs(stag - stag_o) < 1e-9 and abs(mean - mean_o) < 1e-9
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -491,3 +503,40 @@ def test_64x64_staggered_field_closed_form(prec):
     t = tol(prec)
     assert om == pytest.approx(om_ref, rel=t["om"])
     assert np.max(np.abs(g - g_a * s)) <= t["g"] * max(1.0, abs(g_a)) * 10
+
+
+@pytest.mark.slow
+def test_c3_autograd_gradient_matches_central_differences():
+    """The 40x40 workload (256 blocks of 1600 x 1600, U = 4, Delta = 1, T = 0.1): the gradient
+    from the autograd Function (forward keeps the inverses, backward runs the adjoint diag(G)
+    stage) on the FP64 and BF16x3 paths against central differences of the FP64 path,
+    h = 1e-6, on 32 seeded random components.  Each difference is formed block by block,
+    sum_b [ld_b(phi + h e_i) - ld_b(phi - h e_i)], so the large constant part of Omega cancels
+    inside every block (LU-only evaluations)."""
+    torch = pytest.importorskip("torch")
+    wl = inputs.WORKLOADS["ionic_40x40"]
+    phi = inputs.seed_phi(wl.seed, wl.L * wl.L)
+    N, h = phi.size, 1e-6
+    comps = np.random.default_rng(2311).choice(N, 32, replace=False)
+    grads = {}
+    for prec in ("fp64", "bf16x3"):
+        p = api.Params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, prec=prec)
+        with api.Context(p) as c:
+            x = torch.tensor(phi, dtype=torch.float64, device="cuda", requires_grad=True)
+            api.sca_potential(x, c).backward()
+            grads[prec] = x.grad.cpu().numpy()
+            if prec != "fp64":
+                continue
+            fd = np.zeros(len(comps))
+            for k, i in enumerate(comps):
+                e = np.zeros(N)
+                e[i] = h
+                ld_p = c.blocks(phi + e, grad=False)
+                ld_m = c.blocks(phi - e, grad=False)
+                quad = ((phi[i] + h) ** 2 - (phi[i] - h) ** 2) / wl.U
+                fd[k] = (quad - 2.0 * wl.T * np.sum(ld_p - ld_m)) / (2.0 * h)
+    for prec, g in grads.items():
+        err = np.abs(g[comps] - fd)
+        assert np.all(err <= 1e-5 * np.maximum(1.0, np.abs(fd))), (prec, err.max())
+    scale = max(1.0, np.abs(grads["fp64"]).max())
+    assert np.max(np.abs(grads["bf16x3"] - grads["fp64"])) <= 1e-6 * scale

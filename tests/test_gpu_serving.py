@@ -131,3 +131,84 @@ def test_bucket_spread_over_passes():
         ids = [srv.submit(p, a) for p, a in reqs]
         mixed = [_wait(srv, rid, p.N) for rid, (p, _) in zip(ids, reqs)]
     _check_same(reqs, mixed, alone)
+
+
+def test_large_bucketed_requests_match_oracle():
+    """BF16x3 requests of the serving sweep's larger sizes (L = 24: 576 sites, L = 32: 1024
+    sites, tensor-core path with pivoted and dominant blocks) served together in one mix: each
+    result after its 25 gated Adam updates matches the oracle's Adam run (spectral route) from
+    the same seeded start."""
+    import oracle
+
+    reqs = [(api.Params(24, 32, U=4.0, T=0.1, delta=0.6, prec="bf16x3"),
+             api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=25, seed=31)),
+            (api.Params(32, 16, U=5.0, T=0.2, delta=0.3, prec="bf16x3"),
+             api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=25, seed=32)),
+            (api.Params(24, 11, U=6.0, T=0.3, delta=1.2, prec="bf16x3"),
+             api.AdamConfig(lr=0.02, grad_tol=1e-6, max_steps=25, seed=33))]
+    with api.Server(hbm_budget_bytes=40 << 30, max_slots=4) as srv:
+        ids = [srv.submit(p, a) for p, a in reqs]
+        mixed = [_wait(srv, rid, p.N) for rid, (p, _) in zip(ids, reqs)]
+    for (p, a), r in zip(reqs, mixed):
+        op = oracle.make_params(p.L, p.n_omega, U=p.U, T=p.T, delta=p.delta)
+        phi_o, k_o, om_o, gm_o = oracle.adam_run_spectral(
+            op, oracle.seed_phi(a.seed, p.N), lr=a.lr, grad_tol=a.grad_tol, max_steps=a.max_steps)
+        assert r.steps == k_o == a.max_steps
+        assert np.max(np.abs(r.phi - phi_o)) <= 1e-6
+        assert r.omega == pytest.approx(om_o, rel=1e-5)
+        assert r.gmax == pytest.approx(gm_o, rel=1e-4, abs=1e-6)
+
+
+def _replay(trace, dt, slots, budget):
+    """Replays an arrival trace on a manual server: round r runs at virtual time r * dt, after
+    the submission of every request that arrived by then.  Returns the per-round (in flight,
+    queued) log and, per request, its times, update count and result."""
+    reqs = [(api.Params(q.L, q.n_omega, U=q.U, T=q.T, delta=q.delta, prec="bf16x3"),
+             api.AdamConfig(lr=0.01, grad_tol=1e-6, max_steps=40, seed=q.seed)) for q in trace]
+    log, ids = [], []
+    with api.Server(hbm_budget_bytes=budget, max_slots=slots, manual=True) as srv:
+        k, r = 0, 0
+        while True:
+            t = r * dt
+            while k < len(trace) and trace[k].arrival_s <= t:
+                ids.append(srv.submit(*reqs[k]))
+                k += 1
+            fl, q = srv.step(t)
+            log.append((fl, q))
+            assert fl <= slots
+            if k == len(trace) and fl == 0 and q == 0:
+                break
+            r += 1
+            assert r < 10000
+        out = []
+        for rid, (p, _) in zip(ids, reqs):
+            res = srv.poll(rid, p.N)
+            assert res is not None
+            out.append((rid, srv.times(rid), res.steps, res.omega, res.gmax, res.phi))
+    return log, out, reqs
+
+
+def test_replayed_trace_bookkeeping_is_bit_exact():
+    """A 14-request slice of the serving trace (L in {8, 12, 16, 20}, BF16x3: fused small
+    requests and size buckets) replayed twice on a manual server with a virtual clock: the
+    admission order, the in-flight and queued counts of every round, the request times, the
+    update counts and the results agree bit for bit; admission follows arrival order and never
+    exceeds the slots; each result equals the request solved alone."""
+    from paper_2311_04435_gb300 import inputs
+
+    trace = inputs.serving_trace(14, rate_per_s=20.0, seed=77, sizes=(8, 12, 16, 20))
+    a = _replay(trace, 0.05, slots=4, budget=6 << 30)
+    b = _replay(trace, 0.05, slots=4, budget=6 << 30)
+    assert a[0] == b[0]
+    for x, y in zip(a[1], b[1]):
+        assert x[0] == y[0] and x[1] == y[1] and x[2] == y[2]
+        assert x[3] == y[3] and x[4] == y[4] and np.array_equal(x[5], y[5])
+    admits = [o[1][1] for o in a[1]]
+    assert admits == sorted(admits)
+    for o in a[1]:
+        sub, adm, st, fin = o[1]
+        assert 0 <= sub <= adm <= st <= fin
+    assert max(fl for fl, _ in a[0]) == 4  # the slots were the limit at some point
+    for (p, ad), o in list(zip(a[2], a[1]))[:4]:
+        alone = api.solve(p, ad)
+        assert alone.steps == o[2] and np.array_equal(alone.phi, o[5]) and alone.omega == o[3]

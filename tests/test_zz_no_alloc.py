@@ -5,9 +5,13 @@ sca_grad_noalloc_dev serves callers that cannot let the library allocate device 
 workspace is a static 64 MiB device array shared by every call, so the test checks two
 calls in a row (the second sees the first call's leftovers), a problem large enough to be
 processed in several chunks of that array, and the rejection of a problem whose single block
-does not fit.  This file is collected last on purpose.
+does not fit, and a call after the device's context was re-created (the array's address
+moves with the context).  This file is collected last on purpose.
 """
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -54,3 +58,63 @@ def test_noalloc_rejects_problem_beyond_static_workspace():
         _noalloc(p, x)
     msg = _lib.lib().sca_last_error().decode()
     assert "too large" in msg
+
+
+_RESET_CHILD = r"""
+import ctypes, os, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2311_04435_gb300 import _lib, api, inputs
+
+lib = _lib.lib()
+# the CUDA runtime the library is linked against (already loaded by it)
+rt_path = next(ln.split()[-1] for ln in open("/proc/self/maps") if "libcudart.so" in ln)
+rt = ctypes.CDLL(rt_path)
+vp = ctypes.c_void_p
+
+def ok(err, what):
+    assert err == 0, f"{what}: CUDA error {err}"
+
+def noalloc(p, phi):
+    n = p.N
+    d = [vp(), vp(), vp()]
+    for k, size in enumerate((8 * n, 8, 8 * n)):
+        ok(rt.cudaMalloc(ctypes.byref(d[k]), ctypes.c_size_t(size)), "cudaMalloc")
+    ok(rt.cudaMemcpy(d[0], phi.ctypes.data_as(vp), ctypes.c_size_t(8 * n), 1), "upload")
+    _lib.check(lib.sca_grad_noalloc_dev(ctypes.byref(p.c()), d[0], d[1], d[2], None))
+    ok(rt.cudaDeviceSynchronize(), "sync")
+    om, g = np.zeros(1), np.zeros(n)
+    ok(rt.cudaMemcpy(om.ctypes.data_as(vp), d[1], ctypes.c_size_t(8), 2), "read Omega")
+    ok(rt.cudaMemcpy(g.ctypes.data_as(vp), d[2], ctypes.c_size_t(8 * n), 2), "read grad")
+    for x in d:
+        ok(rt.cudaFree(x), "cudaFree")
+    return float(om[0]), g
+
+def reference(p, phi):
+    with api.Context(p) as c:
+        return c.grad(phi)
+
+# 100 sites in float64: the pivoted blocks' panel kernel needs more than 48 KB of shared memory,
+# an opt-in that belongs to the context as much as the array's address does
+p = api.Params(10, 16, U=4.0, T=0.1, delta=0.5, prec="fp64")
+for rnd in range(2):
+    phi = inputs.random_phi(60 + rnd, p.N)
+    om_ref, g_ref = reference(p, phi)
+    om, g = noalloc(p, phi)
+    assert abs(om - om_ref) <= 1e-10 * abs(om_ref), (rnd, om, om_ref)
+    assert np.max(np.abs(g - g_ref)) <= 1e-10 * max(1.0, np.abs(g_ref).max()), rnd
+    if rnd == 0:
+        ok(rt.cudaDeviceReset(), "cudaDeviceReset")  # ends this process's context only
+print("noalloc-after-reset ok")
+"""
+
+
+def test_noalloc_after_context_reset():
+    """In a fresh process: a call, cudaDeviceReset (which re-creates the device's primary
+    context, so the array's device address may change), and another call; both match the
+    context path."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _RESET_CHILD, root], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "noalloc-after-reset ok" in r.stdout
