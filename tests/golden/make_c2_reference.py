@@ -41,10 +41,10 @@ def main():
         f.write("# betas (0.9, 0.999), eps 1e-8, no gate.  Written by make_c2_reference.py.\n")
         f.write("# steps omega max|g| stag|phi| mean|phi|  (Omega and max|g| at the field after the steps)\n")
         for k, om, gm, stag, mean in rows:
-            f.write(f"{k} {om!r} {gm!r} {stag!r} {mean!r}\n")
+            f.write(f"{k} {float(om)!r} {float(gm)!r} {float(stag)!r} {float(mean)!r}\n")
         f.write(f"# phi after {done} steps, site order i = x*L + y\n")
         for v in phi:
-            f.write(f"{v!r}\n")
+            f.write(f"{float(v)!r}\n")
 
 
 if __name__ == "__main__":
