@@ -158,18 +158,44 @@ FP32_SIMT_TFLOPS = 75.0
 FP64_SIMT_TFLOPS = 1.20
 
 
-def update_algorithmic(prec: str, N: int, nb: int, sym: bool):
-    """Algorithmic flops and bytes of one dominant-group update launch, per block: 8 kb flops
-    per updated complex entry (lower triangle on or below the diagonal when symmetric), the
-    updated tiles of M read and written once (complex64), the F (4) and W (6) split planes
-    read once (bf16 or float32 elements)."""
-    tiles = (N + 127) // 128
-    rows = [min(128, N - 128 * t) for t in range(tiles)]
-    area = sum(rows[a] * rows[b] for a in range(tiles) for b in range(tiles) if b <= a or not sym)
-    flops = 8.0 * nb * (N * (N + 1) / 2 if sym else float(N) * N)
+def dominant_update_launches(prec: str, N: int, nb: int, sym: bool, paired: bool):
+    """Algorithmic flops and bytes, per dominant block, of every update launch of one gradient
+    evaluation, in launch order: a list of (kind, flops, bytes).  Flops: 8 per complex
+    multiply-add, K = the step widths, over the lower triangle (diagonal included) when the
+    block is updated symmetrically, else the full block.  Bytes: the updated tiles of M read and
+    written once (complex64) plus the F and W split planes of the launch's steps read once
+    (4 + 4 planes of N x nb, bf16 or float32 elements).  With paired steps a pair is one update
+    of the second step's cross (its tile row and column, K = the first step) and one merged
+    update of every other lower tile (K = both steps) and of the cross (K = the second step)."""
     es = 2 if prec == "bf16x3" else 4
-    bytes_ = 2.0 * 8.0 * area + 10.0 * N * nb * es
-    return flops, bytes_
+    T = (N + 127) // 128
+    rows = [min(128, N - 128 * t) for t in range(T)]
+    tiles = [(a, b) for a in range(T) for b in range(T) if b <= a or not sym]
+
+    def area(ts):
+        return sum(rows[a] * rows[b] for a, b in ts)
+
+    def entries(ts):  # algorithmic entries: the diagonal tiles' lower triangles when symmetric
+        return sum(rows[a] * (rows[a] + 1) / 2 if (sym and a == b) else rows[a] * rows[b]
+                   for a, b in ts)
+
+    planes = 8.0 * N * nb * es
+    out, k0 = [], 0
+    while k0 < N:
+        kb = min(nb, N - k0)
+        if paired and k0 + kb < N:
+            k2 = k0 + kb
+            kb2 = min(nb, N - k2)
+            t2 = k2 // 128
+            cross = [(t2, j) for j in range(t2 + 1)] + [(i, t2) for i in range(t2 + 1, T)]
+            out.append(("update_cross", 8.0 * kb * entries(cross), 16.0 * area(cross) + planes))
+            out.append(("update", 8.0 * (kb + kb2) * entries(tiles) - 8.0 * kb * entries(cross),
+                        16.0 * area(tiles) + 2 * planes))
+            k0 = k2 + kb2
+        else:
+            out.append(("update", 8.0 * kb * entries(tiles), 16.0 * area(tiles) + planes))
+            k0 += kb
+    return out
 
 
 def roofline_for(prec: str, flops: float, bytes_: float, seconds: float, traffic):
@@ -191,7 +217,7 @@ def roofline_for(prec: str, flops: float, bytes_: float, seconds: float, traffic
     tflops = flops / seconds / 1e12 if seconds > 0 else 0.0
     gbs = bytes_ / seconds / 1e9 if seconds > 0 else 0.0
     intensity = flops / bytes_
-    out = {"kernel": "update (rank-nb Gauss-Jordan contraction)",
+    out = {"kernel": "update (merged pairs of rank-128 Gauss-Jordan steps: one K = 256 contraction per pair)",
            "intensity_flop_per_byte": round(intensity, 2),
            "tensor_tflops": round(tflops, 3), "tensor_peak": round(peak, 3)}
     if bound == "tensor" and intensity * hbm / 1e3 < peak:
@@ -277,9 +303,16 @@ def run_ours(args):
     # 4 N^2 (N + 1) per block; the full update (CUDA cores, or SCA_SYM=0) needs 8 N^3.
     upd_ms, upd_n = prof["update"]
     n_dom = 2 * wl.n_omega - api.pivoted_blocks(params)
-    sym = prec in ("3xtf32", "bf16x3") and os.environ.get("SCA_SYM", "1") != "0"
-    fl_blk, by_blk = update_algorithmic(prec, params.N, 128 if prec in ("3xtf32", "bf16x3") else 64,
-                                        sym)
+    tcp = prec in ("3xtf32", "bf16x3")
+    sym = tcp and os.environ.get("SCA_SYM", "1") != "0"
+    paired = sym and os.environ.get("SCA_PAIR", "1") != "0"
+    sched = dominant_update_launches(prec, params.N, 128 if tcp else 64, sym, paired)
+    upd = [(f, b) for k, f, b in sched if k == "update"]
+    assert len(upd) == upd_n, (len(upd), upd_n)
+    # per launch (averaged over the step's update launches): flops and bytes of all dominant
+    # blocks, and the average duration
+    fl_blk = sum(f for f, _ in upd) / len(upd)
+    by_blk = sum(b for _, b in upd) / len(upd)
     launch_s = (upd_ms / 1e3) / max(upd_n, 1)  # average duration of one update launch
     traffic = None
     per_block = UPDATE_BYTES_PER_BLOCK_N1600.get(prec)

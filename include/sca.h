@@ -356,7 +356,9 @@ sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
  * between the two sizes, which the driver's 8-SM granularity does not offer).
  * pivoted_sms = 0 removes the partition (the dominant group's persistent tensor-core launches
  * then leave 8 SMs free, and priorities do the rest).  Contexts with 1024 <= N <= 2048 and at
- * least 64 dominant blocks start with a partition of 8 SMs in mode 3 when the driver grants it.
+ * least 64 dominant blocks start with a partition when the driver grants it: 16 SMs in mode 1
+ * where the dominant blocks' elimination steps are merged in pairs (the tensor-core path), else
+ * 8 SMs in mode 3.
  * Needs the
  * tensor-core path; results do not depend on the partition (tile order and reductions are
  * fixed).  SCA_ECUDA when the driver refuses the partition; the context then keeps its
@@ -378,7 +380,9 @@ sca_status sca_sm_partition(sca_ctx* ctx, int32_t* pivoted_sms, int32_t* dominan
  * of the pivoted group, 10 fused small-block Adam launch, 11 wall span of the pivoted group on
  * its stream, 12 wall span of the dominant group on the main stream (spans contain the
  * kernels above, so they are not part of any sum), 13 update of the rest of a pivoted outer
- * panel after each sub-panel, 14 rank-nb factors of the pivoted group.  Enabling resets the
+ * panel after each sub-panel, 14 rank-nb factors of the pivoted group, 15 the first update of a
+ * merged pair of elimination steps of the dominant blocks (only the second step's row and column
+ * strips; the merged update of the rest is kind 5).  Enabling resets the
  * counters.  Timing adds a small host overhead per launch; keep it off when measuring
  * throughput.  With the environment variable SCA_PROFILE_TRACE set to a file name, each
  * synchronisation also appends the launches it collected to that file, one line each:

@@ -238,7 +238,8 @@ class Context:
 
     # ---- streams and per-kernel timing
     KINDS = ["assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
-             "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv"]
+             "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv",
+             "update_cross"]
 
     def set_stream(self, stream=None):
         """Enqueue on a torch.cuda.Stream (or raw handle); None restores the own stream."""

@@ -26,10 +26,13 @@ thread_local std::string t_err;
 constexpr int kDefaultSmReserve = 8;
 // Problems with 1024 <= N <= 2048 and at least 64 dominant blocks start with an SM partition
 // that keeps the dominant group's launches off this many SMs (sca_set_sm_partition changes
-// it): the dominant group keeps the 144 SMs its persistent launches use anyway, and the
-// pivoted chain's 8 SMs no longer fill up with the dominant group's other kernels.  At larger
-// N the dominant group's work dwarfs the chain and the partition only costs.
+// it), so that the pivoted chain's kernels never wait for a dominant CTA to leave an SM.  With
+// the dominant group's elimination steps merged in pairs its span shrinks, and 16 SMs for the
+// pivoted chain (mode 1) balance the two spans best at 40x40 (23.2 ms against 24.3 with 8 SMs
+// in mode 3 and 25.6 with 32); without merged pairs 8 SMs in mode 3 did.  At larger N the
+// dominant group's work dwarfs the chain and the partition only costs.
 constexpr int kDefaultPartitionSms = 8;
+constexpr int kDefaultPartitionSmsPaired = 16;
 }
 
 void set_error(const std::string& msg) { t_err = msg; }
@@ -155,9 +158,15 @@ sca_status plan(const sca_params& p, Engine& e) {
   e.fw_plane = (size_t)e.N * e.nb;
   e.fw_mat = (e.tc ? 6 : 2) * e.fw_plane;
   const size_t C = S;  // compute type of the small kernels = storage type
+  // merged two-step updates of the symmetric dominant blocks (second factor pair F2, W2): on
+  // the tensor-core path when at least two elimination steps remain after the first one
+  e.pair = e.tc && e.nb == 128 && e.N > e.nb && e.B > e.piv_blocks;
+  if (const char* v = std::getenv("SCA_PAIR"))
+    if (std::atoi(v) == 0) e.pair = false;
   size_t bytes = 0;
   bytes += (size_t)e.chunk * e.mat_stride * S;           // blocks
   bytes += 2 * (size_t)e.chunk * e.fw_mat * S;            // F, W
+  if (e.pair) bytes += 2 * (size_t)e.chunk * e.fw_mat * S;  // F2, W2
   bytes += (size_t)e.chunk * 2 * e.nb * e.nb * 2 * C;     // Tinv
   if (e.tc) bytes += (size_t)e.chunk * kTtPlanes * e.nb * e.nb * 4;  // -T^T split planes
   bytes += (size_t)e.chunk * e.N * 2 * sizeof(float);     // Re A_jj as double-float
@@ -216,6 +225,13 @@ sca_status allocate(Engine& e) {
   if (err == cudaSuccess) err = cudaMemset(e.W, 0, (size_t)e.chunk * e.fw_mat * S);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
   if (e.tc) SCA_ALLOC(e.tt, (size_t)e.chunk * kTtPlanes * e.nb * e.nb * sizeof(float), "T planes");
+  if (e.pair) {
+    SCA_ALLOC(e.F2, (size_t)e.chunk * e.fw_mat * S, "F2");
+    SCA_ALLOC(e.W2, (size_t)e.chunk * e.fw_mat * S, "W2");
+    err = cudaMemset(e.F2, 0, (size_t)e.chunk * e.fw_mat * S);
+    if (err == cudaSuccess) err = cudaMemset(e.W2, 0, (size_t)e.chunk * e.fw_mat * S);
+    if (err != cudaSuccess) { release(e); return cuda_fail(err, "cudaMemset"); }
+  }
   if (e.tc && (st = tc_prepare(e)) != SCA_OK) { release(e); return st; }
 #undef SCA_ALLOC
   if ((st = fused_prepare(e)) != SCA_OK) { release(e); return st; }
@@ -238,11 +254,16 @@ sca_status allocate(Engine& e) {
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "side stream"); }
   err = cudaEventCreateWithFlags(&e.ev_join2, cudaEventDisableTiming);
   if (err != cudaSuccess) { release(e); return cuda_fail(err, "join event"); }
-  if (e.tc && e.piv_blocks > 0 && e.N >= 1024 && e.N <= 2048 && e.B - e.piv_blocks >= 64)
-    // two dominant partitions (mode 3); one if the driver refuses the second; ordinary
-    // streams if it refuses both
-    if (!partition_setup(e, kDefaultPartitionSms, 3))
+  if (e.tc && e.piv_blocks > 0 && e.N >= 1024 && e.N <= 2048 && e.B - e.piv_blocks >= 64) {
+    // merged pairs: one partition of 16 SMs (8 if refused); otherwise two dominant partitions
+    // (mode 3), one if the driver refuses the second; ordinary streams if it refuses both
+    if (e.pair) {
+      if (!partition_setup(e, kDefaultPartitionSmsPaired, 1))
+        (void)partition_setup(e, kDefaultPartitionSms, 1);
+    } else if (!partition_setup(e, kDefaultPartitionSms, 3)) {
       (void)partition_setup(e, kDefaultPartitionSms, 1);
+    }
+  }
   return SCA_OK;
 }
 
@@ -295,7 +316,8 @@ void prof_end(Engine& e, int kind, cudaStream_t s) {
 // Names of the kinds in the timeline file (SCA_PROFILE_TRACE), in KernelKind order.
 static const char* const kKindNames[kKinds] = {
     "assemble", "panel", "swap", "trinv", "prep", "update", "refine", "reduce", "diag",
-    "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv"};
+    "update_piv", "fused", "span_pivoted", "span_dominant", "panel_update", "prep_piv",
+    "update_cross"};
 
 void prof_collect(Engine& e) {
   Profiler* p = e.prof;
@@ -352,14 +374,15 @@ void release(Engine& e) {
   if (e.ev_aux1) cudaEventDestroy(e.ev_aux1);
   e.side = e.aux = nullptr;
   e.ev_fork = e.ev_join = e.ev_aux0 = e.ev_aux1 = nullptr;
-  void* ptrs[] = {e.M, e.F, e.W, e.Tinv, e.tt, e.adiag, e.piv, e.perm, e.flags, e.ld, e.d_z, e.tr, e.gd,
-                  e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status, e.d_omega};
+  void* ptrs[] = {e.M, e.F, e.W, e.F2, e.W2, e.Tinv, e.tt, e.adiag, e.piv, e.perm, e.flags, e.ld,
+                  e.d_z, e.tr, e.gd, e.eps_extra, e.d_phi, e.d_m, e.d_v, e.d_g, e.d_status,
+                  e.d_omega};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (e.h_status) cudaFreeHost(e.h_status);
   if (e.h_flags) cudaFreeHost(e.h_flags);
   e.h_flags = nullptr;
-  e.M = e.F = e.W = e.Tinv = nullptr;
+  e.M = e.F = e.W = e.F2 = e.W2 = e.Tinv = nullptr;
   e.tt = nullptr;
   e.adiag = nullptr;
   e.piv = e.perm = e.flags = nullptr;

@@ -1850,6 +1850,9 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
   bool sym = tcg && !pivoted && e.tt != nullptr;
   if (const char* v = std::getenv("SCA_SYM"))
     if (std::atoi(v) == 0) sym = false;
+  // inverses of symmetric dominant blocks: elimination steps merged in pairs
+  const bool pair_ok = sym && want_grad && e.pair && e.F2 && e.W2 && e.tmap && nb == e.nb &&
+                       sizeof(S) == 4;
   // SM partition mode 3: some of the dominant group's launches run on the second partition
   // (more SMs left to the pivoted group), by step and phase (alt_policy); each switch of
   // stream is ordered by an event
@@ -1879,6 +1882,79 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     if (alt) {
       const cudaError_t err = switch_to(pre2);
       if (err != cudaSuccess) return cuda_fail(err, "partition switch");
+    }
+    if (pair_ok && kend < N) {
+      // Two Gauss-Jordan steps K1 = [k0, kend), K2 = [kend, kend + kb2) in one pass over the
+      // lower triangle: K1's factors update only K2's cross (its row and column strips), K2's
+      // pivot block and factors follow from that, and one K = 2 nb update does the rest.
+      const int k2 = kend, kb2 = std::min(nb, N - k2);
+      S* W2 = static_cast<S*>(e.W2) + (size_t)m0 * e.fw_mat;
+      const size_t smw = 2 * sizeof(S) * (size_t)64 * (nb + 4);
+      for (int step = 0; step < 2; ++step) {
+        const int ka = step == 0 ? k0 : k2, kba = step == 0 ? kb : kb2;
+        S* Wout = step == 0 ? W : W2;
+        cudaStream_t sw = e.aux ? e.aux : s;
+        if (e.aux) {
+          cudaError_t err = cudaEventRecord(e.ev_aux0, s);
+          if (err == cudaSuccess) err = cudaStreamWaitEvent(e.aux, e.ev_aux0, 0);
+          if (err != cudaSuccess) return cuda_fail(err, "aux fork");
+        }
+        prof_begin(e, kPrep, sw);
+        k_prep_w<S><<<dim3((N + 63) / 64, cnt), 256, smw, sw>>>(
+            M, N, e.ldm, e.mat_stride, e.plane_stride, ka, kba, nb, Wout, fw_plane, e.fw_mat, 0,
+            1, split, 1);
+        prof_end(e, kPrep, sw);
+        SCA_LAUNCH_CHECK("prep w");
+        if (e.aux) {
+          cudaError_t err = cudaEventRecord(e.ev_aux1, e.aux);
+          if (err != cudaSuccess) return cuda_fail(err, "aux join");
+        }
+        prof_begin(e, kDiag, s);
+        {
+          float* TT = e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb;
+          sca_status st;
+          if constexpr (sizeof(C) == 4) {
+            if (e.tmap && e.diag_tc) {
+              st = tc_diag(M, e.ldm, e.mat_stride, e.plane_stride, cnt, ka, kba, nb, b0, e.ld,
+                           Tinv, TT, e.bf16 ? 1 : 0, e.flags, s);
+              if (st != SCA_OK) return st;
+            } else {
+              k_diag_gjb<512><<<cnt, 512, 0, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, ka, kba,
+                                                  nb, b0, e.ld, Tinv, TT, e.bf16 ? 1 : 0, e.flags);
+            }
+          } else {
+            (void)TT;
+            (void)st;
+            set_error("merged two-step update needs float32 blocks");
+            return SCA_EINVAL;
+          }
+        }
+        prof_end(e, kDiag, s);
+        SCA_LAUNCH_CHECK("diag");
+        if (e.aux) {
+          cudaError_t err = cudaStreamWaitEvent(s, e.ev_aux1, 0);
+          if (err != cudaSuccess) return cuda_fail(err, "aux join");
+        }
+        prof_begin(e, kPrep, s);
+        sca_status st = tc_prep_split(e, m0, cnt, 0, ka, kba, true, s, step == 1);
+        if (st != SCA_OK) return st;
+        prof_end(e, kPrep, s);
+        if (alt) {
+          const cudaError_t err = switch_to(upd2);
+          if (err != cudaSuccess) return cuda_fail(err, "partition switch");
+        }
+        const int kind = step == 0 ? kUpdateCross : kUpdate;
+        prof_begin(e, kind, s);
+        st = tc_update_pair(e, m0, cnt, k0, kb, k2, kb2, step == 0 ? 1 : 2, s);
+        if (st != SCA_OK) return st;
+        prof_end(e, kind, s);
+        if (alt && step == 0) {
+          const cudaError_t err = switch_to(pre2);
+          if (err != cudaSuccess) return cuda_fail(err, "partition switch");
+        }
+      }
+      k0 += nb;  // the loop adds the first step's width
+      continue;
     }
     if (pivoted) {
       // outer panel [k0, kend) factorised by shared-memory sub-panels of width nbi

@@ -100,6 +100,11 @@ struct Engine {
   void* M = nullptr;        // chunk blocks
   void* F = nullptr;        // chunk x 2 planes x N x nb (x2 hi/lo for tc)
   void* W = nullptr;        // same, W^T
+  // second factor pair of the merged two-step update (symmetric dominant blocks, tensor cores;
+  // null when that path is off), laid out as F and W
+  void* F2 = nullptr;
+  void* W2 = nullptr;
+  bool pair = false;        // merged two-step updates for the symmetric dominant blocks
   void* Tinv = nullptr;     // chunk x 2 x nb x nb complex (compute type)
   float* tt = nullptr;      // chunk x 6 x nb x nb: -T^T split planes (tensor-core prep)
   float* adiag = nullptr;   // chunk x N x 2: Re A_jj = mu - eps_j as a double-float pair
@@ -168,6 +173,7 @@ enum KernelKind {
   kSpanDom,    // wall span of the dominant group on the main stream (fork to its last kernel)
   kPanelUpd,   // pivoted group: update of the rest of the outer panel after a sub-panel
   kPrepPiv,    // pivoted group: rank-nb factors
+  kUpdateCross,  // merged two-step update: the first step's update of the second step's strips
   kKinds
 };
 
@@ -251,7 +257,12 @@ sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool 
 // Prep product of the symmetric dominant blocks: F = S (W^T T) written as the four TF32
 // planes of F, with S = -1 on the swept rows (< k0) and the rows of K replaced by -T.
 sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
-                         cudaStream_t s);
+                         cudaStream_t s, bool second = false);
+// Two adjacent Gauss-Jordan steps K1 = [k1, k1 + kb1), K2 = [k2, k2 + kb2) of the symmetric
+// dominant blocks: merge 1 updates only the cross of K2 with F1 W1; merge 2 updates every other
+// lower tile with F1 W1 + F2 W2 (the K1 mask) and the cross of K2 with F2 W2 (the K2 mask).
+sca_status tc_update_pair(Engine& e, int m0, int cnt, int k1, int kb1, int k2, int kb2, int merge,
+                          cudaStream_t s);
 
 
 // ----------------------------------------------------------- size buckets

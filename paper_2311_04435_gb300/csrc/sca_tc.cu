@@ -231,6 +231,13 @@ struct TcArgs {
   int split_out, split_neg;
   const float2* T;                     // pivot-block inverses, (mat0+mat) * t_mat + r * nb + j
   long long t_mat;
+  // Two Gauss-Jordan steps K1 = [k0, k0 + kb) and K2 = [kc0, kc0 + kcb) in one pass (symmetric
+  // blocks, tile row/column cross_t = K2's tiles).  merge 1: only the cross of K2 (tiles
+  // (cross_t, j <= cross_t) and (i > cross_t, cross_t)) with F1 W1 from the first map pair;
+  // merge 2: every lower tile, K = nb from (F, W) then nb from (F2, W2) with the K1 mask,
+  // except the cross of K2, which takes only the second pair with the K2 mask.  merge 0: one
+  // step as before.
+  int merge, cross_t, kc0, kcb;
 };
 
 // Tile t -> (block, tile row, tile column).  With `sym` only tiles on or below the diagonal
@@ -239,6 +246,11 @@ struct TcArgs {
 __device__ __forceinline__ void decode_tile(const TcArgs& a, int t, int& mat, int& tm, int& tn) {
   mat = t / a.per_block;
   const int rem = t - mat * a.per_block;
+  if (a.merge == 1) {  // the cross of tile row / column cross_t, lower tiles only
+    if (rem <= a.cross_t) { tm = a.cross_t; tn = rem; }
+    else { tm = rem; tn = a.cross_t; }
+    return;
+  }
   if (!a.sym) {
     tm = rem / a.tiles_n;
     tn = rem - tm * a.tiles_n;
@@ -249,6 +261,18 @@ __device__ __forceinline__ void decode_tile(const TcArgs& a, int t, int& mat, in
   while (i * (i + 1) / 2 > rem) --i;
   tm = i;
   tn = rem - i * (i + 1) / 2;
+}
+
+// K stages [ks_lo, ks_hi) of a tile (units of kKE elements; stages from ks_a on come from the
+// second map pair) and the Gauss-Jordan mask [mk0, mk0 + mkb) of its epilogue.
+__device__ __forceinline__ void tile_k(const TcArgs& a, int tm, int tn, int kke, int& ks_lo,
+                                       int& ks_hi, int& mk0, int& mkb) {
+  const int ka = a.nb / kke;
+  const bool cross = a.merge == 2 && (tm == a.cross_t || tn == a.cross_t);
+  ks_lo = cross ? ka : 0;
+  ks_hi = a.merge == 2 ? 2 * ka : ka;
+  mk0 = cross ? a.kc0 : a.k0;
+  mkb = cross ? a.kcb : a.kb;
 }
 
 // Shared-memory stage layout (each slot one 128-row plane of 64-byte K rows, 8 KB,
@@ -263,7 +287,8 @@ __constant__ int kWPlaneOfSlot[4] = {0, 1, 2, 3};  // re_hi, im_hi, re_lo, im_lo
 template <bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_update_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmW,
-                const __grid_constant__ CUtensorMap tmM, TcArgs a) {
+                const __grid_constant__ CUtensorMap tmM, const __grid_constant__ CUtensorMap tmF2,
+                const __grid_constant__ CUtensorMap tmW2, TcArgs a) {
   constexpr int kKE = BF ? 32 : kKS;  // K elements per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -303,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int ksteps = a.nb / kKE;
+  const int ka = a.nb / kKE;  // K stages per map pair
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -323,18 +348,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(&rfull[rslot]);
         if (++rslot == kRing) { rslot = 0; rphase ^= 1; }
         if (t < 0) break;
-        int mat, tm, tn;
+        int mat, tm, tn, ks_lo, ks_hi, mk0, mkb;
         decode_tile(a, t, mat, tm, tn);
+        tile_k(a, tm, tn, kKE, ks_lo, ks_hi, mk0, mkb);
         const int frow = a.r0 + tm * kBM, wrow = a.c0 + tn * kBNc;
-        for (int ks = 0; ks < ksteps; ++ks) {
+        for (int ks = ks_lo; ks < ks_hi; ++ks) {
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
           mbar_expect_tx(&full[stage], kStageBytes);
           unsigned char* st = smem + stage * kStageBytes;
+          const bool second = ks >= ka;
+          const CUtensorMap* mf = second ? &tmF2 : &tmF;
+          const CUtensorMap* mw = second ? &tmW2 : &tmW;
+          const int kx = (second ? ks - ka : ks) * kKE;
           for (int s = 0; s < 4; ++s)
-            tma_load_3d(st + s * kTileBytes, &tmF, &full[stage], ks * kKE, frow,
+            tma_load_3d(st + s * kTileBytes, mf, &full[stage], kx, frow,
                         (a.mat0 + mat) * a.fplanes + kFPlaneOfSlot[s]);
           for (int s = 0; s < 4; ++s)
-            tma_load_3d(st + (4 + s) * kTileBytes, &tmW, &full[stage], ks * kKE, wrow,
+            tma_load_3d(st + (4 + s) * kTileBytes, mw, &full[stage], kx, wrow,
                         (a.mat0 + mat) * a.wplanes + kWPlaneOfSlot[s]);
           last_parity[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -365,7 +395,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256);
         bool ok = true;
-        for (int ks = 0; ks < ksteps; ++ks) {
+        int ks_lo, ks_hi;
+        {
+          int mat, tm, tn, mk0, mkb;
+          decode_tile(a, t, mat, tm, tn);
+          tile_k(a, tm, tn, kKE, ks_lo, ks_hi, mk0, mkb);
+        }
+        for (int ks = ks_lo; ks < ks_hi; ++ks) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + stage * kStageBytes);
@@ -385,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             constexpr uint32_t kI128 = idesc<BF, false, false>();
             constexpr uint32_t kI128n = idesc<BF, false, true>();
             const uint32_t d_im = d_tmem + (uint32_t)kBNc;  // imaginary half of the accumulator
-            const uint32_t acc0 = (ks > 0 || k8 > 0) ? 1u : 0u;
+            const uint32_t acc0 = (ks > ks_lo || k8 > 0) ? 1u : 0u;
             // (re | im) += F_re (W_re; W_im)
             mma_d<BF>(d_tmem, fr_hi, bre_hi, kI256, acc0);
             mma_d<BF>(d_tmem, fr_hi, bre_lo, kI256, 1u);
@@ -449,11 +485,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (leader && !a.split_out && prefetched != t) issue_load(t, 0, ebuf);
       const int buf = iter & 1;
       const uint32_t use = (uint32_t)(iter >> 1);
-      int mat, tm, tn;
+      int mat, tm, tn, ks_lo, ks_hi, mk0, mkb;
       decode_tile(a, t, mat, tm, tn);
+      tile_k(a, tm, tn, kKE, ks_lo, ks_hi, mk0, mkb);
       const int i = a.r0 + tm * kBM + row;
       const int j0 = a.c0 + tn * kBNc;
-      const bool rowk = a.gj && i >= a.k0 && i < a.k0 + a.kb;
+      const bool rowk = a.gj && i >= mk0 && i < mk0 + mkb;
       if (!epi_all(mbar_wait(&tfull[buf], use & 1, abort_flag))) { ok = false; break; }
       tc_fence_after();
       const uint32_t tbase = tmem_base + (uint32_t)(buf * 256) + ((uint32_t)(q * 32) << 16);
@@ -469,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int jc = j0 + c * kEpiCols;
           const bool neg = a.split_neg && i < a.k0;
           const float2* trow =
-              rowk ? a.T + (size_t)(a.mat0 + mat) * a.t_mat + (size_t)(i - a.k0) * a.nb : nullptr;
+              rowk ? a.T + (size_t)(a.mat0 + mat) * a.t_mat + (size_t)(i - mk0) * a.nb : nullptr;
           unsigned char* s0 = epi;
           unsigned char* s1 = epi + kEpiBufBytes;
           if constexpr (BF) {
@@ -578,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         eph[eb] ^= 1;
         unsigned char* st = epi + eb * kEpiBufBytes;
         const int jc = j0 + c * kEpiCols;
-        const bool colk = a.gj && (jc < a.k0 + a.kb) && (jc + kEpiCols > a.k0);
+        const bool colk = a.gj && (jc < mk0 + mkb) && (jc + kEpiCols > mk0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int off = row * 128 + ((k ^ (row & 7)) << 4);
@@ -589,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int j = jc + 4 * k + e;
-              const bool keep = !(rowk || (j >= a.k0 && j < a.k0 + a.kb));
+              const bool keep = !(rowk || (j >= mk0 && j < mk0 + mkb));
               if (!keep) { (&vr.x)[e] = 0.f; (&vi.x)[e] = 0.f; }
             }
           }
@@ -1064,6 +1101,10 @@ struct TcMaps {
   CUtensorMap TL;      // -inv(L)^T bf16 planes of the pivoted group (second halves of TT's)
   CUtensorMap FP;      // planar F = M[:, K] T (W scratch planes 4, 5): output of that product
   CUtensorMap FO;      // the F planes themselves: split output of the symmetric prep product
+  // second factor pair of a merged two-step update of the symmetric dominant blocks (F2, W2
+  // planes as F, W) and the split output map of its prep product
+  CUtensorMap F2, W2, FO2;
+  bool has2 = false;
   int sms = 0;
 };
 
@@ -1171,6 +1212,16 @@ sca_status tc_prepare(Engine& e) {
       return SCA_ECUDA;
     }
   }
+  if (e.F2 && e.W2) {
+    if (!make_fw_map(&t->F2, e.F2, e.nb, e.N, zf, e.bf16) ||
+        !make_fw_map(&t->W2, e.W2, e.nb, e.N, zf, e.bf16) ||
+        !make_m_map_rows(&t->FO2, e.F2, e.nb, e.N, e.nb, (long long)e.fw_plane, zf, e.bf16)) {
+      delete t;
+      set_error("cuTensorMapEncodeTiled failed for the merged two-step update");
+      return SCA_ECUDA;
+    }
+    t->has2 = true;
+  }
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1240,6 +1291,9 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   a.split_out = a.split_neg = 0;
   a.T = nullptr;
   a.t_mat = 0;
+  a.merge = 0;
+  a.cross_t = -1;
+  a.kc0 = a.kcb = 0;
   if (a.tiles <= 0) return SCA_OK;
   if (e.tc_next >= kCounters) {
     set_error("too many tensor-core launches in one pass");
@@ -1247,14 +1301,67 @@ sca_status tc_update(Engine& e, int m0, int cnt, int k0, int kb, int r0, int c0,
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
-  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, a);
+  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, t->F, t->W, a);
+  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, t->F, t->W, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 update launch");
   return SCA_OK;
 }
 
+
+sca_status tc_update_pair(Engine& e, int m0, int cnt, int k1, int kb1, int k2, int kb2, int merge,
+                          cudaStream_t s) {
+  TcMaps* t = static_cast<TcMaps*>(e.tmap);
+  if (!t || !t->has2 || (merge != 1 && merge != 2) || kb1 != e.nb || k2 != k1 + kb1 ||
+      kb2 < 1 || kb2 > e.nb || k2 % kBM != 0) {
+    set_error("merged tensor-core update: needs the second factor pair and two adjacent steps");
+    return SCA_EINVAL;
+  }
+  TcArgs a;
+  a.M = static_cast<float*>(e.M) + (size_t)m0 * e.mat_stride;
+  a.mat0 = m0;
+  a.N = e.N;
+  a.ldm = e.ldm;
+  a.mat_stride = (long long)e.mat_stride;
+  a.plane_stride = (long long)e.plane_stride;
+  a.nb = e.nb;
+  a.r0 = 0;
+  a.c0 = 0;
+  a.k0 = k1;
+  a.kb = kb1;
+  a.gj = 1;
+  a.tiles_m = a.tiles_n = (e.N + kBM - 1) / kBM;
+  a.sym = 1;
+  a.merge = merge;
+  a.cross_t = k2 / kBM;
+  a.kc0 = k2;
+  a.kcb = kb2;
+  a.per_block = merge == 1 ? a.tiles_m : a.tiles_m * (a.tiles_m + 1) / 2;
+  a.tiles = a.per_block * cnt;
+  a.fplanes = a.wplanes = (int)(e.fw_mat / e.fw_plane);
+  a.m_zmul = 2;
+  a.m_zoff = 0;
+  a.err = e.flags;
+  a.split_out = a.split_neg = 0;
+  a.T = nullptr;
+  a.t_mat = 0;
+  if (a.tiles <= 0) return SCA_OK;
+  if (e.tc_next >= kCounters) {
+    set_error("too many tensor-core launches in one pass");
+    return SCA_EINVAL;
+  }
+  a.counter = e.tc_counters + e.tc_next++;
+  const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
+  if (e.bf16)
+    k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, t->F2, t->W2, a);
+  else
+    k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->F, t->W, t->M, t->F2, t->W2, a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "tcgen05 merged update launch");
+  return SCA_OK;
+}
 
 sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
@@ -1288,6 +1395,9 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   a.split_out = a.split_neg = 0;
   a.T = nullptr;
   a.t_mat = 0;
+  a.merge = 0;
+  a.cross_t = -1;
+  a.kc0 = a.kcb = 0;
   if (a.tiles <= 0) return SCA_OK;
   if (e.tc_next >= kCounters) {
     set_error("too many tensor-core launches in one pass");
@@ -1295,7 +1405,7 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, a);
+  k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FP, t->W, t->TT, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
@@ -1303,9 +1413,9 @@ sca_status tc_prep(Engine& e, int m0, int cnt, int r0, cudaStream_t s) {
 }
 
 sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool gj,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool second) {
   TcMaps* t = static_cast<TcMaps*>(e.tmap);
-  if (!t || !e.tt) {
+  if (!t || !e.tt || (second && !t->has2)) {
     set_error("tensor-core prep used before tc_prepare");
     return SCA_ENOSTATE;
   }
@@ -1336,6 +1446,9 @@ sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, boo
   a.split_neg = 1;
   a.T = static_cast<const float2*>(e.Tinv);
   a.t_mat = 2ll * e.nb * e.nb;
+  a.merge = 0;
+  a.cross_t = -1;
+  a.kc0 = a.kcb = 0;
   if (a.tiles <= 0) return SCA_OK;
   if (e.tc_next >= kCounters) {
     set_error("too many tensor-core launches in one pass");
@@ -1343,8 +1456,11 @@ sca_status tc_prep_split(Engine& e, int m0, int cnt, int r0, int k0, int kb, boo
   }
   a.counter = e.tc_counters + e.tc_next++;
   const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
-  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(t->W, t->TT, t->FO, a);
+  // A = the W planes of this step (W or W2), output = its F planes (F or F2)
+  const CUtensorMap& ta = second ? t->W2 : t->W;
+  const CUtensorMap& to = second ? t->FO2 : t->FO;
+  if (e.bf16) k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(ta, t->TT, to, ta, t->TT, a);
+  else k_update_tc<false><<<grid, kThreads, kSmemBytes, s>>>(ta, t->TT, to, ta, t->TT, a);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return cuda_fail(err, "tcgen05 prep launch");
@@ -1391,14 +1507,17 @@ sca_status tc_prep_piv(Engine& e, int m0, int cnt, int r0, int k0, int kb, bool 
     a.split_neg = 0;
     a.T = static_cast<const float2*>(e.Tinv);
     a.t_mat = 2ll * e.nb * e.nb;
+    a.merge = 0;
+    a.cross_t = -1;
+    a.kc0 = a.kcb = 0;
     if (e.tc_next >= kCounters) {
       set_error("too many tensor-core launches in one pass");
       return SCA_EINVAL;
     }
     a.counter = e.tc_counters + e.tc_next++;
     const int grid = std::min(a.tiles, e.tc_cap > 0 ? std::min(e.tc_cap, t->sms) : t->sms);
-    k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->W, part == 0 ? t->TT : t->TL, t->FO,
-                                                          a);
+    const CUtensorMap& tb = part == 0 ? t->TT : t->TL;
+    k_update_tc<true><<<grid, kThreads, kSmemBytes, s>>>(t->W, tb, t->FO, t->W, tb, a);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "tcgen05 pivoted prep launch");

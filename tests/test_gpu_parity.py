@@ -417,7 +417,11 @@ def test_profile_kinds_and_group_spans():
         after = c.profile_read()
     steps = -(-p.N // 128)  # elimination steps of width 128
     assert prof["span_pivoted"][1] == 1 and prof["span_dominant"][1] == 1
-    assert prof["update"][1] == steps and prof["diag"][1] == steps
+    # the dominant blocks' steps run in merged pairs: per pair one update of the second step's
+    # strips (update_cross) and one merged update; an odd last step updates alone
+    pairs = steps // 2
+    assert prof["update_cross"][1] == pairs and prof["update"][1] == steps - pairs
+    assert prof["diag"][1] == steps
     assert prof["panel"][1] > 0 and prof["refine"][1] >= 2 and prof["reduce"][1] == 1
     # 16-wide sub-panels: the rest of each outer panel is updated after every sub-panel
     assert prof["panel_update"][1] > 0 and prof["prep_piv"][1] == steps
