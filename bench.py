@@ -137,14 +137,14 @@ def peaks():
 TF32_OVER_BF16 = 1.1 / 2.25
 DEFAULT_PREC = "bf16x3"
 DEFAULT_SM_PARTITION = -1  # the library's default (8 SMs for 1024 <= N <= 2048, >= 64 dominant blocks)
-# DRAM traffic of one symmetric dominant-group update launch, per block (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum averaged over the 13 update launches of one
-# step of the 16-block workload ionic_40x40_w8, divided by 16; traffic grows with the blocks),
-# for the kernel as captured (profiles/): BF16x3 344.5 MB, 3xTF32 404.0 MB per 16-block launch.
-UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 344.5e6 / 16, "3xtf32": 404.0e6 / 16}
+# DRAM traffic of the dominant group's update launches, per block: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the 7 update launches of one step of the 16-block workload
+# ionic_40x40_w8 (6 merged pairs at 400.2 MB, one single last step at 344.6 MB per 16-block
+# launch), averaged and divided by 16 (traffic grows with the blocks; profiles/).
+UPDATE_BYTES_PER_BLOCK_N1600 = {"bf16x3": 392.3e6 / 16}
 # sha256 (first 16 hex digits) of csrc/sca_tc.cu when those counters were taken: the traffic
 # is reported only while the update kernel's source is unchanged, else null.
-UPDATE_TRAFFIC_SOURCE_SHA16 = None
+UPDATE_TRAFFIC_SOURCE_SHA16 = "95644598858c27db"
 
 
 def tc_source_sha16():
@@ -320,7 +320,8 @@ def run_ours(args):
     if sym and params.N == 1600 and per_block and src_sha == UPDATE_TRAFFIC_SOURCE_SHA16:
         traffic = round(per_block * n_dom, 0)  # bytes per launch
     traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 16-block capture "
-                    "(workload ionic_40x40_w8) per block, times the dominant blocks; reported "
+                    "(workload ionic_40x40_w8), mean over the step's update launches, per "
+                    "block, times the dominant blocks; reported "
                     f"only for the kernel source it was taken on (sca_tc.cu sha16 "
                     f"{UPDATE_TRAFFIC_SOURCE_SHA16}; this run {src_sha})")
     per_kernel = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()}
