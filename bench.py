@@ -451,14 +451,40 @@ def run_ours(args):
                  "ms_per_step": round(mt_s * 1e3 / args.metro_steps, 3), "delta": 0.01,
                  "acceptance": round(float(acc.mean()), 3), "timed_steps": args.metro_steps}
 
+    # ---------------- the pivoted blocks' panel factorisation in float64 (same workload)
+    panel64, blk_p64 = None, None
+    if args.variant_steps > 0 and rank == 0 and prec in ("3xtf32", "bf16x3") and \
+            api.pivoted_blocks(params) > 0:
+        cq = api.Context(params)
+        cq.set_stream(stream)
+        cq.set_panel_precision("fp64")
+        cq.adam_init(adam)
+        cq.adam_step(1)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        omq, gmq = cq.adam_step(args.variant_steps)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        msq = a0.elapsed_time(a1) / args.variant_steps
+        if not args.no_cpu_baseline:
+            blk_p64 = cq.blocks(phi_s, grad=True)
+        cq.close()
+        panel64 = {"steps_per_s": round(1e3 / msq, 4), "ms_per_step": round(msq, 3),
+                   "timed_steps": args.variant_steps, "warmup": 1, "final_omega": omq,
+                   "over_fp32_panel": round(msq / ms_per_step, 3)}
+
     cpu = None
     mixed_vs_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, sample, o_ld, o_gd = cpu_baseline(args, wl, with_blocks=True)
+        npb = api.pivoted_blocks(params)
         mixed_vs_oracle = {"blocks": [int(b) for b in sample],
-                           prec: block_errors(blk_gpu, sample, o_ld, o_gd)}
+                           prec: block_errors(blk_gpu, sample, o_ld, o_gd, npb)}
+        if blk_p64 is not None:
+            mixed_vs_oracle[prec + "_fp64_panel"] = block_errors(blk_p64, sample, o_ld, o_gd, npb)
         if blk_64 is not None:
-            mixed_vs_oracle["fp64"] = block_errors(blk_64, sample, o_ld, o_gd)
+            mixed_vs_oracle["fp64"] = block_errors(blk_64, sample, o_ld, o_gd, npb)
         mixed_vs_oracle["note"] = ("per-block ln|det A_b| and sigma Re G_b,ii at the seeded "
                                    "start field against the FP64 oracle on the CPU baseline's "
                                    "sample of blocks")
@@ -493,6 +519,7 @@ def run_ours(args):
             "fp64_path": fp64,
             "no_pivoting_variant": nopiv,
             "other_precision": other,
+            "fp64_panel_variant": panel64,
             "dos": dos,
             "metropolis": metro,
             "clocks": clk,
@@ -506,16 +533,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def block_errors(blk, sample, o_ld, o_gd):
-    """Largest errors of the GPU's per-block ld and sigma Re G_ii on the sampled blocks."""
+def block_errors(blk, sample, o_ld, o_gd, n_piv=0):
+    """Largest errors of the GPU's per-block ld and sigma Re G_ii on the sampled blocks, and on
+    the sampled pivoted ones (blocks b < n_piv) alone."""
     import numpy as np
     ld, gd = blk
-    d_ld = np.abs(ld[sample] - o_ld)
-    d_gd = np.abs(gd[sample] - o_gd)
-    return {"ld_max_abs_err": float(d_ld.max()),
-            "ld_max_rel_err": float((d_ld / np.maximum(1.0, np.abs(o_ld))).max()),
-            "gdiag_max_abs_err": float(d_gd.max()),
-            "gdiag_scale": float(max(1.0, np.abs(o_gd).max()))}
+    sample = np.asarray(sample)
+
+    def errs(sel):
+        d_ld = np.abs(ld[sample[sel]] - o_ld[sel])
+        d_gd = np.abs(gd[sample[sel]] - o_gd[sel])
+        return {"ld_max_abs_err": float(d_ld.max()),
+                "ld_max_rel_err": float((d_ld / np.maximum(1.0, np.abs(o_ld[sel]))).max()),
+                "gdiag_max_abs_err": float(d_gd.max()),
+                "gdiag_scale": float(max(1.0, np.abs(o_gd[sel]).max()))}
+    out = errs(np.ones(len(sample), bool))
+    piv = sample < n_piv
+    if piv.any():
+        out["pivoted"] = errs(piv)
+    return out
 
 
 def cpu_baseline(args, wl, steps_timed=1, with_blocks=False):
@@ -532,7 +568,14 @@ def cpu_baseline(args, wl, steps_timed=1, with_blocks=False):
     nblk = min(nblk, B)
     p = oracle.make_params(wl.L, wl.n_omega, U=wl.U, T=wl.T, delta=wl.delta, t=wl.t, mu=wl.mu)
     phi = inputs.seed_phi(wl.seed, wl.L * wl.L)
-    blocks = np.linspace(0, B - 1, nblk).astype(np.int32)
+    # the pivoted blocks (lowest frequencies, omega_n <= 4|t|: 2 per frequency) first, up to
+    # three quarters of the sample, then dominant blocks spread over the rest
+    n_piv = 0
+    while n_piv < wl.n_omega and (2 * n_piv + 1) * math.pi * wl.T <= 4.0 * abs(wl.t) * (1 + 1e-3):
+        n_piv += 1
+    take = min(2 * n_piv, (3 * nblk) // 4)
+    rest = np.linspace(2 * n_piv, B - 1, nblk - take) if nblk > take else np.zeros(0)
+    blocks = np.concatenate([np.arange(take), rest]).astype(np.int32)
     t0 = time.perf_counter()
     o_ld, o_gd = oracle.blocks_sample(p, phi, blocks)
     dt = time.perf_counter() - t0

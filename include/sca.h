@@ -344,6 +344,14 @@ sca_status sca_metropolis_step(sca_ctx* ctx, int32_t n_steps, double* omega_trac
 typedef enum { SCA_PIVOT_PARTIAL = 0, SCA_PIVOT_NONE = 1 } sca_pivot;
 sca_status sca_set_pivoting(sca_ctx* ctx, int32_t mode);
 
+/* Arithmetic of the pivoted blocks' panel factorisation (the sub-panel LU with its pivot search,
+ * the interchanges with U12 and the rest-of-panel update) on the reduced-precision paths:
+ * SCA_PREC_FP32 (default: the blocks' compute type) or SCA_PREC_FP64 (float64 arithmetic on
+ * the float32 blocks; the doubled shared-memory panel narrows the sub-panels, e.g. to 4
+ * columns at N = 1600).  The pivot-block inverses and the contractions are unchanged.  Float64
+ * contexts accept only SCA_PREC_FP64.  Applies from the next call; SCA_EINVAL otherwise. */
+sca_status sca_set_panel_precision(sca_ctx* ctx, int32_t prec);
+
 /* SM partitions for the two block groups (driver green contexts).  The pivoted group (the
  * lowest frequencies, a chain of short dependent launches) and the dominant group (bandwidth-
  * bound launches that fill every SM they reach) run side by side on one GPU; with a

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("sca_set_stream", ctypes.c_int, [_vp, _vp]),
     ("sca_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("sca_set_pivoting", ctypes.c_int, [_vp, ctypes.c_int32]),
+    ("sca_set_panel_precision", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("sca_set_sm_partition", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("sca_sm_partition", ctypes.c_int, [_vp, _i32p, _i32p]),
     ("sca_dos", ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int32, ctypes.c_double, _dp]),

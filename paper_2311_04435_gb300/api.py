@@ -258,6 +258,13 @@ class Context:
             raise ValueError(f"pivoting mode must be one of {sorted(modes)}")
         check(_lib.lib().sca_set_pivoting(self._h, modes[mode]))
 
+    def set_panel_precision(self, prec: str = "fp32"):
+        """Arithmetic of the pivoted blocks' panel factorisation: 'fp32' (the blocks' compute
+        type, default) or 'fp64' (float64 on the float32 blocks of the mixed path)."""
+        if prec not in ("fp32", "fp64"):
+            raise ValueError("panel precision must be 'fp32' or 'fp64'")
+        check(_lib.lib().sca_set_panel_precision(self._h, _lib.PREC[prec]))
+
     def set_sm_partition(self, pivoted_sms: int = 0, mode: str = "dominant"):
         """Keep the dominant group's launches off `pivoted_sms` SMs (green contexts); mode
         'dominant' leaves the pivoted group free to use any SM, 'both' confines it to its

@@ -144,6 +144,12 @@ sca_status plan(const sca_params& p, Engine& e) {
   // narrower than nb: the outer panel is factorised in sub-panels of at most 16 columns
   if (nbp < e.nb) nbp = std::min(nbp, 16);
   e.nb_piv = nbp;
+  {  // a float64 panel (16 bytes per complex entry) on the float32 blocks of the mixed path
+    int n64 = 1;
+    while (n64 * 2 <= e.nb && (size_t)e.N * (n64 * 2 + 1) * 16 <= 220 * 1024) n64 *= 2;
+    if (n64 < e.nb) n64 = std::min(n64, 16);
+    e.nb_piv64 = n64;
+  }
   if (const char* v = std::getenv("SCA_DIAG_TC")) e.diag_tc = std::atoi(v) != 0;
   if (const char* v = std::getenv("SCA_ALT_POLICY")) e.alt_policy = std::min(3, std::max(1, std::atoi(v)));
   e.ldm = (int)round_up((size_t)e.N, 32);
@@ -894,6 +900,17 @@ sca_status sca_set_pivoting(sca_ctx* c, int32_t mode) {
   }
   c->e.piv_blocks = (mode == SCA_PIVOT_NONE) ? 0 : c->e.piv_planned;
   c->e.nopiv = (mode == SCA_PIVOT_NONE);
+  return SCA_OK;
+}
+
+sca_status sca_set_panel_precision(sca_ctx* c, int32_t prec) {
+  if (!c || (prec != SCA_PREC_FP64 && prec != SCA_PREC_FP32) ||
+      (c->e.fp64 && prec != SCA_PREC_FP64)) {
+    set_error("bad context or panel precision (SCA_PREC_FP32 or SCA_PREC_FP64; float64 blocks "
+              "take only SCA_PREC_FP64)");
+    return SCA_EINVAL;
+  }
+  c->e.panel_fp64 = !c->e.fp64 && prec == SCA_PREC_FP64;
   return SCA_OK;
 }
 

@@ -120,7 +120,9 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(256)
     k_gemm_panel(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int s0, int kbi,
                  int c_end) {
-  constexpr int NCMAX = sizeof(C) == 8 ? 64 : 128;
+  // columns of the outer panel: nb = 32 on the float64 path, up to 128 with float32 storage
+  // (also when the panel computes in float64)
+  constexpr int NCMAX = sizeof(S) == 8 ? 64 : 128;
   constexpr int RSTEP = 256 / NCMAX;               // rows covered by one pass of the CTA
   constexpr int MA = kGemmPanelRows / RSTEP;       // A22 entries per thread
   constexpr int MU = 16 / RSTEP;                   // U12 entries per thread
@@ -1828,6 +1830,47 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, 
   return SCA_OK;
 }
 
+// Pivoted outer panel [k0, k0 + kb) of the slots in M .. (cnt blocks) by shared-memory sub-panels
+// of width nb_sub, in compute type CP: each sub-panel's pivoted LU, its interchanges on the
+// other columns with U12 for the rest of the outer panel, then A22 -= L21 U12 there.
+template <typename S, typename CP>
+sca_status piv_subpanels(Engine& e, S* M, int b0, int cnt, int k0, int kb, int nb_sub, int* piv,
+                         int* perm, bool want_grad, cudaStream_t s) {
+  const int N = e.N, kend = k0 + kb;
+  const int nbi = std::min(nb_sub, kb);
+  for (int s0 = k0; s0 < kend; s0 += nbi) {
+    const int kbi = std::min(nbi, kend - s0);
+    const size_t sm = sizeof(cpx<CP>) * (size_t)(N - s0) * (kbi + 1) + 5 * sizeof(int) * kbi;
+    prof_begin(e, kPanel, s);
+    k_panel_smem<S, CP, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, s0,
+                                                   kbi, b0, e.ld, piv, perm, e.flags);
+    prof_end(e, kPanel, s);
+    SCA_LAUNCH_CHECK("panel");
+    if (!want_grad && s0 + kbi == N) break;
+    const int jstart = want_grad ? 0 : k0;
+    const int ncols = N - jstart;
+    // interchanges on the other columns, then U12 for the rest of the outer panel
+    if (s0 + kbi < kend && kbi > 16) {
+      set_error("pivoted sub-panel wider than 16 inside an outer panel");
+      return SCA_EINVAL;
+    }
+    prof_begin(e, kSwap, s);
+    k_swap_trsm<S, CP><<<dim3((ncols + 127) / 128, cnt), 128, 0, s>>>(
+        M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, jstart, kend, piv);
+    prof_end(e, kSwap, s);
+    SCA_LAUNCH_CHECK("swap");
+    if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
+      prof_begin(e, kPanelUpd, s);
+      const int gx = (N - s0 - kbi + kGemmPanelRows - 1) / kGemmPanelRows;
+      k_gemm_panel<S, CP><<<dim3(gx, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
+                                                         e.plane_stride, s0, kbi, kend);
+      prof_end(e, kPanelUpd, s);
+      SCA_LAUNCH_CHECK("panel update");
+    }
+  }
+  return SCA_OK;
+}
+
 // One group of blocks (workspace slots m0 .. m0+cnt-1, global indices b0 ..) through all
 // elimination steps.  pivoted: partial pivoting with the shared-memory panel of width nb;
 // otherwise the blocks are diagonally dominant and only the pivot block is factorised.
@@ -1957,38 +2000,14 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       continue;
     }
     if (pivoted) {
-      // outer panel [k0, kend) factorised by shared-memory sub-panels of width nbi
-      const int nbi = std::min(e.nb_piv, kb);
-      for (int s0 = k0; s0 < kend; s0 += nbi) {
-        const int kbi = std::min(nbi, kend - s0);
-        const size_t sm = sizeof(cpx<C>) * (size_t)(N - s0) * (kbi + 1) + 5 * sizeof(int) * kbi;
-        prof_begin(e, kPanel, s);
-        k_panel_smem<S, C, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
-                                                      s0, kbi, b0, e.ld, piv, perm, e.flags);
-        prof_end(e, kPanel, s);
-        SCA_LAUNCH_CHECK("panel");
-        if (!want_grad && s0 + kbi == N) break;
-        const int jstart = want_grad ? 0 : k0;
-        const int ncols = N - jstart;
-        // interchanges on the other columns, then U12 for the rest of the outer panel
-        if (s0 + kbi < kend && kbi > 16) {
-          set_error("pivoted sub-panel wider than 16 inside an outer panel");
-          return SCA_EINVAL;
-        }
-        prof_begin(e, kSwap, s);
-        k_swap_trsm<S, C><<<dim3((ncols + 127) / 128, cnt), 128, 0, s>>>(
-            M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, jstart, kend, piv);
-        prof_end(e, kSwap, s);
-        SCA_LAUNCH_CHECK("swap");
-        if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
-          prof_begin(e, kPanelUpd, s);
-          const int gx = (N - s0 - kbi + kGemmPanelRows - 1) / kGemmPanelRows;
-          k_gemm_panel<S, C><<<dim3(gx, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,
-                                                           e.plane_stride, s0, kbi, kend);
-          prof_end(e, kPanelUpd, s);
-          SCA_LAUNCH_CHECK("panel update");
-        }
-      }
+      // outer panel [k0, kend) factorised by shared-memory sub-panels; float64 arithmetic in
+      // them when the context asks for it (sca_set_panel_precision), else the compute type
+      sca_status st;
+      if (e.panel_fp64 && sizeof(C) == 4)
+        st = piv_subpanels<S, double>(e, M, b0, cnt, k0, kb, e.nb_piv64, piv, perm, want_grad, s);
+      else
+        st = piv_subpanels<S, C>(e, M, b0, cnt, k0, kb, e.nb_piv, piv, perm, want_grad, s);
+      if (st != SCA_OK) return st;
       if (!want_grad && kend == N) break;
     }
     const bool last_lu = !want_grad && kend == N;  // LU: nothing trails the last pivot block
@@ -2271,6 +2290,9 @@ sca_status set_smem_limits() {
   if (once.done()) return SCA_OK;
   cudaError_t err;
   if ((err = allow_max_smem(k_panel_smem<S, C, 512>)) != cudaSuccess) return cuda_fail(err, "smem panel");
+  if constexpr (sizeof(S) == 4)  // the float64 panel of the mixed path
+    if ((err = allow_max_smem(k_panel_smem<S, double, 512>)) != cudaSuccess)
+      return cuda_fail(err, "smem panel fp64");
   if ((err = allow_max_smem(k_prep_w<S>)) != cudaSuccess) return cuda_fail(err, "smem prep");
   if ((err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, true>)) != cudaSuccess ||
       (err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, false>)) != cudaSuccess)

@@ -84,6 +84,8 @@ struct Engine {
   int L = 0, N = 0, B = 0;
   int nb = 0;            // Gauss-Jordan / LU block width (diagonally dominant blocks)
   int nb_piv = 0;        // block width of the pivoted group (shared-memory panel)
+  int nb_piv64 = 0;      // the same for a float64 panel on float32 blocks
+  bool panel_fp64 = false;  // the pivoted group's sub-panels compute in float64 (mixed path)
   bool diag_tc = true;   // dominant pivot-block inverses on the tensor cores (nb = 128)
   int piv_planned = 0;   // piv_blocks under partial pivoting
   int piv_blocks = 0;    // blocks b < piv_blocks need partial pivoting (omega_n <= 4|t|)

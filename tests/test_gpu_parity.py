@@ -544,3 +544,28 @@ def test_c3_autograd_gradient_matches_central_differences():
         assert np.all(err <= 1e-5 * np.maximum(1.0, np.abs(fd))), (prec, err.max())
     scale = max(1.0, np.abs(grads["fp64"]).max())
     assert np.max(np.abs(grads["bf16x3"] - grads["fp64"])) <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("L,nw", [(20, 10), (40, 8)])
+def test_fp64_panel_on_the_mixed_path_matches_oracle(L, nw):
+    """The pivoted blocks' panel factorisation in float64 on the float32 blocks of the BF16x3
+    path (sca_set_panel_precision): per-block ln|det| and diag(G) of every pivoted block (and
+    the dominant ones) against the oracle at the mixed tolerances, beside the float32 panel.
+    400 sites (16-wide float64 sub-panels) and 1600 sites (4-wide), 12 pivoted blocks each."""
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=0.5, prec="bf16x3")
+    npiv = api.pivoted_blocks(p)
+    assert npiv == 12
+    phi = inputs.seed_phi(8, p.N)
+    res = {}
+    for panel in ("fp32", "fp64"):
+        with api.Context(p) as c:
+            c.set_panel_precision(panel)
+            res[panel] = c.blocks(phi, grad=True)
+        with pytest.raises(ValueError):
+            c.set_panel_precision("bf16")
+    sample = list(range(npiv)) + [npiv, 2 * nw - 1]
+    o_ld, o_gd = oracle.blocks_sample(oparams(p), phi, sample)
+    t = tol("bf16x3")
+    for ld, gd in res.values():
+        assert np.allclose(ld[sample], o_ld, rtol=t["ld"], atol=t["ld"])
+        assert np.max(np.abs(gd[sample] - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
