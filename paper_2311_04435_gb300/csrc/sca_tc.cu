@@ -123,6 +123,10 @@ __device__ __forceinline__ void bulk_wait_read0() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// all but the most recent bulk group have finished reading their shared-memory source
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -458,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t eph[kEpiBufs] = {0, 0};
     bool pending[kEpiBufs] = {false, false};  // leader: load issued, not yet consumed
     int ebuf = 0;
+    int sbuf = 0;  // staging buffer of the next split-output chunk (bf16 planes)
     bool ok = true;
     // issue the load of chunk c of tile t into staging buffer eb
     auto issue_load = [&](int t, int c, int eb) {
@@ -501,14 +506,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld32(tbase + (uint32_t)(c * kEpiCols), cr);
           tmem_ld32(tbase + (uint32_t)(kBNc + c * kEpiCols), ci);
           tmem_ld_wait();
-          if (leader) bulk_wait_read0();  // the previous chunk's stores have read the staging
+          // bf16 planes fill one staging buffer: chunks alternate between the two, so a chunk
+          // waits only for the stores of the chunk before last (which read this buffer); the
+          // float planes fill both buffers and wait for the previous chunk's stores
+          if (leader) {
+            if constexpr (BF) bulk_wait_read1();
+            else bulk_wait_read0();
+          }
           epi_bar();
           const int jc = j0 + c * kEpiCols;
           const bool neg = a.split_neg && i < a.k0;
           const float2* trow =
               rowk ? a.T + (size_t)(a.mat0 + mat) * a.t_mat + (size_t)(i - mk0) * a.nb : nullptr;
-          unsigned char* s0 = epi;
+          unsigned char* s0 = BF ? epi + sbuf * kEpiBufBytes : epi;
           unsigned char* s1 = epi + kEpiBufBytes;
+          sbuf ^= 1;
           if constexpr (BF) {
             // four bf16 planes of 128 rows x 64 bytes (8 KB each) in buffer 0, 64-byte swizzle:
             // 16-byte unit u of row r sits at unit u ^ ((r >> 1) & 3)
