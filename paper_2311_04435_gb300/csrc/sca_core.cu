@@ -1615,6 +1615,226 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
+// ---------------------------------------------- refinement from the lower triangle
+// The symmetric dominant blocks leave X = A^{-1} in the tiles on or below the diagonal only.
+// The quadratic form of row i, q_i = Re(x^T A x) with x_j = X_ij (k_refine_direct's sum of
+// e_j = a_j Re x_j^2 - 2 w Re x_j Im x_j + 2t Re(x_j (x_{j+x} + x_{j+y}))), splits exactly into
+//   row part     : the site terms of j <= i and the bonds with both ends <= i (x_j = X[i][j]),
+//   column part  : the site terms of j > i and the bonds with both ends > i (x_j = X[j][i]),
+//   boundary     : the bonds with one end on each side: (i, i+1), (j, j+L) for i-L < j <= i, and
+//                  the periodic wraps (j, j+1-L) for i < j < i+L with y_j = L-1, (j, j+L-N) for
+//                  j >= N-L with j+L-N <= i (at most 2L+2 bonds, in double-float),
+// so every value comes from the lower triangle and no mirror pass is needed.  k_refine_lower_rows
+// sums the row part and the boundary (one warp per row, as k_refine_direct but with the columns
+// past i masked) into a double-float partial; k_refine_lower_cols streams each 32-column strip
+// down its rows for the column part, adds the partial in a fixed order and writes G_ii.
+constexpr int kLowerRowsPerCta = 64;
+
+// one bond term t2 Re(x_j x_k) in double-float
+__device__ __forceinline__ dsf bond_ds(float a, float b, float c, float d, dsf t2) {
+  return ds_mul(t2, ds_sub(two_prod(a, c), two_prod(b, d)));
+}
+
+__global__ void __launch_bounds__(256, 4)
+    k_refine_lower_rows(const float* __restrict__ M, int ldm, size_t mat_stride,
+                        size_t plane_stride, int b0, Lattice la0,
+                        const dsf* __restrict__ adiag_g, double* __restrict__ gd) {
+  extern __shared__ unsigned char smem_raw[];
+  dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
+  const int N = la0.N, L = la0.L;
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = adiag_g[(size_t)mat * N + r];
+  __syncthreads();
+  const float* re0 = M + mat * mat_stride;
+  const float* im0 = re0 + plane_stride;
+  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
+  const float small = 0x1.0p-18f / (float)N;
+  const int dxs = 32 / L, dys = 32 % L;
+  const int i_end = min(N, (int)(blockIdx.x + 1) * kLowerRowsPerCta);
+  for (int i = blockIdx.x * kLowerRowsPerCta + warp; i < i_end; i += 8) {
+    const float* re = re0 + (size_t)i * ldm;  // row i: X[i][j] for j <= i
+    const float* im = im0 + (size_t)i * ldm;
+    dsf acc = {0.f, 0.f};
+    float accf = 0.f;
+    int xx = lane / L, yy = lane - (lane / L) * L;
+    for (int j0 = 0; j0 <= i; j0 += 32 * kRefineUnroll) {  // warp-uniform trip count
+      float a[kRefineUnroll], bq[kRefineUnroll], ax[kRefineUnroll], bx[kRefineUnroll];
+      float ay[kRefineUnroll], by[kRefineUnroll];
+#pragma unroll
+      for (int u = 0; u < kRefineUnroll; ++u) {
+        const int j = j0 + 32 * u + lane;
+        const bool in = j <= i;
+        const int jx = (xx + 1 == L) ? yy : j + L;
+        const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
+        const bool inx = in && jx <= i, iny = in && jy <= i;  // bonds with both ends <= i
+        a[u] = in ? re[j] : 0.f;
+        bq[u] = in ? im[j] : 0.f;
+        ax[u] = inx ? re[jx] : 0.f;
+        bx[u] = inx ? im[jx] : 0.f;
+        ay[u] = iny ? re[jy] : 0.f;
+        by[u] = iny ? im[jy] : 0.f;
+        yy += dys;
+        xx += dxs;
+        if (yy >= L) { yy -= L; xx += 1; }
+      }
+#pragma unroll
+      for (int u = 0; u < kRefineUnroll; ++u) {
+        const int j = j0 + 32 * u + lane;
+        const dsf ad = j <= i ? adiag[j] : dsf{0.f, 0.f};
+        const float aa = fabsf(a[u]), ba = fabsf(bq[u]);
+        const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
+                         t2a * (aa * (fabsf(ax[u]) + fabsf(ay[u])) +
+                                ba * (fabsf(bx[u]) + fabsf(by[u])));
+        if (__any_sync(0xffffffffu, !(sj <= small))) {
+          const dsf q = ds_sub(two_prod(a[u], a[u]), two_prod(bq[u], bq[u]));
+          const dsf ab = two_prod(a[u], bq[u]);
+          const dsf uu = ds_add(ds_sub(two_prod(a[u], ax[u]), two_prod(bq[u], bx[u])),
+                                ds_sub(two_prod(a[u], ay[u]), two_prod(bq[u], by[u])));
+          const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, uu));
+          acc = ds_add(acc, e);
+        } else {
+          accf += ad.h * (a[u] * a[u] - bq[u] * bq[u]) - w2f * (a[u] * bq[u]) +
+                  t2f * (a[u] * (ax[u] + ay[u]) - bq[u] * (bx[u] + by[u]));
+        }
+      }
+    }
+    // boundary bonds: candidate t of 3L (t < L: (i-t, i-t+L); t == L: (i, i+1);
+    // L < t < 2L: (j, j+1-L) with j = i + t - L; t >= 2L: (j, j+L-N) with j = N - 3L + t,
+    // i.e. N - L <= j < N)
+    dsf accb = {0.f, 0.f};
+    for (int t = lane; t < 3 * L; t += 32) {
+      int jr = -1, kc = -1;  // the end <= i (row i) and the end > i (column i)
+      if (t < L) {
+        const int j = i - t;
+        if (j >= 0 && j / L != L - 1 && j + L > i) { jr = j; kc = j + L; }
+      } else if (t == L) {
+        if (i % L != L - 1 && i + 1 < N) { jr = i; kc = i + 1; }
+      } else if (t < 2 * L) {
+        const int j = i + t - L;
+        if (j < N && j % L == L - 1 && j + 1 - L <= i) { jr = j + 1 - L; kc = j; }
+      } else {
+        const int j = N - 3 * L + t;  // N - L .. N - 1
+        if (j > i && j + L - N <= i) { jr = j + L - N; kc = j; }
+      }
+      if (jr >= 0) {
+        const float ra = re[jr], rb = im[jr];
+        const float ca = re0[(size_t)kc * ldm + i], cb = im0[(size_t)kc * ldm + i];
+        accb = ds_add(accb, bond_ds(ra, rb, ca, cb, t2));
+      }
+    }
+    acc = ds_add(acc, dsf{accf, 0.f});
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const dsf o = {__shfl_xor_sync(0xffffffffu, acc.h, off),
+                     __shfl_xor_sync(0xffffffffu, acc.l, off)};
+      acc = ds_add(acc, o);
+      const dsf ob = {__shfl_xor_sync(0xffffffffu, accb.h, off),
+                      __shfl_xor_sync(0xffffffffu, accb.l, off)};
+      accb = ds_add(accb, ob);
+    }
+    if (lane == 0) {
+      const dsf r = ds_add(acc, accb);
+      gd[(size_t)b * N + i] = (double)r.h + (double)r.l;
+    }
+  }
+}
+
+// Column part of the refinement and the combine.  A CTA takes the 32 columns [i0, i0 + 32) of
+// one block (lane = column i) and its 8 warps split the rows below i0 into contiguous ranges;
+// row j contributes, for each column i < j, the site term of x_j = X[j][i] and its bonds to
+// the partners x_{j+x}, x_{j+y} that lie past i (X[j+x][i], X[j+y][i]: rows a few steps ahead,
+// served by L1).  Reads are 128-byte row segments of the lower triangle, each row of the strip
+// once from DRAM.  The 8 warp partials are added to the row part in warp order, so the result
+// does not depend on scheduling.  The row part arrives in gd as the exact float64 value of a
+// double-float pair (h + l needs at most 49 bits) and is read back into the pair exactly.
+constexpr int kColUnroll = 4;
+
+__global__ void __launch_bounds__(256, 4)
+    k_refine_lower_cols(const float* __restrict__ M, int ldm, size_t mat_stride,
+                        size_t plane_stride, int b0, Lattice la0,
+                        const dsf* __restrict__ adiag_g, double* __restrict__ gd) {
+  __shared__ dsf part[8][32];
+  const int N = la0.N, L = la0.L;
+  const int mat = blockIdx.y, b = b0 + mat;
+  int n, sg;
+  const Lattice la = block_lattice(la0, b, n, sg);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32, i = i0 + lane;
+  const float* re0 = M + mat * mat_stride;
+  const float* im0 = re0 + plane_stride;
+  const dsf* adiag = adiag_g + (size_t)mat * N;
+  const double w = (2.0 * n + 1.0) * kPi * la.T;
+  const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
+  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
+  const float small = 0x1.0p-18f / (float)N;
+  const int icol = min(i, N - 1);  // lanes past N read a valid column and are masked
+  // rows i0 + 1 .. N - 1, in 8 contiguous ranges
+  const int rows = max(0, N - 1 - i0);
+  const int per = (rows + 7) / 8;
+  const int jb = i0 + 1 + warp * per, je = min(N, jb + per);
+  dsf acc = {0.f, 0.f};
+  float accf = 0.f;
+  int xj = jb / L, yj = jb - (jb / L) * L;
+  for (int j0 = jb; j0 < je; j0 += kColUnroll) {  // warp-uniform trip count
+    float a[kColUnroll], bq[kColUnroll], ax[kColUnroll], bx[kColUnroll];
+    float ay[kColUnroll], by[kColUnroll];
+    int xs = xj, ys = yj;
+#pragma unroll
+    for (int u = 0; u < kColUnroll; ++u) {
+      const int j = j0 + u;
+      const bool in = j < je && j > i && i < N;
+      const int jx = (xs + 1 == L) ? ys : j + L;
+      const int jy = (ys + 1 == L) ? j + 1 - L : j + 1;
+      const bool inx = in && jx > i, iny = in && jy > i;  // bonds with both ends past i
+      a[u] = in ? re0[(size_t)j * ldm + icol] : 0.f;
+      bq[u] = in ? im0[(size_t)j * ldm + icol] : 0.f;
+      ax[u] = inx ? re0[(size_t)jx * ldm + icol] : 0.f;
+      bx[u] = inx ? im0[(size_t)jx * ldm + icol] : 0.f;
+      ay[u] = iny ? re0[(size_t)jy * ldm + icol] : 0.f;
+      by[u] = iny ? im0[(size_t)jy * ldm + icol] : 0.f;
+      if (++ys == L) { ys = 0; ++xs; }
+    }
+#pragma unroll
+    for (int u = 0; u < kColUnroll; ++u) {
+      const int j = j0 + u;
+      const dsf ad = j < je ? adiag[j] : dsf{0.f, 0.f};
+      const float aa = fabsf(a[u]), ba = fabsf(bq[u]);
+      const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
+                       t2a * (aa * (fabsf(ax[u]) + fabsf(ay[u])) +
+                              ba * (fabsf(bx[u]) + fabsf(by[u])));
+      if (__any_sync(0xffffffffu, !(sj <= small))) {
+        const dsf q = ds_sub(two_prod(a[u], a[u]), two_prod(bq[u], bq[u]));
+        const dsf ab = two_prod(a[u], bq[u]);
+        const dsf uu = ds_add(ds_sub(two_prod(a[u], ax[u]), two_prod(bq[u], bx[u])),
+                              ds_sub(two_prod(a[u], ay[u]), two_prod(bq[u], by[u])));
+        const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, uu));
+        acc = ds_add(acc, e);
+      } else {
+        accf += ad.h * (a[u] * a[u] - bq[u] * bq[u]) - w2f * (a[u] * bq[u]) +
+                t2f * (a[u] * (ax[u] + ay[u]) - bq[u] * (bx[u] + by[u]));
+      }
+    }
+    xj = xs;
+    yj = ys;
+  }
+  part[warp][lane] = ds_add(acc, dsf{accf, 0.f});
+  __syncthreads();
+  if (warp == 0 && i < N) {
+    const double r = gd[(size_t)b * N + i];
+    const float rh = (float)r;
+    dsf tot = {rh, (float)(r - (double)rh)};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot = ds_add(tot, part[k][lane]);
+    const double qsum = (double)tot.h + (double)tot.l;
+    gd[(size_t)b * N + i] = sg * (2.0 * (double)re0[(size_t)i * ldm + i] - qsum);
+  }
+}
+
 // Im Tr G per block for the density of states: X_ii = R[i, sperm[i]] (sperm the inverse of
 // the column permutation of the pivoted elimination), summed in float64 in a fixed order.
 template <typename S>
@@ -1784,8 +2004,22 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
     if (err__ != cudaSuccess) return cuda_fail(err__, where);     \
   } while (0)
 
+// The dominant blocks on the tensor cores are inverted in their lower tiles only.  With the
+// float32 refinement on, diag(G) is read from those tiles (k_refine_lower_rows/_cols) and the
+// upper tiles are never filled; otherwise k_mirror copies the lower triangle up and the row
+// kernels read whole rows.
+bool lower_refine(const Engine& e) {
+  if (!e.refine || e.fp64 || !e.tc || e.tt == nullptr) return false;
+  if (const char* v = std::getenv("SCA_SYM"))
+    if (std::atoi(v) == 0) return false;
+  if (const char* v = std::getenv("SCA_REFINE_LOWER"))
+    if (std::atoi(v) == 0) return false;
+  return true;
+}
+
 // diag(G) of the workspace slots m0 .. m0+cnt-1 (global blocks b0 + m0 ..): pivoted blocks
-// through the permutation (k_refine), unpivoted ones by the direct kernel.
+// through the permutation (k_refine), unpivoted ones by the direct kernel or, for blocks held
+// as a lower triangle, by the row and column parts.
 template <typename S>
 sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, cudaStream_t s) {
   if (cnt <= 0) return SCA_OK;
@@ -1815,10 +2049,20 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, 
       dsf* tab = reinterpret_cast<dsf*>(e.adiag) + (size_t)(m0 + np) * N;
       k_adiag<<<dim3((N + 255) / 256, cnt - np), 256, 0, s>>>(la, bg + np, tab);
       SCA_LAUNCH_CHECK("diagonal table");
-      k_refine_direct<<<dim3(gx, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
-          reinterpret_cast<const float*>(M) + (size_t)np * e.mat_stride, e.ldm, e.mat_stride,
-          e.plane_stride, bg + np, la, tab, e.gd);
-      SCA_LAUNCH_CHECK("refine direct");
+      const float* Md = reinterpret_cast<const float*>(M) + (size_t)np * e.mat_stride;
+      if (lower_refine(e)) {
+        const int gr = (N + kLowerRowsPerCta - 1) / kLowerRowsPerCta;
+        k_refine_lower_rows<<<dim3(gr, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
+            Md, e.ldm, e.mat_stride, e.plane_stride, bg + np, la, tab, e.gd);
+        SCA_LAUNCH_CHECK("refine rows");
+        k_refine_lower_cols<<<dim3((N + 31) / 32, cnt - np), 256, 0, s>>>(
+            Md, e.ldm, e.mat_stride, e.plane_stride, bg + np, la, tab, e.gd);
+        SCA_LAUNCH_CHECK("refine columns");
+      } else {
+        k_refine_direct<<<dim3(gx, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
+            Md, e.ldm, e.mat_stride, e.plane_stride, bg + np, la, tab, e.gd);
+        SCA_LAUNCH_CHECK("refine direct");
+      }
     }
   } else {
     const int gx = std::max(1, std::min((N + 255) / 256, 16));
@@ -2146,7 +2390,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
     const cudaError_t err = switch_to(false);
     if (err != cudaSuccess) return cuda_fail(err, "partition switch");
   }
-  if (sym && want_grad) {  // the fully swept inverse is symmetric: fill the upper tiles
+  if (sym && want_grad && !lower_refine(e)) {  // symmetric inverse: fill the upper tiles
     const int nt = (N + 31) / 32;
     prof_begin(e, kPrep, s);
     k_mirror<S><<<dim3(nt * (nt + 1) / 2, cnt), 256, 0, s>>>(M, N, e.ldm, e.mat_stride,

@@ -327,6 +327,32 @@ def test_symmetric_update_matches_full_update(monkeypatch):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("L,nw", [(6, 12), (20, 10), (34, 6)])
+def test_lower_triangle_refinement_matches_mirrored_rows(L, nw, prec, monkeypatch):
+    """diag(G) of the symmetric dominant blocks refined straight from the lower triangle (row
+    part, boundary bonds, column part) equals the refinement of whole rows after the mirror
+    pass up to summation order, and both match the oracle.  N = 36, 400 and 1156 span one to
+    ten 128-wide tiles and 2 to 37 column strips, each with a ragged end; at L = 6 and 34 the
+    lattice rows (and so the periodic wraps) fall off the 32-column strip boundaries."""
+    monkeypatch.setenv("SCA_FUSED", "0")
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=1.0, prec=prec)
+    phi = inputs.seed_phi(11, p.N)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCA_REFINE_LOWER", flag)
+        with api.Context(p) as c:
+            res[flag] = c.blocks(phi, grad=True)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    for ld, gd in res.values():
+        assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+        assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+    assert np.array_equal(res["1"][0], res["0"][0])
+    scale = np.maximum(1.0, np.abs(res["0"][1]))
+    assert np.max(np.abs(res["1"][1] - res["0"][1]) / scale) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
 def test_tensor_core_pivot_block_inverse_matches_register_kernel(prec, monkeypatch):
     """The dominant pivot-block inverse on the tensor cores (tableau in TMEM, split-TF32
     rank-16 updates) and the register Gauss-Jordan kernel give log-dets, diag(G), Omega and the
