@@ -1617,98 +1617,179 @@ __global__ void __launch_bounds__(256, 4)
 
 // ---------------------------------------------- refinement from the lower triangle
 // The symmetric dominant blocks leave X = A^{-1} in the tiles on or below the diagonal only.
-// The quadratic form of row i, q_i = Re(x^T A x) with x_j = X_ij (k_refine_direct's sum of
-// e_j = a_j Re x_j^2 - 2 w Re x_j Im x_j + 2t Re(x_j (x_{j+x} + x_{j+y}))), splits exactly into
+// The quadratic form of row i, q_i = Re(x^T A x) with x_j = X_ij, is a sum over sites j of
+//   e_j = a_j Re x_j^2 - 2 w Re x_j Im x_j + 2t Re(x_j (x_{j+x} + x_{j+y}))
+// (a_j = Re A_jj, bonds to the +x and +y neighbours), which splits exactly into
 //   row part     : the site terms of j <= i and the bonds with both ends <= i (x_j = X[i][j]),
 //   column part  : the site terms of j > i and the bonds with both ends > i (x_j = X[j][i]),
 //   boundary     : the bonds with one end on each side: (i, i+1), (j, j+L) for i-L < j <= i, and
 //                  the periodic wraps (j, j+1-L) for i < j < i+L with y_j = L-1, (j, j+L-N) for
 //                  j >= N-L with j+L-N <= i (at most 2L+2 bonds, in double-float),
 // so every value comes from the lower triangle and no mirror pass is needed.  k_refine_lower_rows
-// sums the row part and the boundary (one warp per row, as k_refine_direct but with the columns
-// past i masked) into a double-float partial; k_refine_lower_cols streams each 32-column strip
-// down its rows for the column part, adds the partial in a fixed order and writes G_ii.
+// sums the row part and the boundary (one warp per row) into a double-float partial;
+// k_refine_lower_cols streams each 64-column strip down its rows for the column part, adds the
+// partial in a fixed order and writes G_ii.
+//
+// Both kernels take two adjacent entries per lane (8-byte loads; L and N are even, so a pair
+// never straddles a lattice row in the row kernel and the +x partners form a pair too) and
+// vote per group of 64 entries on m = the largest |Re|, |Im| among the entries and their bond
+// partners.  Every term satisfies |e_j| <= C m^2 with C = 2 max|a_j| + 2w + 4|2t|, so a group
+// with m^2 <= small / C (small = 2^-18 / N, the bound of k_refine_direct) is summed in float32
+// within the same 2^-39 total error; any other group takes the double-float path.  There the
+// exact products (two_prod) go into three compensated sums (the terms a_j Re x_j^2, the Re x Im x
+// products and the bond products; each a float32 sum and the float32 sum of the rounding errors
+// of its additions), scaled by -2w and 2t once per row.
 constexpr int kLowerRowsPerCta = 64;
+constexpr int kLowerUnroll = 2;  // 64-entry groups per round of loads
 
-// one bond term t2 Re(x_j x_k) in double-float
-__device__ __forceinline__ dsf bond_ds(float a, float b, float c, float d, dsf t2) {
-  return ds_mul(t2, ds_sub(two_prod(a, c), two_prod(b, d)));
+// compensated float32 sum of exact products: s the running sum, e the rounding errors of its
+// additions plus the products' low parts
+struct csum {
+  float s, e;
+};
+__device__ __forceinline__ void csum_add(csum& c, dsf p) {
+  const dsf t = two_sum(c.s, p.h);
+  c.s = t.h;
+  c.e += t.l + p.l;
+}
+__device__ __forceinline__ dsf csum_val(csum c) { return fast_two_sum(c.s, c.e); }
+
+// the double-float terms of one site: a_j Re x^2 into s1, Re x Im x into s2, the two bond
+// products Re(x x_x) + Re(x x_y) into s3
+__device__ __forceinline__ void site_terms_ds(float a, float b, float ax, float bx, float ay,
+                                              float by, dsf ad, csum& s1, csum& s2, csum& s3) {
+  csum_add(s1, ds_mul(ad, ds_sub(two_prod(a, a), two_prod(b, b))));
+  csum_add(s2, two_prod(a, b));
+  csum_add(s3, two_prod(a, ax));
+  csum_add(s3, two_prod(-b, bx));
+  csum_add(s3, two_prod(a, ay));
+  csum_add(s3, two_prod(-b, by));
 }
 
+// the same terms in float32 (f1: a_j Re x^2, f2: Re x Im x, f3: bond products)
+__device__ __forceinline__ void site_terms_f(float a, float b, float ax, float bx, float ay,
+                                             float by, float adh, float& f1, float& f2,
+                                             float& f3) {
+  f1 = fmaf(adh, fmaf(a, a, -b * b), f1);
+  f2 = fmaf(a, b, f2);
+  f3 = fmaf(a, ax + ay, f3);
+  f3 = fmaf(-b, bx + by, f3);
+}
+
+// one lane's total: S1 - 2w S2 + 2t S3 plus the float32 parts
+__device__ __forceinline__ dsf lane_total(csum s1, csum s2, csum s3, float f1, float f2,
+                                          float f3, dsf w2, dsf t2) {
+  dsf r = ds_sub(csum_val(s1), ds_mul(w2, csum_val(s2)));
+  r = ds_add(r, ds_mul(t2, csum_val(s3)));
+  return ds_add(r, two_sum(f1, fmaf(-w2.h, f2, t2.h * f3)));
+}
+
+// stage the block's Re A_jj table in shared memory and return m^2's threshold small / C
+__device__ __forceinline__ float stage_adiag(const dsf* __restrict__ adiag_g, dsf* adiag, int N,
+                                             float w2a, float t2a, float* red) {
+  float amax = 0.f;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const dsf v = adiag_g[r];
+    adiag[r] = v;
+    amax = fmaxf(amax, fabsf(v.h));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  amax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmaxf(amax, red[w]);
+  // C rounded up by a relative 2^-20 (|a_j| carries its low part, w and t their roundings)
+  const float C = (2.f * amax + w2a + 4.f * t2a) * (1.f + 0x1.0p-20f);
+  return (0x1.0p-18f / (float)N) / C;
+}
+
+// Row part and boundary bonds, one warp per row i.  Round r covers the sites j0 .. j0 + 127 as
+// two groups of 64, lane l taking the pair (p, p + 1), p = j0 + 64 u + 2 l: y_p is even, so p + 1
+// is p's +y partner (no wrap) and p's +x partner jx is even with jx + 1 the +x partner of p + 1;
+// only p + 1's +y partner (p + 2, or p + 2 - L on a wrap) is loaded on its own.  Masks are
+// applied only in the rounds that reach past site i - L.
 __global__ void __launch_bounds__(256, 4)
     k_refine_lower_rows(const float* __restrict__ M, int ldm, size_t mat_stride,
                         size_t plane_stride, int b0, Lattice la0,
                         const dsf* __restrict__ adiag_g, double* __restrict__ gd) {
   extern __shared__ unsigned char smem_raw[];
   dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
+  __shared__ float red[8];
   const int N = la0.N, L = la0.L;
   const int mat = blockIdx.y, b = b0 + mat;
   int n, sg;
   const Lattice la = block_lattice(la0, b, n, sg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = threadIdx.x; r < N; r += blockDim.x) adiag[r] = adiag_g[(size_t)mat * N + r];
-  __syncthreads();
   const float* re0 = M + mat * mat_stride;
   const float* im0 = re0 + plane_stride;
   const double w = (2.0 * n + 1.0) * kPi * la.T;
   const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
-  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
-  const float small = 0x1.0p-18f / (float)N;
-  const int dxs = 32 / L, dys = 32 % L;
+  const float thr2 = stage_adiag(adiag_g + (size_t)mat * N, adiag, N, fabsf(w2.h), fabsf(t2.h), red);
+  const int dx64 = 64 / L, dy64 = 64 % L;
   const int i_end = min(N, (int)(blockIdx.x + 1) * kLowerRowsPerCta);
   for (int i = blockIdx.x * kLowerRowsPerCta + warp; i < i_end; i += 8) {
     const float* re = re0 + (size_t)i * ldm;  // row i: X[i][j] for j <= i
     const float* im = im0 + (size_t)i * ldm;
-    dsf acc = {0.f, 0.f};
-    float accf = 0.f;
-    int xx = lane / L, yy = lane - (lane / L) * L;
-    for (int j0 = 0; j0 <= i; j0 += 32 * kRefineUnroll) {  // warp-uniform trip count
-      float a[kRefineUnroll], bq[kRefineUnroll], ax[kRefineUnroll], bx[kRefineUnroll];
-      float ay[kRefineUnroll], by[kRefineUnroll];
+    csum s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
+    float f1 = 0.f, f2 = 0.f, f3 = 0.f;
+    int xx = (2 * lane) / L, yy = (2 * lane) - ((2 * lane) / L) * L;
+    for (int j0 = 0; j0 <= i; j0 += 64 * kLowerUnroll) {  // warp-uniform trip count
+      const bool full = j0 + 64 * kLowerUnroll + L <= i;  // every entry and partner <= i
+      float2 a[kLowerUnroll], bq[kLowerUnroll], ax[kLowerUnroll], bx[kLowerUnroll];
+      float ay[kLowerUnroll], by[kLowerUnroll];
 #pragma unroll
-      for (int u = 0; u < kRefineUnroll; ++u) {
-        const int j = j0 + 32 * u + lane;
-        const bool in = j <= i;
-        const int jx = (xx + 1 == L) ? yy : j + L;
-        const int jy = (yy + 1 == L) ? j + 1 - L : j + 1;
-        const bool inx = in && jx <= i, iny = in && jy <= i;  // bonds with both ends <= i
-        a[u] = in ? re[j] : 0.f;
-        bq[u] = in ? im[j] : 0.f;
-        ax[u] = inx ? re[jx] : 0.f;
-        bx[u] = inx ? im[jx] : 0.f;
-        ay[u] = iny ? re[jy] : 0.f;
-        by[u] = iny ? im[jy] : 0.f;
-        yy += dys;
-        xx += dxs;
+      for (int u = 0; u < kLowerUnroll; ++u) {
+        const int p = j0 + 64 * u + 2 * lane;
+        const int jx = (xx + 1 == L) ? yy : p + L;
+        const int jy = (yy + 2 == L) ? p + 2 - L : p + 2;
+        if (full) {
+          a[u] = *reinterpret_cast<const float2*>(re + p);
+          bq[u] = *reinterpret_cast<const float2*>(im + p);
+          ax[u] = *reinterpret_cast<const float2*>(re + jx);
+          bx[u] = *reinterpret_cast<const float2*>(im + jx);
+          ay[u] = re[jy];
+          by[u] = im[jy];
+        } else {
+          const bool in0 = p <= i, in1 = p + 1 <= i;
+          const bool inx0 = in0 && jx <= i, inx1 = in1 && jx + 1 <= i, iny1 = in1 && jy <= i;
+          const float2 z = make_float2(0.f, 0.f);
+          a[u] = in0 ? *reinterpret_cast<const float2*>(re + p) : z;
+          bq[u] = in0 ? *reinterpret_cast<const float2*>(im + p) : z;
+          ax[u] = inx0 ? *reinterpret_cast<const float2*>(re + jx) : z;
+          bx[u] = inx0 ? *reinterpret_cast<const float2*>(im + jx) : z;
+          ay[u] = iny1 ? re[jy] : 0.f;
+          by[u] = iny1 ? im[jy] : 0.f;
+          if (!in1) { a[u].y = 0.f; bq[u].y = 0.f; }
+          if (!inx1) { ax[u].y = 0.f; bx[u].y = 0.f; }
+        }
+        yy += dy64;
+        xx += dx64;
         if (yy >= L) { yy -= L; xx += 1; }
       }
 #pragma unroll
-      for (int u = 0; u < kRefineUnroll; ++u) {
-        const int j = j0 + 32 * u + lane;
-        const dsf ad = j <= i ? adiag[j] : dsf{0.f, 0.f};
-        const float aa = fabsf(a[u]), ba = fabsf(bq[u]);
-        const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
-                         t2a * (aa * (fabsf(ax[u]) + fabsf(ay[u])) +
-                                ba * (fabsf(bx[u]) + fabsf(by[u])));
-        if (__any_sync(0xffffffffu, !(sj <= small))) {
-          const dsf q = ds_sub(two_prod(a[u], a[u]), two_prod(bq[u], bq[u]));
-          const dsf ab = two_prod(a[u], bq[u]);
-          const dsf uu = ds_add(ds_sub(two_prod(a[u], ax[u]), two_prod(bq[u], bx[u])),
-                                ds_sub(two_prod(a[u], ay[u]), two_prod(bq[u], by[u])));
-          const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, uu));
-          acc = ds_add(acc, e);
+      for (int u = 0; u < kLowerUnroll; ++u) {
+        const int pc = min(j0 + 64 * u + 2 * lane, N - 2);  // masked lanes read a valid entry
+        const dsf ad0 = adiag[pc], ad1 = adiag[pc + 1];
+        const float m = fmaxf(fmaxf(fmaxf(fabsf(a[u].x), fabsf(a[u].y)),
+                                    fmaxf(fabsf(bq[u].x), fabsf(bq[u].y))),
+                              fmaxf(fmaxf(fmaxf(fabsf(ax[u].x), fabsf(ax[u].y)),
+                                          fmaxf(fabsf(bx[u].x), fabsf(bx[u].y))),
+                                    fmaxf(fabsf(ay[u]), fabsf(by[u]))));
+        if (__any_sync(0xffffffffu, !(m * m <= thr2))) {
+          site_terms_ds(a[u].x, bq[u].x, ax[u].x, bx[u].x, a[u].y, bq[u].y, ad0, s1, s2, s3);
+          site_terms_ds(a[u].y, bq[u].y, ax[u].y, bx[u].y, ay[u], by[u], ad1, s1, s2, s3);
         } else {
-          accf += ad.h * (a[u] * a[u] - bq[u] * bq[u]) - w2f * (a[u] * bq[u]) +
-                  t2f * (a[u] * (ax[u] + ay[u]) - bq[u] * (bx[u] + by[u]));
+          site_terms_f(a[u].x, bq[u].x, ax[u].x, bx[u].x, a[u].y, bq[u].y, ad0.h, f1, f2, f3);
+          site_terms_f(a[u].y, bq[u].y, ax[u].y, bx[u].y, ay[u], by[u], ad1.h, f1, f2, f3);
         }
       }
     }
-    // boundary bonds: candidate t of 3L (t < L: (i-t, i-t+L); t == L: (i, i+1);
-    // L < t < 2L: (j, j+1-L) with j = i + t - L; t >= 2L: (j, j+L-N) with j = N - 3L + t,
-    // i.e. N - L <= j < N)
-    dsf accb = {0.f, 0.f};
+    // boundary bonds into the bond sum: candidate t of 3L (t < L: (i-t, i-t+L); t == L:
+    // (i, i+1); L < t < 2L: (j, j+1-L) with j = i + t - L; t >= 2L: (j, j+L-N) with
+    // j = N - 3L + t, i.e. N - L <= j < N); the end <= i from row i, the other from column i
     for (int t = lane; t < 3 * L; t += 32) {
-      int jr = -1, kc = -1;  // the end <= i (row i) and the end > i (column i)
+      int jr = -1, kc = -1;
       if (t < L) {
         const int j = i - t;
         if (j >= 0 && j / L != L - 1 && j + L > i) { jr = j; kc = j + L; }
@@ -1718,122 +1799,123 @@ __global__ void __launch_bounds__(256, 4)
         const int j = i + t - L;
         if (j < N && j % L == L - 1 && j + 1 - L <= i) { jr = j + 1 - L; kc = j; }
       } else {
-        const int j = N - 3 * L + t;  // N - L .. N - 1
+        const int j = N - 3 * L + t;
         if (j > i && j + L - N <= i) { jr = j + L - N; kc = j; }
       }
       if (jr >= 0) {
         const float ra = re[jr], rb = im[jr];
         const float ca = re0[(size_t)kc * ldm + i], cb = im0[(size_t)kc * ldm + i];
-        accb = ds_add(accb, bond_ds(ra, rb, ca, cb, t2));
+        csum_add(s3, two_prod(ra, ca));
+        csum_add(s3, two_prod(-rb, cb));
       }
     }
-    acc = ds_add(acc, dsf{accf, 0.f});
+    dsf tl = lane_total(s1, s2, s3, f1, f2, f3, w2, t2);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const dsf o = {__shfl_xor_sync(0xffffffffu, acc.h, off),
-                     __shfl_xor_sync(0xffffffffu, acc.l, off)};
-      acc = ds_add(acc, o);
-      const dsf ob = {__shfl_xor_sync(0xffffffffu, accb.h, off),
-                      __shfl_xor_sync(0xffffffffu, accb.l, off)};
-      accb = ds_add(accb, ob);
+      const dsf o = {__shfl_xor_sync(0xffffffffu, tl.h, off),
+                     __shfl_xor_sync(0xffffffffu, tl.l, off)};
+      tl = ds_add(tl, o);
     }
-    if (lane == 0) {
-      const dsf r = ds_add(acc, accb);
-      gd[(size_t)b * N + i] = (double)r.h + (double)r.l;
-    }
+    if (lane == 0) gd[(size_t)b * N + i] = (double)tl.h + (double)tl.l;
   }
 }
 
-// Column part of the refinement and the combine.  A CTA takes the 32 columns [i0, i0 + 32) of
-// one block (lane = column i) and its 8 warps split the rows below i0 into contiguous ranges;
-// row j contributes, for each column i < j, the site term of x_j = X[j][i] and its bonds to
-// the partners x_{j+x}, x_{j+y} that lie past i (X[j+x][i], X[j+y][i]: rows a few steps ahead,
-// served by L1).  Reads are 128-byte row segments of the lower triangle, each row of the strip
-// once from DRAM.  The 8 warp partials are added to the row part in warp order, so the result
-// does not depend on scheduling.  The row part arrives in gd as the exact float64 value of a
-// double-float pair (h + l needs at most 49 bits) and is read back into the pair exactly.
-constexpr int kColUnroll = 4;
+// Column part of the refinement and the combine.  A CTA takes the 64 columns [i0, i0 + 64) of
+// one block (lane = the column pair c, c + 1 with c = i0 + 2 lane) and its 8 warps take the
+// rows below i0 in turn (warp w the rows i0 + 1 + w + 8k); row j contributes, for each column
+// c < j, the site term of x_j = X[j][c] and its bonds to the partners x_{j+x}, x_{j+y} that lie
+// past c (X[j+x][c], X[j+y][c]).  The CTA sweeps down its strip together, so the partner rows,
+// at most L rows ahead, are still in L1 when their own warp reaches them: 256-byte row segments
+// of the lower triangle, each read once from DRAM.  The 8 warp partials are added to the
+// row part in warp order, so the result does not depend on scheduling.  The row part arrives in
+// gd as the float64 value of a double-float pair and is split back into one.
+constexpr int kColUnroll = 2;
 
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
     k_refine_lower_cols(const float* __restrict__ M, int ldm, size_t mat_stride,
                         size_t plane_stride, int b0, Lattice la0,
                         const dsf* __restrict__ adiag_g, double* __restrict__ gd) {
-  __shared__ dsf part[8][32];
+  extern __shared__ unsigned char smem_raw[];
+  dsf* adiag = reinterpret_cast<dsf*>(smem_raw);
+  __shared__ float red[8];
+  __shared__ dsf part[8][64];
   const int N = la0.N, L = la0.L;
   const int mat = blockIdx.y, b = b0 + mat;
   int n, sg;
   const Lattice la = block_lattice(la0, b, n, sg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * 32, i = i0 + lane;
+  const int i0 = blockIdx.x * 64, c = i0 + 2 * lane;
   const float* re0 = M + mat * mat_stride;
   const float* im0 = re0 + plane_stride;
-  const dsf* adiag = adiag_g + (size_t)mat * N;
   const double w = (2.0 * n + 1.0) * kPi * la.T;
   const dsf w2 = ds_of(2.0 * w), t2 = ds_of(2.0 * la.t);
-  const float w2f = w2.h, t2f = t2.h, w2a = fabsf(w2.h), t2a = fabsf(t2.h);
-  const float small = 0x1.0p-18f / (float)N;
-  const int icol = min(i, N - 1);  // lanes past N read a valid column and are masked
-  // rows i0 + 1 .. N - 1, in 8 contiguous ranges
-  const int rows = max(0, N - 1 - i0);
-  const int per = (rows + 7) / 8;
-  const int jb = i0 + 1 + warp * per, je = min(N, jb + per);
-  dsf acc = {0.f, 0.f};
-  float accf = 0.f;
+  const float thr2 = stage_adiag(adiag_g + (size_t)mat * N, adiag, N, fabsf(w2.h), fabsf(t2.h), red);
+  const int cc = min(c, N - 2);  // lanes past N read a valid column pair and are masked
+  // rows i0 + 1 + warp + 8k below the strip
+  const int jb = i0 + 1 + warp;
+  const int dx8 = 8 / L, dy8 = 8 % L;
+  csum s1[2] = {}, s2[2] = {}, s3[2] = {};
+  float f1[2] = {0.f, 0.f}, f2[2] = {0.f, 0.f}, f3[2] = {0.f, 0.f};
   int xj = jb / L, yj = jb - (jb / L) * L;
-  for (int j0 = jb; j0 < je; j0 += kColUnroll) {  // warp-uniform trip count
-    float a[kColUnroll], bq[kColUnroll], ax[kColUnroll], bx[kColUnroll];
-    float ay[kColUnroll], by[kColUnroll];
-    int xs = xj, ys = yj;
+  for (int j0 = jb; j0 < N; j0 += 8 * kColUnroll) {  // warp-uniform trip count
+    float2 a[kColUnroll], bq[kColUnroll], ax[kColUnroll], bx[kColUnroll];
+    float2 ay[kColUnroll], by[kColUnroll];
 #pragma unroll
     for (int u = 0; u < kColUnroll; ++u) {
-      const int j = j0 + u;
-      const bool in = j < je && j > i && i < N;
-      const int jx = (xs + 1 == L) ? ys : j + L;
-      const int jy = (ys + 1 == L) ? j + 1 - L : j + 1;
-      const bool inx = in && jx > i, iny = in && jy > i;  // bonds with both ends past i
-      a[u] = in ? re0[(size_t)j * ldm + icol] : 0.f;
-      bq[u] = in ? im0[(size_t)j * ldm + icol] : 0.f;
-      ax[u] = inx ? re0[(size_t)jx * ldm + icol] : 0.f;
-      bx[u] = inx ? im0[(size_t)jx * ldm + icol] : 0.f;
-      ay[u] = iny ? re0[(size_t)jy * ldm + icol] : 0.f;
-      by[u] = iny ? im0[(size_t)jy * ldm + icol] : 0.f;
-      if (++ys == L) { ys = 0; ++xs; }
+      const int j = j0 + 8 * u;
+      const int jx = (xj + 1 == L) ? yj : j + L;
+      const int jy = (yj + 1 == L) ? j + 1 - L : j + 1;
+      const bool row = j < N;
+      const bool in0 = row && j > c, in1 = row && j > c + 1;
+      const bool inx0 = in0 && jx > c, inx1 = in1 && jx > c + 1;
+      const bool iny0 = in0 && jy > c, iny1 = in1 && jy > c + 1;
+      const float2 z = make_float2(0.f, 0.f);
+      a[u] = in0 ? *reinterpret_cast<const float2*>(re0 + (size_t)j * ldm + cc) : z;
+      bq[u] = in0 ? *reinterpret_cast<const float2*>(im0 + (size_t)j * ldm + cc) : z;
+      ax[u] = inx0 ? *reinterpret_cast<const float2*>(re0 + (size_t)jx * ldm + cc) : z;
+      bx[u] = inx0 ? *reinterpret_cast<const float2*>(im0 + (size_t)jx * ldm + cc) : z;
+      ay[u] = iny0 ? *reinterpret_cast<const float2*>(re0 + (size_t)jy * ldm + cc) : z;
+      by[u] = iny0 ? *reinterpret_cast<const float2*>(im0 + (size_t)jy * ldm + cc) : z;
+      if (!in1) { a[u].y = 0.f; bq[u].y = 0.f; }
+      if (!inx1) { ax[u].y = 0.f; bx[u].y = 0.f; }
+      if (!iny1) { ay[u].y = 0.f; by[u].y = 0.f; }
+      yj += dy8;
+      xj += dx8;
+      if (yj >= L) { yj -= L; ++xj; }
     }
 #pragma unroll
     for (int u = 0; u < kColUnroll; ++u) {
-      const int j = j0 + u;
-      const dsf ad = j < je ? adiag[j] : dsf{0.f, 0.f};
-      const float aa = fabsf(a[u]), ba = fabsf(bq[u]);
-      const float sj = fabsf(ad.h) * (aa * aa + ba * ba) + w2a * (aa * ba) +
-                       t2a * (aa * (fabsf(ax[u]) + fabsf(ay[u])) +
-                              ba * (fabsf(bx[u]) + fabsf(by[u])));
-      if (__any_sync(0xffffffffu, !(sj <= small))) {
-        const dsf q = ds_sub(two_prod(a[u], a[u]), two_prod(bq[u], bq[u]));
-        const dsf ab = two_prod(a[u], bq[u]);
-        const dsf uu = ds_add(ds_sub(two_prod(a[u], ax[u]), two_prod(bq[u], bx[u])),
-                              ds_sub(two_prod(a[u], ay[u]), two_prod(bq[u], by[u])));
-        const dsf e = ds_add(ds_sub(ds_mul(ad, q), ds_mul(w2, ab)), ds_mul(t2, uu));
-        acc = ds_add(acc, e);
+      const dsf ad = adiag[min(j0 + 8 * u, N - 1)];
+      const float m = fmaxf(fmaxf(fmaxf(fmaxf(fabsf(a[u].x), fabsf(a[u].y)),
+                                        fmaxf(fabsf(bq[u].x), fabsf(bq[u].y))),
+                                  fmaxf(fmaxf(fabsf(ax[u].x), fabsf(ax[u].y)),
+                                        fmaxf(fabsf(bx[u].x), fabsf(bx[u].y)))),
+                            fmaxf(fmaxf(fabsf(ay[u].x), fabsf(ay[u].y)),
+                                  fmaxf(fabsf(by[u].x), fabsf(by[u].y))));
+      if (__any_sync(0xffffffffu, !(m * m <= thr2))) {
+        site_terms_ds(a[u].x, bq[u].x, ax[u].x, bx[u].x, ay[u].x, by[u].x, ad, s1[0], s2[0], s3[0]);
+        site_terms_ds(a[u].y, bq[u].y, ax[u].y, bx[u].y, ay[u].y, by[u].y, ad, s1[1], s2[1], s3[1]);
       } else {
-        accf += ad.h * (a[u] * a[u] - bq[u] * bq[u]) - w2f * (a[u] * bq[u]) +
-                t2f * (a[u] * (ax[u] + ay[u]) - bq[u] * (bx[u] + by[u]));
+        site_terms_f(a[u].x, bq[u].x, ax[u].x, bx[u].x, ay[u].x, by[u].x, ad.h, f1[0], f2[0], f3[0]);
+        site_terms_f(a[u].y, bq[u].y, ax[u].y, bx[u].y, ay[u].y, by[u].y, ad.h, f1[1], f2[1], f3[1]);
       }
     }
-    xj = xs;
-    yj = ys;
   }
-  part[warp][lane] = ds_add(acc, dsf{accf, 0.f});
+  part[warp][2 * lane] = lane_total(s1[0], s2[0], s3[0], f1[0], f2[0], f3[0], w2, t2);
+  part[warp][2 * lane + 1] = lane_total(s1[1], s2[1], s3[1], f1[1], f2[1], f3[1], w2, t2);
   __syncthreads();
-  if (warp == 0 && i < N) {
-    const double r = gd[(size_t)b * N + i];
+  const int ic = i0 + (int)threadIdx.x;
+  if (threadIdx.x < 64 && ic < N) {
+    const double r = gd[(size_t)b * N + ic];
     const float rh = (float)r;
     dsf tot = {rh, (float)(r - (double)rh)};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) tot = ds_add(tot, part[k][lane]);
+    for (int k = 0; k < 8; ++k) tot = ds_add(tot, part[k][threadIdx.x]);
     const double qsum = (double)tot.h + (double)tot.l;
-    gd[(size_t)b * N + i] = sg * (2.0 * (double)re0[(size_t)i * ldm + i] - qsum);
+    gd[(size_t)b * N + ic] = sg * (2.0 * (double)re0[(size_t)ic * ldm + ic] - qsum);
   }
 }
+
 
 // Im Tr G per block for the density of states: X_ii = R[i, sperm[i]] (sperm the inverse of
 // the column permutation of the pivoted elimination), summed in float64 in a fixed order.
@@ -2055,7 +2137,7 @@ sca_status launch_refine(Engine& e, const Lattice& la, int b0, int m0, int cnt, 
         k_refine_lower_rows<<<dim3(gr, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
             Md, e.ldm, e.mat_stride, e.plane_stride, bg + np, la, tab, e.gd);
         SCA_LAUNCH_CHECK("refine rows");
-        k_refine_lower_cols<<<dim3((N + 31) / 32, cnt - np), 256, 0, s>>>(
+        k_refine_lower_cols<<<dim3((N + 63) / 64, cnt - np), 256, (size_t)N * sizeof(dsf), s>>>(
             Md, e.ldm, e.mat_stride, e.plane_stride, bg + np, la, tab, e.gd);
         SCA_LAUNCH_CHECK("refine columns");
       } else {
