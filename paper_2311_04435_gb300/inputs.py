@@ -101,6 +101,10 @@ WORKLOADS = {
     # -> 16 blocks of 1600x1600 (328 MB, above the L2), all diagonally dominant (w_0 > 4t)
     "ionic_40x40_w8": Workload("ionic_40x40_w8", 40, 4.0, 1.0, 1.5, 8,
                                note="16 complex 1600x1600 blocks, none pivoted"),
+    # profiling case of the refinement: the 40x40 workload cut to its 32 lowest frequencies
+    # -> 64 blocks (12 pivoted, 52 dominant; 1.3 GB of blocks), the same per-block kernels
+    "ionic_40x40_w32": Workload("ionic_40x40_w32", 40, 4.0, 1.0, 0.1, 32,
+                                note="64 complex 1600x1600 blocks, 12 pivoted"),
 }
 
 
