@@ -70,7 +70,8 @@ __global__ void k_assemble(S* M, int ldm, size_t mat_stride, size_t plane_stride
 // Zero fill and assembly in one pass, one warp per row (16-byte zero stores): blocks
 // [0, full_blocks) get whole rows; the later ones (symmetric dominant blocks, lower tiles
 // only) get the columns up to the end of the row's diagonal tile of width `tile`: their
-// strictly upper tiles are never read before k_mirror overwrites them.
+// strictly upper tiles are never read (the refinement reads the lower triangle; only the
+// whole-row comparison path has k_mirror fill them first).
 template <typename S>
 __global__ void __launch_bounds__(256)
     k_assemble_rows(S* M, int ldm, size_t mat_stride, size_t plane_stride, int b0, Lattice la0,
@@ -826,7 +827,8 @@ __global__ void k_split_cols(const S* M, int N, int ldm, size_t mat_stride, size
 // touch an upper tile are redirected to the transposed lower entry with that sign.
 
 // Completes the fully swept (symmetric) inverse: M[i][j] = M[j][i] for i < j, 32x32 tiles
-// through shared memory.
+// through shared memory.  Only for the whole-row refinement (SCA_REFINE_LOWER=0); by default
+// diag(G) is refined from the lower triangle.
 template <typename S>
 __global__ void k_mirror(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride) {
   __shared__ S tr[32][33], ti[32][33];
