@@ -330,7 +330,36 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
   int* s_val = s_pos + 2 * kb;
   S* re = M + mat * mat_stride;
   S* im = re + plane_stride;
-  if (sizeof(S) == 4 && kb % 4 == 0 && k0 % 4 == 0 && ldm % 4 == 0) {
+  if (sizeof(S) == 4 && kb == 16 && k0 % 4 == 0 && ldm % 4 == 0) {
+    // 16 columns: float4 loads of 4 consecutive entries of one plane, LB of them in flight
+    // per thread; the row, plane and column of unit e by shifts (8 units per row)
+    constexpr int LB = 8;
+    const int tot = m * 8;
+    for (int e0 = tid; e0 < tot; e0 += NT * LB) {
+      float4 v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int e = e0 + NT * u;
+        if (e < tot) {
+          const int r = e >> 3, pl = (e >> 2) & 1, c4 = (e & 3) * 4;
+          const S* src = (pl == 0 ? re : im) + (size_t)(k0 + r) * ldm + k0 + c4;
+          v[u] = *reinterpret_cast<const float4*>(src);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int e = e0 + NT * u;
+        if (e < tot) {
+          const int r = e >> 3, pl = (e >> 2) & 1, c4 = (e & 3) * 4;
+          C* dst = reinterpret_cast<C*>(P + r * ps + c4) + pl;  // .re or .im of 4 entries
+          dst[0] = (C)v[u].x;
+          dst[2] = (C)v[u].y;
+          dst[4] = (C)v[u].z;
+          dst[6] = (C)v[u].w;
+        }
+      }
+    }
+  } else if (sizeof(S) == 4 && kb % 4 == 0 && k0 % 4 == 0 && ldm % 4 == 0) {
     // float4 loads of 4 consecutive entries of one plane, LB of them in flight per thread
     constexpr int LB = 8;
     const int q4 = kb / 4, per_row = 2 * q4, tot = m * per_row;
@@ -417,18 +446,34 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
     // eliminate below the pivot; the new column c+1 feeds the next pivot search
     best = (C)-1;
     bi = m;
-    for (int r = c + 1 + tid; r < m; r += NT) {
-      const cpx<C> l = cmul(P[r * ps + c], inv);
-      P[r * ps + c] = l;
+    // two rows per pass (r and r + NT): each entry of the pivot row is read once for both
+    for (int r = c + 1 + tid; r < m; r += 2 * NT) {
+      const int r2 = r + NT;
+      const bool two = r2 < m;
+      cpx<C>* row = P + r * ps;
+      cpx<C>* row2 = P + (two ? r2 : r) * ps;
+      const cpx<C> l = cmul(row[c], inv);
+      const cpx<C> l2 = cmul(row2[c], inv);
+      row[c] = l;
+      if (two) row2[c] = l2;
       for (int j = c + 1; j < kb; ++j) {
         const cpx<C> u = P[c * ps + j];
-        P[r * ps + j].re -= l.re * u.re - l.im * u.im;
-        P[r * ps + j].im -= l.re * u.im + l.im * u.re;
+        row[j].re -= l.re * u.re - l.im * u.im;
+        row[j].im -= l.re * u.im + l.im * u.re;
+        if (two) {
+          row2[j].re -= l2.re * u.re - l2.im * u.im;
+          row2[j].im -= l2.re * u.im + l2.im * u.re;
+        }
       }
       if (c + 1 < kb) {
-        const cpx<C> z = P[r * ps + c + 1];
+        const cpx<C> z = row[c + 1];
         const C v = z.re * z.re + z.im * z.im;
         if (v > best) { best = v; bi = r; }
+        if (two) {
+          const cpx<C> z2 = row2[c + 1];
+          const C v2 = z2.re * z2.re + z2.im * z2.im;
+          if (v2 > best) { best = v2; bi = r2; }
+        }
       }
     }
     if (c + 1 < kb) {
@@ -437,11 +482,22 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
       __syncthreads();
     }
   }
-  for (int e = tid; e < m * kb; e += NT) {
-    const int r = e / kb, c = e - r * kb;
-    const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
-    re[o] = (S)P[r * ps + c].re;
-    im[o] = (S)P[r * ps + c].im;
+  if (kb <= 16) {
+    // a warp per row: lanes 0-15 the real parts, 16-31 the imaginary parts of its columns
+    const int c = lane & 15;
+    S* dstp = lane < 16 ? re : im;
+    if (c < kb)
+      for (int r = warp; r < m; r += NT / 32) {
+        const cpx<C> z = P[r * ps + c];
+        dstp[(size_t)(k0 + r) * ldm + k0 + c] = (S)(lane < 16 ? z.re : z.im);
+      }
+  } else {
+    for (int e = tid; e < m * kb; e += NT) {
+      const int r = e / kb, c = e - r * kb;
+      const size_t o = (size_t)(k0 + r) * ldm + k0 + c;
+      re[o] = (S)P[r * ps + c].re;
+      im[o] = (S)P[r * ps + c].im;
+    }
   }
   // The row permutation: the kb interchanges (c, s_sw[c]) applied in order to the perm
   // entries they touch, gathered once, swapped in shared memory and written back.
