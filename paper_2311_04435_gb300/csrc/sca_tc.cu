@@ -527,29 +527,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int off = row * 64 + ((u ^ ((row >> 1) & 3)) << 4);
-              __nv_bfloat16 h[4][8];
+              // the 8 entries of this 16-byte unit as bf16 pairs packed in registers (the
+              // lower-addressed entry in the low half): planes re_hi, im_hi, re_lo, im_lo
+              uint32_t pk[4][4];
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int j = jc + 8 * u + e;
-                float vr, vi;
-                if (rowk) {
-                  const float2 tv = (j < a.kb) ? trow[j] : make_float2(0.f, 0.f);
-                  vr = -tv.x;
-                  vi = -tv.y;
-                } else {
-                  vr = -__uint_as_float(cr[8 * u + e]);
-                  vi = -__uint_as_float(ci[8 * u + e]);
-                  if (neg) { vr = -vr; vi = -vi; }
+              for (int e2 = 0; e2 < 4; ++e2) {
+                float vr[2], vi[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int e = 2 * e2 + h;
+                  const int j = jc + 8 * u + e;
+                  if (rowk) {
+                    const float2 tv = (j < a.kb) ? trow[j] : make_float2(0.f, 0.f);
+                    vr[h] = -tv.x;
+                    vi[h] = -tv.y;
+                  } else {
+                    vr[h] = -__uint_as_float(cr[8 * u + e]);
+                    vi[h] = -__uint_as_float(ci[8 * u + e]);
+                    if (neg) { vr[h] = -vr[h]; vi[h] = -vi[h]; }
+                  }
                 }
-                h[0][e] = __float2bfloat16_rn(vr);
-                h[1][e] = __float2bfloat16_rn(vi);
-                h[2][e] = __float2bfloat16_rn(vr - __bfloat162float(h[0][e]));
-                h[3][e] = __float2bfloat16_rn(vi - __bfloat162float(h[1][e]));
+                const __nv_bfloat162 hr = __floats2bfloat162_rn(vr[0], vr[1]);
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(vi[0], vi[1]);
+                const float2 hrf = __bfloat1622float2(hr), hif = __bfloat1622float2(hi);
+                const __nv_bfloat162 lr = __floats2bfloat162_rn(vr[0] - hrf.x, vr[1] - hrf.y);
+                const __nv_bfloat162 li = __floats2bfloat162_rn(vi[0] - hif.x, vi[1] - hif.y);
+                pk[0][e2] = *reinterpret_cast<const uint32_t*>(&hr);
+                pk[1][e2] = *reinterpret_cast<const uint32_t*>(&hi);
+                pk[2][e2] = *reinterpret_cast<const uint32_t*>(&lr);
+                pk[3][e2] = *reinterpret_cast<const uint32_t*>(&li);
               }
 #pragma unroll
               for (int pl = 0; pl < 4; ++pl)
                 *reinterpret_cast<uint4*>(s0 + pl * (kBM * 64) + off) =
-                    *reinterpret_cast<const uint4*>(h[pl]);
+                    make_uint4(pk[pl][0], pk[pl][1], pk[pl][2], pk[pl][3]);
             }
             fence_proxy_async();
             epi_bar();
