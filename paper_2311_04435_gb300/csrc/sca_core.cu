@@ -1074,6 +1074,45 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// B operands of the tensor-core prep product F = M[:, K] X as bf16 split planes of -X^T
+// (re_hi, im_hi, re_lo, im_lo; element [j][r] = -X[r][j]): X = T in the first half of each of
+// the block's float-plane slots, X = inv(L) in the second half.  The rows of T and inv(L) just
+// written to global memory are read back through the shared-memory buffer Sm ([nb][nb + 1]).
+template <typename C, int NT>
+__device__ void tinv_split_planes(const cpx<C>* outT, const cpx<C>* outL, cpx<C>* Sm, float* TT,
+                                  int nb, int mat) {
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)nb * nb;
+  float* tt = TT + (size_t)mat * kTtPlanes * P;
+  for (int part = 0; part < 2; ++part) {
+    const cpx<C>* src = part == 0 ? outT : outL;
+    for (int e = tid; e < nb * nb; e += NT) {
+      const int r = e / nb, j = e - r * nb;
+      Sm[(size_t)r * (nb + 1) + j] = src[e];
+    }
+    __syncthreads();
+    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(tt + (part == 0 ? 0 : P / 2));
+    for (int e = tid; e < nb * (nb / 4); e += NT) {
+      const int jr = e / (nb / 4), r4 = (e - jr * (nb / 4)) * 4;
+      __nv_bfloat16 h[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const cpx<C> v = Sm[(size_t)(r4 + t) * (nb + 1) + jr];
+        const float fr = -(float)v.re, fi = -(float)v.im;
+        h[0][t] = __float2bfloat16_rn(fr);
+        h[1][t] = __float2bfloat16_rn(fi);
+        h[2][t] = __float2bfloat16_rn(fr - __bfloat162float(h[0][t]));
+        h[3][t] = __float2bfloat16_rn(fi - __bfloat162float(h[1][t]));
+      }
+      const size_t o = (size_t)jr * nb + r4;
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl)
+        *reinterpret_cast<uint2*>(dst + 2 * pl * P + o) = *reinterpret_cast<const uint2*>(h[pl]);
+    }
+    __syncthreads();
+  }
+}
+
 // Inverses of the pivoted group's pivot block from the packed LU of the outer panel (the
 // interchanges already moved the pivot rows into K, so M_KK = L_KK U_KK):
 //   Tinv slot 0: T = inv(M_KK) = inv(U_KK) inv(L_KK)        slot 1: inv(L_KK)
@@ -1177,41 +1216,263 @@ __global__ void __launch_bounds__(NT)
     }
   }
   if (!TT) return;
-  // B operands of the tensor-core prep product F = M[:, K] X as bf16 split planes of -X^T
-  // (re_hi, im_hi, re_lo, im_lo; element [j][r] = -X[r][j]): X = T in the
-  // first half of each of the block's float-plane slots, X = inv(L) in the second half.
-  // The rows just written are read back through shared memory (the LU is no longer needed).
+  __syncthreads();  // every row of T and inv(L) is written; the LU is no longer needed
+  tinv_split_planes<C, NT>(outT, outL, LU, TT, nb, mat);
+}
+
+// The outputs of k_tinv_warp (float) by blocked triangular inversion, kb a multiple of 16:
+//   1. the 16 x 16 diagonal blocks of L (unit lower) and of U (upper) inverted in place, one
+//      warp per block and one lane per column (L's strictly lower part and U's upper part of a
+//      diagonal block are disjoint, so the two warps of a block never touch each other's data);
+//   2. X = inv(L) block row by block row downwards: Y = L[i, <i] X[<i, <i] into a buffer, then
+//      X[i, <i] = -inv(L_ii) Y in place;
+//   3. inv(U) block row by block row upwards the same way;
+//   4. T = inv(U) inv(L), written with inv(L).
+// Products run on 4 x 4 complex register tiles (4 + 4 operand loads per 16 complex FMAs).  In
+// the block-row products each tile belongs to a group of 8 lanes that split its k-range and add
+// their partial tiles by shuffles in a fixed order, so the result does not depend on timing.
+constexpr int kTinvB = 16;
+
+__device__ __forceinline__ void tile_fma(cpx<float> (&acc)[4][4], const cpx<float> (&a)[4],
+                                         const cpx<float> (&b)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j].re = fmaf(a[i].re, b[j].re, fmaf(-a[i].im, b[j].im, acc[i][j].re));
+      acc[i][j].im = fmaf(a[i].re, b[j].im, fmaf(a[i].im, b[j].re, acc[i][j].im));
+    }
+}
+
+__device__ __forceinline__ void tile_zero(cpx<float> (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = {0.f, 0.f};
+}
+
+// sum of the tiles of the 8 lanes of a group (lanes 8g .. 8g + 7), every lane of the warp
+__device__ __forceinline__ void tile_group_sum(cpx<float> (&acc)[4][4]) {
+#pragma unroll
+  for (int off = 1; off < 8; off <<= 1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[i][j].re += __shfl_xor_sync(0xffffffffu, acc[i][j].re, off);
+        acc[i][j].im += __shfl_xor_sync(0xffffffffu, acc[i][j].im, off);
+      }
+}
+
+template <typename S, int NT>
+__global__ void __launch_bounds__(NT)
+    k_tinv_blocked(const S* M, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+                   int nb, cpx<float>* Tinv, float* TT) {
+  using C = float;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ls = kb;                                        // row stride: tile columns 16-byte aligned
+  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);          // kb x kb: LU, then the inverses
+  cpx<C>* Y = A + (size_t)kb * kb;                          // kTinvB x kb block-row products
+  const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid >> 3, sub = tid & 7;                  // groups of 8 lanes
+  const int nbk = kb / kTinvB;
+  const cpx<C> one = {(C)1, (C)0}, zero = {(C)0, (C)0};
+  const S* re = M + mat * mat_stride + (size_t)k0 * ldm + k0;  // the packed pivot block
+  const S* im = re + plane_stride;
+  for (int e = tid; e < kb * kb; e += NT) {
+    const int a = e / kb, b = e - a * kb;
+    A[e] = {(C)re[(size_t)a * ldm + b], (C)im[(size_t)a * ldm + b]};
+  }
   __syncthreads();
-  const size_t P = (size_t)nb * nb;
-  float* tt = TT + (size_t)mat * kTtPlanes * P;
-  cpx<C>* Sm = LU;  // [nb][nb + 1]
-  for (int part = 0; part < 2; ++part) {
-    const cpx<C>* src = part == 0 ? outT : outL;
-    for (int e = tid; e < nb * nb; e += NT) {
-      const int r = e / nb, j = e - r * nb;
-      Sm[(size_t)r * (nb + 1) + j] = src[e];
+  // 1. diagonal blocks: lane l computes column l of the block's inverse, then writes it
+  for (int task = warp; task < 2 * nbk; task += NT / 32) {
+    if (lane < kTinvB) {
+      const int d0 = (task >> 1) * kTinvB, l = lane;
+      cpx<C>* D = A + (size_t)d0 * ls + d0;
+      cpx<C> x[kTinvB];
+      if ((task & 1) == 0) {  // unit lower: forward substitution
+#pragma unroll
+        for (int r = 0; r < kTinvB; ++r) {
+          cpx<C> v = (r == l) ? one : zero;
+#pragma unroll
+          for (int k = 0; k < r; ++k) {
+            const cpx<C> t = cmul(D[r * ls + k], x[k]);
+            v.re -= t.re;
+            v.im -= t.im;
+          }
+          x[r] = v;
+        }
+        __syncwarp(0xffffu);
+#pragma unroll
+        for (int r = 0; r < kTinvB; ++r)
+          if (r > l) D[r * ls + l] = x[r];
+      } else {  // upper: back substitution with the diagonal
+#pragma unroll
+        for (int r = kTinvB - 1; r >= 0; --r) {
+          cpx<C> v = (r == l) ? one : zero;
+#pragma unroll
+          for (int k = r + 1; k < kTinvB; ++k) {
+            const cpx<C> t = cmul(D[r * ls + k], x[k]);
+            v.re -= t.re;
+            v.im -= t.im;
+          }
+          const cpx<C> u = D[r * ls + r];
+          const C m2 = u.re * u.re + u.im * u.im;
+          x[r] = cmul(v, cpx<C>{u.re / m2, -u.im / m2});
+        }
+        __syncwarp(0xffffu);
+#pragma unroll
+        for (int r = 0; r < kTinvB; ++r)
+          if (r <= l) D[r * ls + l] = x[r];
+      }
+    }
+  }
+  __syncthreads();
+  // 2. inv(L) downwards.  X[k][c] = 1 (k == c), A[k][c] (k > c), 0 (k < c)
+  for (int bi = 1; bi < nbk; ++bi) {
+    const int r0 = bi * kTinvB, tcs = r0 / 4, ntile = 4 * tcs;
+    // (a) Y = L[r0 .., 0 .. r0) X[0 .. r0, 0 .. r0): tile (4 rows R, 4 columns C0), k >= C0
+    for (int t0 = 0; t0 < ntile; t0 += NT / 8) {
+      const int t = t0 + grp;
+      const bool act = t < ntile;
+      const int R = act ? 4 * (t / tcs) : 0, C0 = act ? 4 * (t % tcs) : 0;
+      cpx<C> acc[4][4];
+      tile_zero(acc);
+      if (act)
+        for (int k = C0 + sub; k < r0; k += 8) {
+          cpx<C> a[4], x[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = A[(size_t)(r0 + R + i) * ls + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = C0 + j;
+            x[j] = k > c ? A[(size_t)k * ls + c] : (k == c ? one : zero);
+          }
+          tile_fma(acc, a, x);
+        }
+      tile_group_sum(acc);
+      if (act && sub == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) Y[(R + i) * kb + C0 + j] = acc[i][j];
     }
     __syncthreads();
-    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(tt + (part == 0 ? 0 : P / 2));
-    for (int e = tid; e < nb * (nb / 4); e += NT) {
-      const int jr = e / (nb / 4), r4 = (e - jr * (nb / 4)) * 4;
-      __nv_bfloat16 h[4][4];
+    // (b) X[r0 + r][c] = -(Y[r][c] + sum_{m < r} inv(L_ii)[r][m] Y[m][c]), a tile per thread
+    for (int t = tid; t < ntile; t += NT) {
+      const int R = 4 * (t / tcs), C0 = 4 * (t % tcs);
+      cpx<C> acc[4][4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const cpx<C> v = Sm[(size_t)(r4 + t) * (nb + 1) + jr];
-        const float fr = -(float)v.re, fi = -(float)v.im;
-        h[0][t] = __float2bfloat16_rn(fr);
-        h[1][t] = __float2bfloat16_rn(fi);
-        h[2][t] = __float2bfloat16_rn(fr - __bfloat162float(h[0][t]));
-        h[3][t] = __float2bfloat16_rn(fi - __bfloat162float(h[1][t]));
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Y[(R + i) * kb + C0 + j];
+#pragma unroll 4
+      for (int m = 0; m < R + 3; ++m) {
+        cpx<C> a[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          a[i] = m < R + i ? A[(size_t)(r0 + R + i) * ls + r0 + m] : zero;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = Y[m * kb + C0 + j];
+        tile_fma(acc, a, y);
       }
-      const size_t o = (size_t)jr * nb + r4;
 #pragma unroll
-      for (int pl = 0; pl < 4; ++pl)
-        *reinterpret_cast<uint2*>(dst + 2 * pl * P + o) = *reinterpret_cast<const uint2*>(h[pl]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          A[(size_t)(r0 + R + i) * ls + C0 + j] = {-acc[i][j].re, -acc[i][j].im};
     }
     __syncthreads();
   }
+  // 3. inv(U) upwards.  XU[k][c] = A[k][c] (k <= c), 0 (k > c)
+  for (int bi = nbk - 2; bi >= 0; --bi) {
+    const int r0 = bi * kTinvB, c0 = r0 + kTinvB, tcs = (kb - c0) / 4, ntile = 4 * tcs;
+    // (a) Y[r][cc] = sum_{k = c0}^{c} U[r0 + r][k] XU[k][c], c = c0 + cc
+    for (int t0 = 0; t0 < ntile; t0 += NT / 8) {
+      const int t = t0 + grp;
+      const bool act = t < ntile;
+      const int R = act ? 4 * (t / tcs) : 0, C0 = act ? 4 * (t % tcs) : 0;
+      cpx<C> acc[4][4];
+      tile_zero(acc);
+      if (act)
+        for (int k = c0 + sub; k <= c0 + C0 + 3; k += 8) {
+          cpx<C> a[4], x[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = A[(size_t)(r0 + R + i) * ls + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = c0 + C0 + j;
+            x[j] = k <= c ? A[(size_t)k * ls + c] : zero;
+          }
+          tile_fma(acc, a, x);
+        }
+      tile_group_sum(acc);
+      if (act && sub == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) Y[(R + i) * kb + C0 + j] = acc[i][j];
+    }
+    __syncthreads();
+    // (b) X[r0 + r][c] = -sum_{m >= r} inv(U_ii)[r][m] Y[m][cc], a tile per thread
+    for (int t = tid; t < ntile; t += NT) {
+      const int R = 4 * (t / tcs), C0 = 4 * (t % tcs);
+      cpx<C> acc[4][4];
+      tile_zero(acc);
+#pragma unroll 4
+      for (int m = R; m < kTinvB; ++m) {
+        cpx<C> a[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          a[i] = m >= R + i ? A[(size_t)(r0 + R + i) * ls + r0 + m] : zero;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = Y[m * kb + C0 + j];
+        tile_fma(acc, a, y);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          A[(size_t)(r0 + R + i) * ls + c0 + C0 + j] = {-acc[i][j].re, -acc[i][j].im};
+    }
+    __syncthreads();
+  }
+  // 4. T[r][c] = sum_{k >= max(r, c)} XU[r][k] XL[k][c]: warp = tile row, lane = tile column
+  cpx<C>* outT = Tinv + (size_t)mat * 2 * nb * nb;
+  cpx<C>* outL = outT + (size_t)nb * nb;
+  for (int tr = warp; tr < nb / 4; tr += NT / 32) {
+    const int R0 = 4 * tr;
+    for (int tcl = lane; tcl < nb / 4; tcl += 32) {
+      const int C0 = 4 * tcl;
+      cpx<C> acc[4][4];
+      tile_zero(acc);
+      if (R0 < kb && C0 < kb)
+        for (int k = R0; k < kb; ++k) {
+          cpx<C> u[4], x[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) u[i] = k >= R0 + i ? A[(size_t)(R0 + i) * ls + k] : zero;
+          const float4 x01 = *reinterpret_cast<const float4*>(A + (size_t)k * ls + C0);
+          const float4 x23 = *reinterpret_cast<const float4*>(A + (size_t)k * ls + C0 + 2);
+          const cpx<C> xs[4] = {{x01.x, x01.y}, {x01.z, x01.w}, {x23.x, x23.y}, {x23.z, x23.w}};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = k > C0 + j ? xs[j] : (k == C0 + j ? one : zero);
+          tile_fma(acc, u, x);
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = R0 + i, c = C0 + j;
+          const bool in = r < kb && c < kb;
+          outT[(size_t)r * nb + c] = in ? acc[i][j] : zero;
+          outL[(size_t)r * nb + c] =
+              (in && r >= c) ? (r == c ? one : A[(size_t)r * ls + c]) : zero;
+        }
+    }
+  }
+  if (!TT) return;
+  __syncthreads();  // every row of T and inv(L) is written; the LU copy is no longer needed
+  tinv_split_planes<C, NT>(outT, outL, A, TT, nb, mat);
 }
 
 // A operand of the pivoted group's tensor-core prep product: the columns K of rows
@@ -2148,6 +2409,14 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
 // float32 refinement on, diag(G) is read from those tiles (k_refine_lower_rows/_cols) and the
 // upper tiles are never filled; otherwise k_mirror copies the lower triangle up and the row
 // kernels read whole rows.
+// The pivoted group's pivot-block inverse by blocked triangular inversion (k_tinv_blocked); the
+// row-solve kernel k_tinv_warp where SCA_TINV_BLOCKED=0 (the comparison path of its test).
+bool blocked_tinv() {
+  if (const char* v = std::getenv("SCA_TINV_BLOCKED"))
+    if (std::atoi(v) == 0) return false;
+  return true;
+}
+
 bool lower_refine(const Engine& e) {
   if (!e.refine || e.fp64 || !e.tc || e.tt == nullptr) return false;
   if (const char* v = std::getenv("SCA_SYM"))
@@ -2421,12 +2690,24 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       constexpr int NT = sizeof(C) == 8 ? 512 : 1024;
       constexpr int NBMAX = sizeof(C) == 8 ? 64 : 128;
       float* TT = piv_tc_prep ? e.tt + (size_t)m0 * kTtPlanes * e.nb * e.nb : nullptr;
-      if (kb == NBMAX)
-        k_tinv_warp<S, C, NT, true><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride, e.plane_stride,
-                                                          k0, kb, nb, Tinv, TT);
-      else
-        k_tinv_warp<S, C, NT, false><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride,
-                                                           e.plane_stride, k0, kb, nb, Tinv, TT);
+      bool blocked = false;
+      if constexpr (sizeof(C) == 4) {
+        if (kb % kTinvB == 0 && nb % kTinvB == 0 && kb <= nb && blocked_tinv()) {
+          const size_t smb = sizeof(cpx<C>) * std::max((size_t)kb * kb + (size_t)kTinvB * kb,
+                                                       (size_t)nb * (nb + 1));
+          k_tinv_blocked<S, 512><<<cnt, 512, smb, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
+                                                       kb, nb, Tinv, TT);
+          blocked = true;
+        }
+      }
+      if (!blocked) {
+        if (kb == NBMAX)
+          k_tinv_warp<S, C, NT, true><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride,
+                                                            e.plane_stride, k0, kb, nb, Tinv, TT);
+        else
+          k_tinv_warp<S, C, NT, false><<<cnt, NT, smt, s>>>(M, e.ldm, e.mat_stride,
+                                                             e.plane_stride, k0, kb, nb, Tinv, TT);
+      }
       prof_end(e, kTrinv, s);
       SCA_LAUNCH_CHECK("pivot-block inverse");
     } else {
@@ -2681,6 +2962,9 @@ sca_status set_smem_limits() {
   if ((err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, true>)) != cudaSuccess ||
       (err = allow_max_smem(k_tinv_warp<S, C, sizeof(C) == 8 ? 512 : 1024, false>)) != cudaSuccess)
     return cuda_fail(err, "smem tinv");
+  if constexpr (sizeof(C) == 4)
+    if ((err = allow_max_smem(k_tinv_blocked<S, 512>)) != cudaSuccess)
+      return cuda_fail(err, "smem tinv blocked");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
   once.mark();
   return SCA_OK;

@@ -352,6 +352,32 @@ def test_lower_triangle_refinement_matches_mirrored_rows(L, nw, prec, monkeypatc
     assert np.max(np.abs(res["1"][1] - res["0"][1]) / scale) <= 1e-11
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32", "fp32"])
+@pytest.mark.parametrize("L,nw", [(12, 10), (20, 8), (34, 6)])
+def test_blocked_pivoted_inverse_matches_row_solves(L, nw, prec, monkeypatch):
+    """The pivoted blocks' pivot-block inverse T = inv(U) inv(L) by blocked triangular inversion
+    against the row-solve kernel: both match the oracle, the log-dets agree to float32 rounding
+    (each step's T enters the next trailing matrix, hence the later pivots) and diag(G), after
+    the refinement, to 1e-9.  N = 144, 400 and 1156 end on a pivot block of 16, 16 and 4 x 16
+    rows (128-wide steps and a shorter last one)."""
+    monkeypatch.setenv("SCA_FUSED", "0")
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=1.0, prec=prec)
+    phi = inputs.random_phi(7 + L, p.N, 1.0)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCA_TINV_BLOCKED", flag)
+        with api.Context(p) as c:
+            res[flag] = c.blocks(phi, grad=True)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    for ld, gd in res.values():
+        assert np.allclose(ld, o_ld, rtol=t["ld"], atol=t["ld"])
+        assert np.max(np.abs(gd - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+    assert np.allclose(res["1"][0], res["0"][0], rtol=1e-7, atol=0.0)
+    scale = max(1.0, np.abs(res["0"][1]).max())
+    assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 1e-9 * scale
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
 def test_tensor_core_pivot_block_inverse_matches_register_kernel(prec, monkeypatch):
     """The dominant pivot-block inverse on the tensor cores (tableau in TMEM, split-TF32
