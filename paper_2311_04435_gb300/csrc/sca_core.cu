@@ -1270,9 +1270,11 @@ __global__ void __launch_bounds__(NT)
                    int nb, cpx<float>* Tinv, float* TT) {
   using C = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ls = kb;                                        // row stride: tile columns 16-byte aligned
-  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);          // kb x kb: LU, then the inverses
-  cpx<C>* Y = A + (size_t)kb * kb;                          // kTinvB x kb block-row products
+  // row stride kb + 2: tile columns stay 16-byte aligned and consecutive rows start 4 banks
+  // apart, so the column reads of 8 consecutive rows (the block-row products) do not conflict
+  const int ls = kb + 2;
+  cpx<C>* A = reinterpret_cast<cpx<C>*>(smem_raw);          // kb x ls: LU, then the inverses
+  cpx<C>* Y = A + (size_t)kb * ls;                          // kTinvB x kb block-row products
   const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = tid >> 3, sub = tid & 7;                  // groups of 8 lanes
   const int nbk = kb / kTinvB;
@@ -1281,7 +1283,7 @@ __global__ void __launch_bounds__(NT)
   const S* im = re + plane_stride;
   for (int e = tid; e < kb * kb; e += NT) {
     const int a = e / kb, b = e - a * kb;
-    A[e] = {(C)re[(size_t)a * ldm + b], (C)im[(size_t)a * ldm + b]};
+    A[(size_t)a * ls + b] = {(C)re[(size_t)a * ldm + b], (C)im[(size_t)a * ldm + b]};
   }
   __syncthreads();
   // 1. diagonal blocks: lane l computes column l of the block's inverse, then writes it
@@ -2693,7 +2695,7 @@ sca_status run_group(Engine& e, int b0, int m0, int cnt, bool pivoted, int nb, b
       bool blocked = false;
       if constexpr (sizeof(C) == 4) {
         if (kb % kTinvB == 0 && nb % kTinvB == 0 && kb <= nb && blocked_tinv()) {
-          const size_t smb = sizeof(cpx<C>) * std::max((size_t)kb * kb + (size_t)kTinvB * kb,
+          const size_t smb = sizeof(cpx<C>) * std::max((size_t)kb * (kb + 2) + (size_t)kTinvB * kb,
                                                        (size_t)nb * (nb + 1));
           k_tinv_blocked<S, 512><<<cnt, 512, smb, s>>>(M, e.ldm, e.mat_stride, e.plane_stride, k0,
                                                        kb, nb, Tinv, TT);
