@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--prec", default=None,
                     help="fp32 | 3xtf32 | bf16x3 (default: bf16x3)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (0 = skip)")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="extra timings of the same K-step region (best / median reported)")
+    ap.add_argument("--c1-steps", type=int, default=500,
+                    help="timed steps of the 4x4 Hubbard case (0: skip)")
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="timed steps of the no-pivoting variant (0 = skip)")
     ap.add_argument("--dos-points", type=int, default=128,
@@ -292,6 +296,24 @@ def run_ours(args):
     ms, value = aggregate_replicas(e0.elapsed_time(e1), args.steps, world)
     ms_per_step = ms / args.steps
 
+    # ---------------- the same K-step region timed again, for its spread (best / median of 5);
+    # the line's value stays the single region above
+    repeats = None
+    if rank == 0 and args.repeats > 0:
+        per = []
+        for _ in range(args.repeats):
+            torch.cuda.synchronize()
+            r0e, r1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0e.record(stream)
+            ctx.adam_step(args.steps)
+            r1e.record(stream)
+            torch.cuda.synchronize()
+            per.append(r0e.elapsed_time(r1e) / args.steps)
+        repeats = {"n": args.repeats, "steps_each": args.steps,
+                   "best_ms_per_step": round(min(per), 3),
+                   "median_ms_per_step": round(statistics.median(per), 3),
+                   "worst_ms_per_step": round(max(per), 3)}
+
     # ---------------- per-kernel durations (CUDA events on the launching stream)
     ctx.profile(True)
     ctx.adam_step(1)
@@ -493,6 +515,28 @@ def run_ours(args):
     if rank == 0 and args.serve > 0 and world == 1:
         serve = serve_sweep(args)
 
+    # ---------------- the 4x4 Hubbard case (latency-bound: microseconds per step), FP64
+    c1 = None
+    if rank == 0 and args.c1_steps > 0:
+        w1 = inputs.WORKLOADS["hubbard_4x4"]
+        p1 = api.Params(w1.L, w1.n_omega, U=w1.U, T=w1.T, delta=w1.delta, t=w1.t, mu=w1.mu,
+                        prec="fp64")
+        cc = api.Context(p1)
+        cc.set_stream(stream)
+        cc.adam_init(api.AdamConfig(lr=w1.lr, seed=w1.seed))
+        cc.adam_step(16)
+        torch.cuda.synchronize()
+        c0e, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0e.record(stream)
+        om1, gm1 = cc.adam_step(args.c1_steps)
+        c1e.record(stream)
+        torch.cuda.synchronize()
+        us1 = 1e3 * c0e.elapsed_time(c1e) / args.c1_steps
+        cc.close()
+        c1 = {"workload": "hubbard_4x4: L=4, U=6, Delta=0, T=0.1, 128 blocks of 16x16, FP64",
+              "us_per_step": round(us1, 2), "timed_steps": args.c1_steps, "warmup": 16,
+              "omega": om1, "gmax": gm1}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -516,6 +560,8 @@ def run_ours(args):
             "roofline": dict(roofline_for(prec, fl_blk * n_dom, by_blk * n_dom, launch_s, traffic),
                              traffic_source=traffic_note),
             "kernels_ms_one_step": per_kernel,
+            "repeats": repeats,
+            "hubbard_4x4": c1,
             "fp64_path": fp64,
             "no_pivoting_variant": nopiv,
             "other_precision": other,
