@@ -193,6 +193,144 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------ swap + trsm
+// The interchanges (s0 + c, sp[c]), c = 0 .. kbi - 1 (kbi <= 16; sp absolute rows) composed into
+// one list of row moves over the at most 2 kbi rows they touch: row dst[t] takes the old
+// content of row src[t].  One thread.
+__device__ int compose_moves(const int* sp, int kbi, int s0, int* mv_dst, int* mv_src) {
+  constexpr int TMAX = 16;
+  int row[2 * TMAX], from[2 * TMAX], ns = kbi;
+  for (int x = 0; x < kbi; ++x) row[x] = s0 + x, from[x] = x;
+  for (int cc = 0; cc < kbi; ++cc) {
+    const int p = sp[cc];
+    if (p == s0 + cc) continue;
+    int q = p - s0;
+    if (q >= kbi) {
+      q = kbi;
+      while (q < ns && row[q] != p) ++q;
+      if (q == ns) row[ns] = p, from[ns] = ns, ++ns;
+    }
+    const int t = from[cc];
+    from[cc] = from[q];
+    from[q] = t;
+  }
+  int nmv = 0;
+  for (int x = 0; x < ns; ++x)
+    if (from[x] != x) mv_dst[nmv] = row[x], mv_src[nmv] = row[from[x]], ++nmv;
+  return nmv;
+}
+
+// Column j outside the sub-panel [s0, s0 + kbi) (kbi <= 16): the composed row moves (every load
+// before any store: one memory round trip) and, where trsm is set (the outer panel's columns
+// still to be factored), the forward substitution U12 = inv(L11) A12 with the unit-lower L11
+// (Ls, row stride lst), in place.
+template <typename S, typename C>
+__device__ __forceinline__ void swap_trsm_column(S* re, S* im, int ldm, int j, int nmv,
+                                                 const int* mv_dst, const int* mv_src,
+                                                 const cpx<C>* Ls, int lst, int kbi, int s0,
+                                                 bool trsm) {
+  constexpr int TMAX = 16;
+  S vr[2 * TMAX], vi[2 * TMAX];
+#pragma unroll
+  for (int t = 0; t < 2 * TMAX; ++t)
+    if (t < nmv) {
+      const size_t q = (size_t)mv_src[t] * ldm + j;
+      vr[t] = re[q];
+      vi[t] = im[q];
+    }
+#pragma unroll
+  for (int t = 0; t < 2 * TMAX; ++t)
+    if (t < nmv) {
+      const size_t a = (size_t)mv_dst[t] * ldm + j;
+      re[a] = vr[t];
+      im[a] = vi[t];
+    }
+  if (!trsm) return;
+  cpx<C> u[TMAX];
+#pragma unroll
+  for (int r = 0; r < TMAX; ++r)
+    if (r < kbi) {
+      const size_t o = (size_t)(s0 + r) * ldm + j;
+      u[r] = {(C)re[o], (C)im[o]};
+    }
+#pragma unroll
+  for (int r = 0; r < TMAX; ++r) {
+    if (r >= kbi) break;
+    cpx<C> acc = u[r];
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) {
+      if (k >= r) break;
+      const cpx<C> t = cmul(Ls[r * lst + k], u[k]);
+      acc.re -= t.re;
+      acc.im -= t.im;
+    }
+    u[r] = acc;
+    const size_t o = (size_t)(s0 + r) * ldm + j;
+    re[o] = (S)acc.re;
+    im[o] = (S)acc.im;
+  }
+}
+
+// Column j of the outer panel outside the sub-panel [s0, s0 + kbi) (kbi <= 16), in one memory
+// round trip: row s0 + r takes the old content of row srow[r], row far_dst[t] (below the
+// sub-panel) that of far_src[t]; every load before any store.  Where trsm is set the
+// sub-panel's rows are then solved, U12 = inv(L11) A12 with the unit-lower L11 (Ls, row stride
+// lst), before they are stored.  Entry for entry the same result as swap_trsm_column.
+template <typename S, typename C>
+__device__ __forceinline__ void panel_column_tail(S* re, S* im, int ldm, int j, int kbi, int s0,
+                                                  const int* srow, int nfar, const int* far_dst,
+                                                  const int* far_src, const cpx<C>* Ls, int lst,
+                                                  bool trsm) {
+  constexpr int TMAX = 16;
+  cpx<C> u[TMAX];
+  S fr[TMAX], fi[TMAX];
+#pragma unroll
+  for (int r = 0; r < TMAX; ++r)
+    if (r < kbi) {
+      const size_t q = (size_t)srow[r] * ldm + j;
+      u[r] = {(C)re[q], (C)im[q]};
+    }
+#pragma unroll
+  for (int t = 0; t < TMAX; ++t)
+    if (t < nfar) {
+      const size_t q = (size_t)far_src[t] * ldm + j;
+      fr[t] = re[q];
+      fi[t] = im[q];
+    }
+#pragma unroll
+  for (int t = 0; t < TMAX; ++t)
+    if (t < nfar) {
+      const size_t a = (size_t)far_dst[t] * ldm + j;
+      re[a] = fr[t];
+      im[a] = fi[t];
+    }
+  if (!trsm) {
+#pragma unroll
+    for (int r = 0; r < TMAX; ++r)
+      if (r < kbi && srow[r] != s0 + r) {
+        const size_t o = (size_t)(s0 + r) * ldm + j;
+        re[o] = (S)u[r].re;
+        im[o] = (S)u[r].im;
+      }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < TMAX; ++r) {
+    if (r >= kbi) break;
+    cpx<C> acc = u[r];
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) {
+      if (k >= r) break;
+      const cpx<C> t = cmul(Ls[r * lst + k], u[k]);
+      acc.re -= t.re;
+      acc.im -= t.im;
+    }
+    u[r] = acc;
+    const size_t o = (size_t)(s0 + r) * ldm + j;
+    re[o] = (S)acc.re;
+    im[o] = (S)acc.im;
+  }
+}
+
 // After a pivoted sub-panel [s0, s0+kbi): each thread takes one column j >= jstart outside the
 // sub-panel, applies the sub-panel's interchanges to it in order and, for the columns of the
 // outer panel still to be factored ([s0+kbi, c_end)), the forward substitution with the
@@ -220,87 +358,110 @@ __global__ void __launch_bounds__(128)
   for (int t = threadIdx.x; t < kbi && t < KMAX; t += blockDim.x)
     sp[t] = piv[(size_t)mat * N + s0 + t];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // for a sub-panel of at most TMAX columns, compose its interchanges into one list of row
-    // moves (row dst takes the old content of row src) over the at most 2 kbi rows they touch
-    int nmv = -1;
-    if (kbi <= TMAX) {
-      int row[2 * TMAX], from[2 * TMAX], ns = kbi;
-      for (int x = 0; x < kbi; ++x) row[x] = s0 + x, from[x] = x;
-      for (int cc = 0; cc < kbi; ++cc) {
-        const int p = sp[cc];
-        if (p == s0 + cc) continue;
-        int q = p - s0;
-        if (q >= kbi) {
-          q = kbi;
-          while (q < ns && row[q] != p) ++q;
-          if (q == ns) row[ns] = p, from[ns] = ns, ++ns;
-        }
-        const int t = from[cc];
-        from[cc] = from[q];
-        from[q] = t;
-      }
-      nmv = 0;
-      for (int x = 0; x < ns; ++x)
-        if (from[x] != x) mv_dst[nmv] = row[x], mv_src[nmv] = row[from[x]], ++nmv;
-    }
-    s_nmv = nmv;
-  }
+  if (threadIdx.x == 0) s_nmv = kbi <= TMAX ? compose_moves(sp, kbi, s0, mv_dst, mv_src) : -1;
   __syncthreads();
   const int j = jstart + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N || (j >= s0 && j < s0 + kbi)) return;
   const int nmv = s_nmv;
   if (nmv >= 0) {
-    // every load of the column's moves before any store: one memory round trip
-    S vr[2 * TMAX], vi[2 * TMAX];
-#pragma unroll
-    for (int t = 0; t < 2 * TMAX; ++t)
-      if (t < nmv) {
-        const size_t q = (size_t)mv_src[t] * ldm + j;
-        vr[t] = re[q];
-        vi[t] = im[q];
-      }
-#pragma unroll
-    for (int t = 0; t < 2 * TMAX; ++t)
-      if (t < nmv) {
-        const size_t a = (size_t)mv_dst[t] * ldm + j;
-        re[a] = vr[t];
-        im[a] = vi[t];
-      }
-  } else {
-    for (int cc = 0; cc < kbi && cc < KMAX; ++cc) {
-      const int p = sp[cc];
-      if (p != s0 + cc) {
-        const size_t a = (size_t)(s0 + cc) * ldm + j, q = (size_t)p * ldm + j;
-        const S xr = re[a], xi = im[a];
-        re[a] = re[q]; im[a] = im[q];
-        re[q] = xr; im[q] = xi;
-      }
+    swap_trsm_column<S, C>(re, im, ldm, j, nmv, mv_dst, mv_src, &Ls[0][0], TMAX + 1, kbi, s0,
+                           tr && j >= s0 + kbi && j < c_end);
+    return;
+  }
+  // a sub-panel as wide as its outer panel: the interchanges in order, nothing left to solve
+  for (int cc = 0; cc < kbi && cc < KMAX; ++cc) {
+    const int p = sp[cc];
+    if (p != s0 + cc) {
+      const size_t a = (size_t)(s0 + cc) * ldm + j, q = (size_t)p * ldm + j;
+      const S xr = re[a], xi = im[a];
+      re[a] = re[q]; im[a] = im[q];
+      re[q] = xr; im[q] = xi;
     }
   }
-  if (!tr || j < s0 + kbi || j >= c_end) return;
-  cpx<C> u[TMAX];
-#pragma unroll
-  for (int r = 0; r < TMAX; ++r)
-    if (r < kbi) {
-      const size_t o = (size_t)(s0 + r) * ldm + j;
-      u[r] = {(C)re[o], (C)im[o]};
+}
+
+// The interchanges of a whole outer panel [k0, k0 + kb) (piv: its columns' pivot rows, in
+// order) on the columns outside it, [jstart, k0) and [k0 + kb, N).  Each CTA composes them
+// into one list of at most 2 kb row moves (row dst takes the old content of row src), then
+// moves strips of kSwapStrip columns: every source entry of the strip into shared memory,
+// then every destination.  grid (CTAs per block, blocks); dynamic shared memory
+// swap_outer_smem(N - k0, kb, sizeof(S)).
+constexpr int kSwapStrip = 32;
+constexpr int kSwapCtas = 4;  // CTAs per block (each composes the moves once)
+__host__ __device__ constexpr size_t swap_outer_smem(int m, int kb, int es) {
+  return ((sizeof(int) * ((size_t)m + 5 * (size_t)kb) + 15) / 16) * 16 +
+         (size_t)es * 2 * 2 * kb * kSwapStrip;
+}
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_swap_outer(S* M, int N, int ldm, size_t mat_stride, size_t plane_stride, int k0, int kb,
+                 int jstart, const int* piv) {
+  extern __shared__ unsigned char smem_raw[];
+  const int m = N - k0, kend = k0 + kb, tid = threadIdx.x;
+  int* cur = reinterpret_cast<int*>(smem_raw);  // content of position k0 + x: old row k0 + cur[x]
+  int* mv_dst = cur + m;
+  int* mv_src = mv_dst + 2 * kb;
+  int* sp = mv_src + 2 * kb;
+  S* bre = reinterpret_cast<S*>(smem_raw + ((sizeof(int) * ((size_t)m + 5 * kb) + 15) / 16) * 16);
+  S* bim = bre + 2 * kb * kSwapStrip;
+  __shared__ int s_nmv;
+  const int mat = blockIdx.y;
+  S* re = M + mat * mat_stride;
+  S* im = re + plane_stride;
+  for (int x = tid; x < m; x += blockDim.x) cur[x] = x;
+  for (int c = tid; c < kb; c += blockDim.x) sp[c] = piv[(size_t)mat * N + k0 + c] - k0;
+  if (tid == 0) s_nmv = 0;
+  __syncthreads();
+  if (tid == 0)
+    for (int c = 0; c < kb; ++c) {
+      const int p = sp[c];
+      if (p <= c || p >= m) continue;  // no interchange (a pivot row is never above its column)
+      const int t = cur[c];
+      cur[c] = cur[p];
+      cur[p] = t;
     }
-#pragma unroll
-  for (int r = 0; r < TMAX; ++r) {
-    if (r >= kbi) break;
-    cpx<C> acc = u[r];
-#pragma unroll
-    for (int k = 0; k < TMAX; ++k) {
-      if (k >= r) break;
-      const cpx<C> t = cmul(Ls[r][k], u[k]);
-      acc.re -= t.re;
-      acc.im -= t.im;
+  __syncthreads();
+  for (int x = tid; x < m; x += blockDim.x)
+    if (cur[x] != x) {
+      const int t = atomicAdd(&s_nmv, 1);
+      if (t < 2 * kb) mv_dst[t] = k0 + x, mv_src[t] = k0 + cur[x];
     }
-    u[r] = acc;
-    const size_t o = (size_t)(s0 + r) * ldm + j;
-    re[o] = (S)acc.re;
-    im[o] = (S)acc.im;
+  __syncthreads();
+  const int nmv = s_nmv;  // at most 2 kb: the interchanges touch no other rows
+  if (nmv == 0 || nmv > 2 * kb) return;
+  const int nl = k0 - jstart, nco = nl + (N - kend);
+  const int tot = nmv * kSwapStrip;
+  constexpr int U = 8;
+  for (int v0 = blockIdx.x * kSwapStrip; v0 < nco; v0 += gridDim.x * kSwapStrip) {
+    for (int e0 = tid; e0 < tot; e0 += 256 * U) {
+      S vr[U] = {}, vi[U] = {};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + 256 * u, v = v0 + (e & (kSwapStrip - 1));
+        if (e < tot && v < nco) {
+          const int j = v < nl ? jstart + v : kend + (v - nl);
+          const size_t q = (size_t)mv_src[e / kSwapStrip] * ldm + j;
+          vr[u] = re[q];
+          vi[u] = im[q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + 256 * u;
+        if (e < tot) bre[e] = vr[u], bim[e] = vi[u];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < tot; e += 256) {
+      const int v = v0 + (e & (kSwapStrip - 1));
+      if (v < nco) {
+        const int j = v < nl ? jstart + v : kend + (v - nl);
+        const size_t a = (size_t)mv_dst[e / kSwapStrip] * ldm + j;
+        re[a] = bre[e];
+        im[a] = bim[e];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -313,14 +474,16 @@ __global__ void __launch_bounds__(128)
 template <typename S, typename C, int NT>
 __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t mat_stride,
                                                    size_t plane_stride, int k0, int kb, int b0,
-                                                   double* ld, int* piv, int* perm, int* flags) {
+                                                   double* ld, int* piv, int* perm, int* flags,
+                                                   int swap_from, int c_end) {
   extern __shared__ unsigned char smem_raw[];
   cpx<C>* P = reinterpret_cast<cpx<C>*>(smem_raw);  // m x (kb+1), row-major, padded
   const int ps = kb + 1;  // odd row stride: conflict-free column access
   __shared__ C red_v[NT / 32];
   __shared__ int red_i[NT / 32];
-  __shared__ int s_p;
   __shared__ double piv2[256];
+  // sub-panels <= 16: the source row of each row of the sub-panel, and the moves to rows below it
+  __shared__ int s_srow[16], s_fdst[16], s_fsrc[16], s_nfar;
   const int mat = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = N - k0;
   // after the panel: the pivot row (panel-relative) of each column, then the perm entries
@@ -499,37 +662,77 @@ __global__ void __launch_bounds__(NT) k_panel_smem(S* M, int N, int ldm, size_t 
       im[o] = (S)P[r * ps + c].im;
     }
   }
-  // The row permutation: the kb interchanges (c, s_sw[c]) applied in order to the perm
-  // entries they touch, gathered once, swapped in shared memory and written back.
+  // The row permutation of the kb interchanges (c, s_sw[c]), c in order, over the at most 2 kb
+  // positions they touch.  Slot c < kb is position c; slot kb + c is position s_sw[c] >= kb if
+  // c is the first column with that pivot row (s_pos[kb + c] = kb + that first column; -1 for
+  // pivot rows < kb).  s_val[t] ends as the slot whose old content slot t takes.
   {
     int* pm = perm + (size_t)mat * N + k0;
     if (tid < 2 * kb) {
-      const int q = (tid < kb) ? tid : s_sw[tid - kb];
+      int q = tid;
+      if (tid >= kb) {
+        const int p = s_sw[tid - kb];
+        q = -1;
+        if (p >= kb) {
+          int f = 0;
+          while (s_sw[f] != p) ++f;  // ends at tid - kb at the latest
+          q = kb + f;
+        }
+      }
       s_pos[tid] = q;
-      s_val[tid] = pm[q];
+      s_val[tid] = tid;
     }
     __syncthreads();
     if (tid == 0)
       for (int c = 0; c < kb; ++c) {
         const int p = s_sw[c];
         if (p == c) continue;
-        int a = -1, b = -1;  // first slots holding positions c and p (duplicates share values)
-        for (int t = 0; t < 2 * kb && (a < 0 || b < 0); ++t) {
-          if (a < 0 && s_pos[t] == c) a = t;
-          if (b < 0 && s_pos[t] == p) b = t;
-        }
-        const int tmp = s_val[a];
-        s_val[a] = s_val[b];
-        s_val[b] = tmp;
-        for (int t = a + 1; t < 2 * kb; ++t) if (s_pos[t] == c) s_val[t] = s_val[a];
-        for (int t = b + 1; t < 2 * kb; ++t) if (s_pos[t] == p) s_val[t] = s_val[b];
+        const int b = p < kb ? p : s_pos[kb + c];
+        const int t = s_val[c];
+        s_val[c] = s_val[b];
+        s_val[b] = t;
       }
     __syncthreads();
-    if (tid < 2 * kb) pm[s_pos[tid]] = s_val[tid];  // duplicates write the same value
+    // slot tid: in use, its position, the position its content comes from
+    const bool used = tid < kb || (tid < 2 * kb && s_pos[tid] == tid);
+    int pos = 0, from = 0;
+    if (used) {
+      const int st = s_val[tid];
+      pos = tid < kb ? tid : s_sw[tid - kb];
+      from = st < kb ? st : s_sw[st - kb];
+    }
+    const bool moved = used && from != pos;
+    const int old = moved ? pm[from] : 0;
+    // for the fused tail (kb <= 16: every slot in warp 0): the source rows of the sub-panel's
+    // rows and the moves to rows below it, in slot order
+    if (warp == 0 && kb <= 16) {
+      if (lane < kb) s_srow[lane] = k0 + from;
+      const unsigned mask = __ballot_sync(0xffffffffu, moved && lane >= kb);
+      if (moved && lane >= kb) {
+        const int x = __popc(mask & ((1u << lane) - 1u));
+        s_fdst[x] = k0 + pos;
+        s_fsrc[x] = k0 + from;
+      }
+      if (lane == 0) s_nfar = __popc(mask);
+    }
+    __syncthreads();
+    if (moved) pm[pos] = old;
   }
   {
     const double s = logdet_sum<NT>(piv2, kb, flags);
     if (tid == 0) ld[b0 + mat] += s;
+  }
+  // swap_from >= 0 (sub-panels of at most 16 columns): the sub-panel's interchanges on the
+  // columns [swap_from, c_end) outside it (the rest of its outer panel) and U12 for the columns
+  // [k0 + kb, c_end), with L11 still in the shared panel.  The columns outside the outer panel
+  // take all of its interchanges at once afterwards (k_swap_outer).
+  if (swap_from >= 0 && kb <= 16) {
+    const int nfar = s_nfar;
+    for (int j = swap_from + tid; j < c_end; j += NT) {
+      if (j >= k0 && j < k0 + kb) continue;
+      panel_column_tail<S, C>(re, im, ldm, j, kb, k0, s_srow, nfar, s_fdst, s_fsrc, P, ps,
+                              j >= k0 + kb);
+    }
   }
 }
 
@@ -2411,6 +2614,14 @@ Lattice make_lattice(const Engine& e, const double* d_phi) {
 // float32 refinement on, diag(G) is read from those tiles (k_refine_lower_rows/_cols) and the
 // upper tiles are never filled; otherwise k_mirror copies the lower triangle up and the row
 // kernels read whole rows.
+// The pivoted sub-panel's interchanges and U12 inside the panel launch; k_swap_trsm as a
+// separate launch where SCA_FUSED_SWAP=0 (the comparison path of its test).
+bool fused_panel_swap() {
+  if (const char* v = std::getenv("SCA_FUSED_SWAP"))
+    if (std::atoi(v) == 0) return false;
+  return true;
+}
+
 // The pivoted group's pivot-block inverse by blocked triangular inversion (k_tinv_blocked); the
 // row-solve kernel k_tinv_warp where SCA_TINV_BLOCKED=0 (the comparison path of its test).
 bool blocked_tinv() {
@@ -2493,27 +2704,35 @@ sca_status piv_subpanels(Engine& e, S* M, int b0, int cnt, int k0, int kb, int n
                          int* perm, bool want_grad, cudaStream_t s) {
   const int N = e.N, kend = k0 + kb;
   const int nbi = std::min(nb_sub, kb);
+  const int jstart = want_grad ? 0 : k0;
+  // sub-panels of at most 16 columns apply their interchanges to the rest of the outer panel
+  // and solve U12 there in the same launch; the columns outside the outer panel take all of
+  // its interchanges in one k_swap_outer launch at the end (fused).  Otherwise (a sub-panel as
+  // wide as its outer panel) k_swap_trsm applies them to every other column.
+  const bool fused = nbi <= 16 && fused_panel_swap();
   for (int s0 = k0; s0 < kend; s0 += nbi) {
     const int kbi = std::min(nbi, kend - s0);
     const size_t sm = sizeof(cpx<CP>) * (size_t)(N - s0) * (kbi + 1) + 5 * sizeof(int) * kbi;
-    prof_begin(e, kPanel, s);
-    k_panel_smem<S, CP, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, s0,
-                                                   kbi, b0, e.ld, piv, perm, e.flags);
-    prof_end(e, kPanel, s);
-    SCA_LAUNCH_CHECK("panel");
-    if (!want_grad && s0 + kbi == N) break;
-    const int jstart = want_grad ? 0 : k0;
-    const int ncols = N - jstart;
-    // interchanges on the other columns, then U12 for the rest of the outer panel
+    const bool lu_done = !want_grad && s0 + kbi == N;  // LU only: nothing trails the last one
     if (s0 + kbi < kend && kbi > 16) {
       set_error("pivoted sub-panel wider than 16 inside an outer panel");
       return SCA_EINVAL;
     }
-    prof_begin(e, kSwap, s);
-    k_swap_trsm<S, CP><<<dim3((ncols + 127) / 128, cnt), 128, 0, s>>>(
-        M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, jstart, kend, piv);
-    prof_end(e, kSwap, s);
-    SCA_LAUNCH_CHECK("swap");
+    prof_begin(e, kPanel, s);
+    k_panel_smem<S, CP, 512><<<cnt, 512, sm, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride, s0,
+                                                   kbi, b0, e.ld, piv, perm, e.flags,
+                                                   fused && !lu_done ? k0 : -1, kend);
+    prof_end(e, kPanel, s);
+    SCA_LAUNCH_CHECK("panel");
+    if (lu_done) break;
+    if (!fused) {
+      const int ncols = N - jstart;
+      prof_begin(e, kSwap, s);
+      k_swap_trsm<S, CP><<<dim3((ncols + 127) / 128, cnt), 128, 0, s>>>(
+          M, N, e.ldm, e.mat_stride, e.plane_stride, s0, kbi, jstart, kend, piv);
+      prof_end(e, kSwap, s);
+      SCA_LAUNCH_CHECK("swap");
+    }
     if (s0 + kbi < kend) {  // bring the rest of the outer panel up to date
       prof_begin(e, kPanelUpd, s);
       const int gx = (N - s0 - kbi + kGemmPanelRows - 1) / kGemmPanelRows;
@@ -2522,6 +2741,16 @@ sca_status piv_subpanels(Engine& e, S* M, int b0, int cnt, int k0, int kb, int n
       prof_end(e, kPanelUpd, s);
       SCA_LAUNCH_CHECK("panel update");
     }
+  }
+  const int nco = (k0 - jstart) + (N - kend);  // columns outside the outer panel
+  if (fused && nco > 0) {
+    const size_t smo = swap_outer_smem(N - k0, kb, sizeof(S));
+    const int gx = std::min((nco + kSwapStrip - 1) / kSwapStrip, kSwapCtas);
+    prof_begin(e, kSwap, s);
+    k_swap_outer<S><<<dim3(gx, cnt), 256, smo, s>>>(M, N, e.ldm, e.mat_stride, e.plane_stride,
+                                                     k0, kb, jstart, piv);
+    prof_end(e, kSwap, s);
+    SCA_LAUNCH_CHECK("outer swap");
   }
   return SCA_OK;
 }
@@ -2968,6 +3197,7 @@ sca_status set_smem_limits() {
     if ((err = allow_max_smem(k_tinv_blocked<S, 512>)) != cudaSuccess)
       return cuda_fail(err, "smem tinv blocked");
   if ((err = allow_max_smem(k_refine<S>)) != cudaSuccess) return cuda_fail(err, "smem refine");
+  if ((err = allow_max_smem(k_swap_outer<S>)) != cudaSuccess) return cuda_fail(err, "smem swap");
   once.mark();
   return SCA_OK;
 }

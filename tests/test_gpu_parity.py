@@ -378,6 +378,33 @@ def test_blocked_pivoted_inverse_matches_row_solves(L, nw, prec, monkeypatch):
     assert np.max(np.abs(res["1"][1] - res["0"][1])) <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "fp64"])
+@pytest.mark.parametrize("L,nw", [(6, 12), (20, 8), (34, 6)])
+def test_fused_subpanel_interchanges_are_bit_identical(L, nw, prec, monkeypatch):
+    """The pivoted sub-panel's interchanges on the rest of its outer panel with the U12 solve
+    at the end of the panel launch, and the outer panel's composed interchanges on all other
+    columns in one launch afterwards, give bit-identical log-dets, diag(G) and potential to
+    the per-sub-panel k_swap_trsm launches (the same entries moved, the same arithmetic), and
+    match the oracle.  N = 36, 400 and 1156 cover sub-panels of 16 and a narrower last one;
+    the potential alone (LU, no inverse) leaves the columns before the outer panel alone."""
+    monkeypatch.setenv("SCA_FUSED", "0")
+    p = api.Params(L, nw, U=4.0, T=0.1, delta=1.0, prec=prec)
+    phi = inputs.random_phi(5 + L, p.N, 1.0)
+    res, pot = {}, {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SCA_FUSED_SWAP", flag)
+        with api.Context(p) as c:
+            res[flag] = c.blocks(phi, grad=True)
+            pot[flag] = c.potential(phi)
+    o_om, o_g, o_ld, o_gd = oracle.omega_grad(oparams(p), phi, per_block=True)
+    t = tol(prec)
+    assert np.allclose(res["1"][0], o_ld, rtol=t["ld"], atol=t["ld"])
+    assert np.max(np.abs(res["1"][1] - o_gd)) <= t["g"] * max(1.0, np.abs(o_gd).max())
+    assert np.array_equal(res["1"][0], res["0"][0])
+    assert np.array_equal(res["1"][1], res["0"][1])
+    assert pot["1"] == pot["0"]
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
 def test_tensor_core_pivot_block_inverse_matches_register_kernel(prec, monkeypatch):
     """The dominant pivot-block inverse on the tensor cores (tableau in TMEM, split-TF32
