@@ -22,8 +22,12 @@ namespace {
 thread_local std::string t_err;
 
 // SMs the dominant group's persistent tensor-core launches leave free while the pivoted
-// group runs beside them on its own (high-priority) stream.
+// group runs beside them on its own (high-priority) stream.  Above N = 2048 the pivoted chain
+// (sub-panels of 4 columns at N = 4096: over 2000 launches per step) bounds the step, and more
+// SMs shorten it: 64x64 workload at 121.6 / 119.0 / 113.9 / 110.6 / 112.9 / 118.7 ms per step
+// with 8 / 16 / 24 / 32 / 40 / 48 SMs kept free.
 constexpr int kDefaultSmReserve = 8;
+constexpr int kLargeNSmReserve = 32;
 // Problems with 1024 <= N <= 2048 and at least 64 dominant blocks start with an SM partition
 // that keeps the dominant group's launches off this many SMs (sca_set_sm_partition changes
 // it), so that the pivoted chain's kernels never wait for a dominant CTA to leave an SM.  With
@@ -243,7 +247,7 @@ sca_status allocate(Engine& e) {
   if ((st = fused_prepare(e)) != SCA_OK) { release(e); return st; }
   if (e.tc && e.piv_blocks > 0) {
     // SMs kept free for the pivoted group (SCA_SM_RESERVE overrides the default)
-    int r = kDefaultSmReserve;
+    int r = e.N > 2048 ? kLargeNSmReserve : kDefaultSmReserve;
     if (const char* v = std::getenv("SCA_SM_RESERVE")) r = std::atoi(v);
     e.sm_reserve = std::max(0, std::min(r, tc_sms(e) / 2));
   }

@@ -2622,6 +2622,11 @@ bool fused_panel_swap() {
   return true;
 }
 
+bool pivoted_first() {
+  const char* v = std::getenv("SCA_PIVOTED_FIRST");
+  return v && std::atoi(v) != 0;
+}
+
 // The pivoted group's pivot-block inverse by blocked triangular inversion (k_tinv_blocked); the
 // row-solve kernel k_tinv_warp where SCA_TINV_BLOCKED=0 (the comparison path of its test).
 bool blocked_tinv() {
@@ -3131,10 +3136,13 @@ sca_status run_blocks_t(Engine& e, const double* d_phi, bool want_grad, bool ref
       if (r == SCA_OK) prof_span_end(e, span_d, sd);
       return r;
     };
-    // On their own streams the dominant group is enqueued first: its few long launches then
-    // start at once, while the pivoted group's many short ones are still being enqueued (the
-    // host stays ahead of that chain on the device).
-    if (parted) {
+    // The dominant group is enqueued first: its few long launches then start at once, while
+    // the pivoted group's many short ones are still being enqueued (the host stays ahead of
+    // that chain on the device).  Enqueued the other way round, a long pivoted chain (2000+
+    // launches at N = 4096) fills the launch queue, the host blocks, and the dominant group
+    // starts only when the chain has drained far enough.  SCA_PIVOTED_FIRST=1 restores that
+    // order without partitions (the comparison of the two orders).
+    if (parted || !pivoted_first()) {
       if ((st = dominant_group()) != SCA_OK || (st = pivoted_group()) != SCA_OK) return st;
     } else {
       if ((st = pivoted_group()) != SCA_OK || (st = dominant_group()) != SCA_OK) return st;
