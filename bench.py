@@ -140,7 +140,7 @@ def peaks():
 # on this GB300 with an FMA-chain probe (FP32 75.0 TF/s, FP64 1.20 TF/s).
 TF32_OVER_BF16 = 1.1 / 2.25
 DEFAULT_PREC = "bf16x3"
-DEFAULT_SM_PARTITION = -1  # the library's default (8 SMs for 1024 <= N <= 2048, >= 64 dominant blocks)
+DEFAULT_SM_PARTITION = -1  # the library's default (16 SMs in mode 1 for 1024 <= N <= 2048, >= 64 dominant blocks)
 # DRAM traffic of the dominant group's update launches, per block: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the 7 update launches of one step of the 16-block workload
 # ionic_40x40_w8 (6 merged pairs at 400.1 MB, one single last step at 344.6 MB per 16-block

@@ -363,7 +363,7 @@ sca_status sca_set_panel_precision(sca_ctx* ctx, int32_t prec);
  * partition that leaves twice as many SMs to the pivoted group, its updates on the first (in
  * between the two sizes, which the driver's 8-SM granularity does not offer).
  * pivoted_sms = 0 removes the partition (the dominant group's persistent tensor-core launches
- * then leave 8 SMs free, and priorities do the rest).  Contexts with 1024 <= N <= 2048 and at
+ * then leave 8 SMs free, 32 above N = 2048, and priorities do the rest).  Contexts with 1024 <= N <= 2048 and at
  * least 64 dominant blocks start with a partition when the driver grants it: 16 SMs in mode 1
  * where the dominant blocks' elimination steps are merged in pairs (the tensor-core path), else
  * 8 SMs in mode 3.
