@@ -5,8 +5,10 @@ sca_grad_noalloc_dev serves callers that cannot let the library allocate device 
 workspace is a static 64 MiB device array shared by every call, so the test checks two
 calls in a row (the second sees the first call's leftovers), a problem large enough to be
 processed in several chunks of that array, and the rejection of a problem whose single block
-does not fit, and a call after the device's context was re-created (the array's address
-moves with the context).  This file is collected last on purpose.
+does not fit, a call after the device's context was re-created (the array's address
+moves with the context), and, with the CUDA runtime's allocation calls counted by a
+preloaded shim, that the calls themselves allocate nothing.  This file is collected last on
+purpose.
 """
 import ctypes
 import os
@@ -118,3 +120,108 @@ def test_noalloc_after_context_reset():
                        text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "noalloc-after-reset ok" in r.stdout
+
+
+# Counts the CUDA runtime's allocating calls made through the dynamic linker (the library
+# links libcudart dynamically) and forwards each to the runtime.
+_SHIM_SRC = r"""
+#define _GNU_SOURCE
+#include <dlfcn.h>
+#include <stddef.h>
+
+static long g_calls;
+
+long shim_alloc_calls(void) { return __atomic_load_n(&g_calls, __ATOMIC_SEQ_CST); }
+void shim_reset(void) { __atomic_store_n(&g_calls, 0, __ATOMIC_SEQ_CST); }
+
+static void* real_fn(const char* name) {
+  void* fn = dlsym(RTLD_NEXT, name);
+  if (!fn) {  /* the runtime came in with a library loaded RTLD_LOCAL */
+    void* h = dlopen("libcudart.so.13", RTLD_NOLOAD | RTLD_LAZY);
+    if (h) fn = dlsym(h, name);
+  }
+  return fn;
+}
+
+#define SHIM(name, params, args, types)                             \
+  int name params {                                                 \
+    __atomic_add_fetch(&g_calls, 1, __ATOMIC_SEQ_CST);              \
+    int (*fn) types = (int (*) types)real_fn(#name);                \
+    return fn ? fn args : 999; /* cudaErrorUnknown if not found */  \
+  }
+
+SHIM(cudaMalloc, (void** p, size_t n), (p, n), (void**, size_t))
+SHIM(cudaFree, (void* p), (p), (void*))
+SHIM(cudaMallocAsync, (void** p, size_t n, void* s), (p, n, s), (void**, size_t, void*))
+SHIM(cudaFreeAsync, (void* p, void* s), (p, s), (void*, void*))
+SHIM(cudaMallocManaged, (void** p, size_t n, unsigned fl), (p, n, fl), (void**, size_t, unsigned))
+SHIM(cudaMallocPitch, (void** p, size_t* pitch, size_t w, size_t h), (p, pitch, w, h),
+     (void**, size_t*, size_t, size_t))
+SHIM(cudaMallocHost, (void** p, size_t n), (p, n), (void**, size_t))
+SHIM(cudaHostAlloc, (void** p, size_t n, unsigned fl), (p, n, fl), (void**, size_t, unsigned))
+SHIM(cudaFreeHost, (void* p), (p), (void*))
+"""
+
+_COUNT_CHILD = r"""
+import ctypes, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2311_04435_gb300 import _lib, api, inputs
+
+shim = ctypes.CDLL(sys.argv[2])  # the preloaded copy
+shim.shim_alloc_calls.restype = ctypes.c_long
+lib = _lib.lib()
+rt_path = next(ln.split()[-1] for ln in open("/proc/self/maps") if "libcudart.so" in ln)
+rt = ctypes.CDLL(rt_path)  # calls through this handle bypass the shim
+vp = ctypes.c_void_p
+
+def ok(err, what):
+    assert err == 0, f"{what}: CUDA error {err}"
+
+p = api.Params(10, 16, U=4.0, T=0.1, delta=0.5, prec="fp32")
+n = p.N
+d = [vp(), vp(), vp()]
+for k, size in enumerate((8 * n, 8, 8 * n)):
+    ok(rt.cudaMalloc(ctypes.byref(d[k]), ctypes.c_size_t(size)), "cudaMalloc")
+phis = [inputs.random_phi(70 + k, n) for k in range(2)]
+got = []
+shim.shim_reset()
+for phi in phis:  # the first call on this device and the one after it
+    ok(rt.cudaMemcpy(d[0], phi.ctypes.data_as(vp), ctypes.c_size_t(8 * n), 1), "upload")
+    _lib.check(lib.sca_grad_noalloc_dev(ctypes.byref(p.c()), d[0], d[1], d[2], None))
+    ok(rt.cudaDeviceSynchronize(), "sync")
+    om, g = np.zeros(1), np.zeros(n)
+    ok(rt.cudaMemcpy(om.ctypes.data_as(vp), d[1], ctypes.c_size_t(8), 2), "read Omega")
+    ok(rt.cudaMemcpy(g.ctypes.data_as(vp), d[2], ctypes.c_size_t(8 * n), 2), "read grad")
+    got.append((float(om[0]), g))
+calls = shim.shim_alloc_calls()
+assert calls == 0, f"{calls} allocating runtime calls during sca_grad_noalloc_dev"
+for phi, (om, g) in zip(phis, got):
+    with api.Context(p) as c:
+        om_ref, g_ref = c.grad(phi)
+    assert abs(om - om_ref) <= 1e-5 * abs(om_ref), (om, om_ref)
+    assert np.max(np.abs(g - g_ref)) <= 1e-7 * max(1.0, np.abs(g_ref).max())
+# the context path allocates through the same runtime: the shim saw it
+assert shim.shim_alloc_calls() > 0, "the shim did not intercept the runtime's allocation calls"
+for x in d:
+    ok(rt.cudaFree(x), "cudaFree")
+print("noalloc-no-allocating-calls ok")
+"""
+
+
+def test_noalloc_makes_no_allocating_call(tmp_path):
+    """In a fresh process whose CUDA runtime allocation calls (cudaMalloc, cudaFree and their
+    async, managed, pitched and pinned-host forms) are counted by a preloaded shim: two calls
+    of the entry point, the first one on the device included, make none of them, and their
+    results match the context path, whose own allocations the shim does see."""
+    shim = tmp_path / "libcount_alloc.so"
+    src = tmp_path / "count_alloc.c"
+    src.write_text(_SHIM_SRC)
+    subprocess.run(["gcc", "-O1", "-shared", "-fPIC", "-o", str(shim), str(src), "-ldl"],
+                   check=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, LD_PRELOAD=str(shim))
+    r = subprocess.run([sys.executable, "-c", _COUNT_CHILD, root, str(shim)], capture_output=True,
+                       text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "noalloc-no-allocating-calls ok" in r.stdout
